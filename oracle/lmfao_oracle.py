@@ -1,0 +1,218 @@
+"""CPU oracle for batches of group-by aggregates over a natural join.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the engine imports this module: only the tests,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs of
+``bench.py`` may call it. It shares no code with the CUDA path.
+
+What it computes (Section 1 and Section 2 of the paper): every query of a batch is
+
+    SELECT G, SUM(prod_i f_i(x)) ... FROM D WHERE cond GROUP BY G
+
+over ``D``, the natural join of all relations (attributes with equal names are
+equated). The oracle follows that definition literally and does none of the method's
+optimisations (no views, no factorisation, no per-query roots):
+
+1. ``natural_join`` materialises D as one row-index vector per relation, by hash-joining
+   the relations one at a time on all attributes shared with the relations joined so far
+   (duplicate keys give one joined tuple per combination; unmatched tuples drop out).
+2. ``evaluate`` computes, per query, the filter mask (predicates compared on the stored
+   FP32 / integer values), the group key of every joined tuple, each aggregate's product
+   of factors in FP64 from the stored values, and sums them per group in FP64 in tuple
+   order (``numpy.bincount``); COUNT is an INT64 count of joined tuples per group.
+   It also returns, per aggregate and group, the sum of the absolute values of the terms,
+   the scale against which the engine's rounding error is judged.
+3. ``cart_variances`` derives the CART split variances (Section 3, decision trees):
+   VARIANCE = SUM(y^2) - SUM(y)^2 / |T| for the left fragment (buckets 0..k) and the
+   right fragment (the rest) of every threshold, in FP64.
+
+Groups are returned in ascending lexicographic key order and only where COUNT > 0; an
+ungrouped query always returns its single group, even when D is empty.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_OPS = {
+    "le": np.less_equal, "lt": np.less, "ge": np.greater_equal, "gt": np.greater,
+    "eq": np.equal, "ne": np.not_equal,
+}
+
+
+def _cols(R):
+    return {c["attr"]: c for c in R["columns"]}
+
+
+def natural_join(rels, order=None):
+    """Row indices of the natural join of ``rels``: one int64 vector per relation.
+
+    ``order`` is the sequence of relation positions to join (default: start from the
+    first relation and repeatedly take the first remaining relation that shares an
+    attribute with those joined so far). Each step joins on all shared attributes, so
+    the result is the natural join whatever the order.
+    """
+    n = len(rels)
+    if order is None:
+        order = [0]
+        joined_attrs = set(_cols(rels[0]))
+        while len(order) < n:
+            for i in range(n):
+                if i not in order and joined_attrs & set(_cols(rels[i])):
+                    order.append(i)
+                    joined_attrs |= set(_cols(rels[i]))
+                    break
+            else:
+                order.append(next(i for i in range(n) if i not in order))
+                joined_attrs |= set(_cols(rels[order[-1]]))
+    first = order[0]
+    idx = {first: np.arange(rels[first]["nrows"], dtype=np.int64)}
+    attr_home = {a: first for a in _cols(rels[first])}
+    for i in order[1:]:
+        R = rels[i]
+        shared = [a for a in _cols(R) if a in attr_home]
+        m = len(next(iter(idx.values())))
+        if shared:
+            # codes of both sides on the shared attributes, mixed radix with a radix that
+            # exceeds every value seen on either side (so equal codes mean equal values)
+            left = np.zeros(m, dtype=np.int64)
+            right = np.zeros(R["nrows"], dtype=np.int64)
+            for a in shared:
+                home = attr_home[a]
+                lv = _cols(rels[home])[a]["data"][idx[home]].astype(np.int64)
+                rv = _cols(R)[a]["data"].astype(np.int64)
+                radix = 1 + max(int(lv.max(initial=0)), int(rv.max(initial=0)))
+                left = left * radix + lv
+                right = right * radix + rv
+            perm = np.argsort(right, kind="stable")
+            rs = right[perm]
+            lo = np.searchsorted(rs, left, side="left")
+            hi = np.searchsorted(rs, left, side="right")
+        else:
+            perm = np.arange(R["nrows"], dtype=np.int64)
+            lo = np.zeros(m, dtype=np.int64)
+            hi = np.full(m, R["nrows"], dtype=np.int64)
+        cnt = hi - lo
+        rep = np.repeat(np.arange(m, dtype=np.int64), cnt)
+        start = np.repeat(lo, cnt)
+        offs = np.arange(len(rep), dtype=np.int64) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        for k in idx:
+            idx[k] = idx[k][rep]
+        idx[i] = perm[start + offs]
+        for a in _cols(R):
+            attr_home.setdefault(a, i)
+    return [idx[i] for i in range(n)]
+
+
+class JoinedData:
+    """The materialised natural join: attribute values of every joined tuple."""
+
+    def __init__(self, rels, order=None):
+        self.rels = rels
+        self.idx = natural_join(rels, order)
+        self.size = len(self.idx[0]) if rels else 0
+        self._home = {}
+        for i, R in enumerate(rels):
+            for c in R["columns"]:
+                self._home.setdefault(c["attr"], (i, c))
+        self._cache = {}
+
+    def stored(self, attr):
+        """Stored values (FP32 / integer, as loaded) of ``attr`` on every joined tuple."""
+        i, c = self._home[attr]
+        return c["data"][self.idx[i]]
+
+    def f64(self, attr):
+        if attr not in self._cache:
+            self._cache[attr] = self.stored(attr).astype(np.float64)
+        return self._cache[attr]
+
+
+def _factor(J, f):
+    attr, fn, p = f
+    x = J.f64(attr)
+    if fn == "id":
+        return x
+    if fn == "pow":
+        out = np.ones_like(x)
+        for _ in range(int(p)):
+            out = out * x
+        return out
+    raise ValueError(f"unknown factor function {fn}")
+
+
+def _group_code(J, g):
+    attr, kind, thr = g
+    v = J.stored(attr)
+    if kind == "value":
+        return v.astype(np.int64)
+    if kind == "bucket":
+        # bucket(x) = number of thresholds strictly below x (x == t lies in the <= side)
+        t = np.asarray(thr, dtype=np.float32)
+        return np.searchsorted(t, v.astype(np.float32), side="left").astype(np.int64)
+    raise ValueError(f"unknown group-by kind {kind}")
+
+
+def evaluate_query(J, q):
+    """One query over the materialised join ``J``; see the module docstring."""
+    mask = np.ones(J.size, dtype=bool)
+    for attr, op, t in q.get("filters", []):
+        v = J.stored(attr)
+        if v.dtype.kind == "f":
+            mask &= _OPS[op](v, np.float32(t))
+        else:
+            mask &= _OPS[op](v.astype(np.float64), float(np.float32(t)))
+    sel = np.nonzero(mask)[0]
+    gb = q.get("groupby", [])
+    if gb:
+        codes = np.stack([_group_code(J, g)[sel] for g in gb], axis=1) if len(sel) else \
+            np.zeros((0, len(gb)), dtype=np.int64)
+        keys, inv = np.unique(codes, axis=0, return_inverse=True)
+        inv = inv.reshape(-1)
+        ng = len(keys)
+    else:
+        keys = np.zeros((1, 0), dtype=np.int64)
+        inv = np.zeros(len(sel), dtype=np.int64)
+        ng = 1
+    counts = np.bincount(inv, minlength=ng).astype(np.int64)
+    naggs = len(q["aggs"])
+    sums = np.zeros((ng, naggs), dtype=np.float64)
+    abs_sums = np.zeros((ng, naggs), dtype=np.float64)
+    for j, agg in enumerate(q["aggs"]):
+        term = np.ones(len(sel), dtype=np.float64)
+        for f in agg:
+            term = term * _factor(J, f)[sel]
+        sums[:, j] = np.bincount(inv, weights=term, minlength=ng)
+        abs_sums[:, j] = np.bincount(inv, weights=np.abs(term), minlength=ng)
+    return {"keys": keys.astype(np.int64), "counts": counts, "sums": sums, "abs": abs_sums}
+
+
+def evaluate(rels, queries, order=None):
+    """All queries of a batch over the natural join of ``rels`` (FP64 sums, INT64 counts)."""
+    J = JoinedData(rels, order)
+    return [evaluate_query(J, q) for q in queries]
+
+
+def cart_variances(result):
+    """CART split variances from a bucketed query with aggregates COUNT, SUM(y), SUM(y^2)
+    (Section 3): for every threshold k (between bucket k and k+1) the left fragment is
+    buckets 0..k and the right fragment the remaining buckets; VARIANCE of a fragment T is
+    SUM(y^2) - SUM(y)^2 / |T| (0 for an empty fragment). Returns (left, right) arrays over
+    the thresholds of the bucket domain [0, nb) with nb = max bucket + 1 seen."""
+    keys = result["keys"][:, 0]
+    nb = int(keys.max()) + 1 if len(keys) else 1
+    n = np.zeros(nb, dtype=np.int64)
+    s = np.zeros(nb)
+    s2 = np.zeros(nb)
+    n[keys] = result["counts"]
+    s[keys] = result["sums"][:, 1]
+    s2[keys] = result["sums"][:, 2]
+
+    def var(cnt, a, a2):
+        out = np.zeros(len(cnt))
+        nz = cnt > 0
+        out[nz] = a2[nz] - a[nz] * a[nz] / cnt[nz]
+        return out
+
+    cn, cs, cs2 = np.cumsum(n), np.cumsum(s), np.cumsum(s2)
+    left = var(cn[:-1], cs[:-1], cs2[:-1])
+    right = var(cn[-1] - cn[:-1], cs[-1] - cs[:-1], cs2[-1] - cs2[:-1])
+    return left, right
