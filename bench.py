@@ -1,0 +1,297 @@
+"""Throughput of one aggregate batch over a join: fact tuples/s on one B300.
+
+Workload: the Retailer-shaped 5-relation snowflake (84M fact tuples; Item 3,700 x 4 features,
+Location 1,300 x 10 -> Census 1,300 x 14, Weather 160,000 (locn, date) pairs x 8 features;
+3 categoricals of 24/12/50 values) with its ridge-regression batch: COUNT, 37 SUM(x),
+703 SUM(x_i x_j), one-hot group-bys per categorical and per categorical pair
+(Section 3, linear regression). Seeded synthetic data of that shape stand in for the
+Retailer dataset.
+
+A step is one lmfao_run of the whole batch (view kernels, root pass, combine) with the
+relations resident in HBM; the fact columns (1.3 GB) exceed L2, so no flush is needed.
+Prints one JSON line (the driver's contract) with roofline, CPU-oracle baseline, clocks,
+and an end-to-end number through the C ABI from pinned host buffers.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fact tuples/s per aggregate batch"
+UNIT = "tuples/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def workload(n_fact, seed=0):
+    from paper_2008_08657_b300 import workloads as W
+    return W.retailer_schema(n_fact=n_fact, seed=seed), W.retailer_batch()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.p = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"),
+                                       f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            rows = [[x.strip() for x in r] for r in rows if len(r) >= 7]
+            sm = [float(r[0]) for r in rows]
+            mx = max(float(r[1]) for r in rows)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+            return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+        except Exception as e:  # noqa: BLE001
+            return {"error": str(e)}
+
+
+def time_runs(eng, torch, stream, steps, warmup):
+    for _ in range(warmup):
+        eng.run(stream)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    fact_ms = []
+    evs[0].record(stream)
+    for i in range(steps):
+        eng.run(stream)
+        evs[i + 1].record(stream)
+        kt = None
+        if eng._profiling:
+            kt = eng.kernel_times()
+            fact_ms.append(sum(ms for n, ms in kt if n == "fact_pass"))
+    torch.cuda.synchronize()
+    ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    return ms, fact_ms
+
+
+def bench_lmfao(args):
+    import torch
+    from paper_2008_08657_b300.lmfao import Engine
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    rels, qs = workload(args.fact_rows, seed=args.seed)
+    n_fact = rels[0]["nrows"]
+    eng = Engine(local)
+    for R in rels:
+        eng.load_relation(R)
+    eng.add_queries(qs)
+    info = eng.plan(precision=args.precision)
+    desc = eng.describe()
+    stream = torch.cuda.Stream()
+    # kernel-level timing of the dominant kernel (CUDA events inside lmfao_run, same stream)
+    eng.set_profiling(True)
+    eng._profiling = True
+    _, fact_ms = time_runs(eng, torch, stream, max(3, args.steps // 2), 2)
+    eng.set_profiling(False)
+    eng._profiling = False
+    # the timed region proper
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks() as clk:
+        ms, _ = time_runs(eng, torch, stream, args.steps, args.warmup)
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n_fact / (ms_step / 1e3)
+    # plain FP64 GPU form of the same plan shape (same batch, FP64 arithmetic)
+    fp64_ms = None
+    if not args.skip_fp64:
+        eng64 = Engine(local)
+        for R in rels:
+            eng64.load_relation(R)
+        eng64.add_queries(qs)
+        eng64.plan(precision="fp64")
+        eng64._profiling = False
+        ms64, _ = time_runs(eng64, torch, stream, max(2, args.steps // 4), 1)
+        fp64_ms = float(np.mean(ms64))
+        eng64.close()
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    fbytes = desc["physical"]["fact_pass_bytes"]
+    fms = float(np.mean(fact_ms)) if fact_ms else None
+    achieved = fbytes / (fms / 1e3) / 1e9 if fms else None
+    roofline = {"bound": "hbm", "kernel": "fact_pass", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
+                "algorithmic_bytes": fbytes, "kernel_ms": fms, "traffic": None}
+    # end to end through the C ABI: pinned host -> device copies, load, plan, run, fetch
+    e2e = None
+    if not args.skip_e2e:
+        e2e = bench_e2e(args, rels, qs, torch, local)
+    eng.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded, Retailer-shaped)",
+        "config": {"workload": f"retailer-snowflake ridge batch, {n_fact} fact tuples, {len(qs)} queries, "
+                               f"{sum(len(q['aggs']) for q in qs)} aggregates", "fact_tuples": n_fact,
+                   "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
+                   "segments": info["n_segments"], "segment_relation": desc["physical"]["segment_relation"]},
+        "roofline": roofline,
+        "vs_plain_fp64_gpu": (fp64_ms / ms_step) if fp64_ms else None,
+        "plain_fp64_ms_per_step": fp64_ms,
+        "plan_ms": info["plan_ms"],
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": info["n_kernels"] * args.steps,
+    }
+    if rank == 0 and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def bench_e2e(args, rels, qs, torch, local):
+    from paper_2008_08657_b300.lmfao import Engine
+    pinned = []
+    h2d = 0
+    for R in rels:
+        cols = []
+        for c in R["columns"]:
+            t = torch.from_numpy(np.ascontiguousarray(c["data"])).pin_memory()
+            cols.append(t)
+            h2d += t.numel() * t.element_size()
+        pinned.append(cols)
+    steps = max(2, args.steps // 5)
+    times = []
+    d2h = 0
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eng = Engine(local)
+        for R, cols in zip(rels, pinned):
+            dev = [c.cuda(non_blocking=True) for c in cols]
+            torch.cuda.synchronize()
+            eng.load_relation(dict(R, columns=[dict(c, data=d) for c, d in zip(R["columns"], dev)]), where="device")
+        eng.add_queries(qs)
+        eng.plan(precision=args.precision)
+        eng.run()
+        res = eng.fetch_all()
+        t1 = time.perf_counter()
+        eng.close()
+        d2h = sum(r["counts"].nbytes + r["sums"].nbytes + r["keys"].nbytes for r in res)
+        if i > 0:
+            times.append(t1 - t0)
+    s = float(np.mean(times))
+    return {"value": rels[0]["nrows"] / s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "seconds_per_step": s,
+            "includes": "pinned H2D of all relations, lmfao_load_relation, lmfao_plan (trie reorganisation), "
+                        "lmfao_run, lmfao_fetch of every query"}
+
+
+def cpu_baseline(args, sample_rows=300_000):
+    """The oracle as it stands, on a bounded sample of the same workload (first
+    ``sample_rows`` fact tuples with all dimension relations), timed on the host."""
+    from oracle import lmfao_oracle as O
+    rels, qs = workload(sample_rows, seed=args.seed)
+    t0 = time.perf_counter()
+    O.evaluate(rels, qs)
+    dt = time.perf_counter() - t0
+    cores = 1  # numpy evaluation of the oracle runs on one host thread
+    return {"value": sample_rows / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_rows} fact tuples of the same schema and batch, {dt:.1f} s",
+            "host_cpus": os.cpu_count()}
+
+
+def bench_reference(args):
+    """Reference arm: the CPU oracle on a bounded sample per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import lmfao_oracle as O
+    sample = args.ref_rows
+    rels, qs = workload(sample, seed=args.seed)
+    for _ in range(args.warmup):
+        O.evaluate(rels, qs)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.evaluate(rels, qs)
+        t.append(time.perf_counter() - t0)
+    s = float(np.mean(t))
+    v = sample / s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, Retailer-shaped)",
+        "config": {"workload": f"retailer-snowflake ridge batch, sample of {sample} fact tuples per step",
+                   "fact_tuples": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} fact tuples per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lmfao", choices=["lmfao", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fact-rows", type=int, default=84_000_000)
+    ap.add_argument("--ref-rows", type=int, default=200_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "lmfao":
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_lmfao(args)
+
+
+if __name__ == "__main__":
+    main()

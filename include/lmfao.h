@@ -1,0 +1,242 @@
+/*
+ * lmfao.h -- C ABI of a B300 (sm_103a) engine for batches of group-by aggregates
+ * over the natural join of an acyclic schema.
+ *
+ * The problem (Section 1, Section 2 of "LMFAO: An Engine for Batches of Group-By
+ * Aggregates"): given relations R_1..R_m whose attributes with equal names are
+ * equated (the natural join D), evaluate many queries of the form
+ *
+ *     SELECT G, SUM(prod_i f_i(x)), ... FROM D WHERE cond GROUP BY G
+ *
+ * in one plan, bottom-up along a join tree, with views keyed by join attributes so
+ * that D is never materialised. The cardinality constraints of Section 2 (relation
+ * sizes, attribute domains) are part of the input: every join or categorical
+ * attribute declares its domain [0, domain).
+ *
+ * Conventions for every call:
+ *   - The return value is an int status: LMFAO_OK (0) or a negative LMFAO_ERR_* code.
+ *     The message of the last failing call on a context is lmfao_last_error(ctx).
+ *     No C++ exception crosses this boundary.
+ *   - Strings are NUL-terminated and only read during the call.
+ *   - Pointers marked "host" are CPU memory; "device" pointers are CUDA device memory
+ *     of the context's device. Nothing is retained after a call returns unless the
+ *     call says so (LMFAO_ADOPT_DEVICE, lmfao_fetch results).
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef LMFAO_H
+#define LMFAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LMFAO_API __attribute__((visibility("default")))
+#else
+#define LMFAO_API
+#endif
+
+typedef struct lmfao_ctx lmfao_ctx;
+
+/* ---- status codes ------------------------------------------------------------------ */
+enum {
+  LMFAO_OK = 0,
+  LMFAO_ERR_ARG = -1,          /* malformed argument, unknown attribute or relation    */
+  LMFAO_ERR_DTYPE = -2,        /* dtype not allowed for the column's role              */
+  LMFAO_ERR_KEY_RANGE = -3,    /* a key/categorical value outside [0, domain)          */
+  LMFAO_ERR_CYCLIC = -4,       /* the schema has no join tree (GYO reduction fails)    */
+  LMFAO_ERR_NOT_PLANNED = -5,  /* lmfao_run / lmfao_fetch before a successful plan/run */
+  LMFAO_ERR_OOM = -6,          /* device allocation failed                             */
+  LMFAO_ERR_CUDA = -7,         /* a CUDA runtime call failed                           */
+  LMFAO_ERR_TIMEOUT = -8,      /* a bounded device wait ran out                        */
+  LMFAO_ERR_UNSUPPORTED = -9   /* outside what this engine evaluates (message says why)*/
+};
+
+/* ---- relations (Section 2: the database schema with its cardinality constraints) ---- */
+enum { LMFAO_I32 = 0, LMFAO_F32 = 1, LMFAO_U8 = 2 };            /* column dtypes */
+enum { LMFAO_KEY = 0, LMFAO_CAT = 1, LMFAO_CONT = 2 };          /* column roles  */
+
+typedef struct lmfao_column {
+  const char *attr;   /* attribute name; equal names in two relations are joined        */
+  int32_t dtype;      /* KEY and CAT: LMFAO_I32; CONT: LMFAO_F32 or LMFAO_U8 (0/1 flags)  */
+  int32_t role;       /* LMFAO_KEY (join attribute), LMFAO_CAT, LMFAO_CONT               */
+  int64_t domain;     /* KEY and CAT: values lie in [0, domain); ignored for CONT        */
+  const void *data;   /* nrows values, host or device memory according to the flags    */
+} lmfao_column;
+
+enum {
+  LMFAO_HOST = 0,          /* column data are host pointers; copied during the call     */
+  LMFAO_DEVICE = 1,        /* column data are device pointers; copied during the call   */
+  LMFAO_ADOPT_DEVICE = 2   /* device pointers borrowed until lmfao_destroy: the caller
+                              keeps them alive and unchanged                             */
+};
+
+/* ---- aggregate batch (Section 2 queries Q1-Q3; Section 3 LR, CART, Rk-means) ---------- */
+enum { LMFAO_FN_ID = 0, LMFAO_FN_POW = 1 };  /* f(x) = x, f(x) = x^param (param >= 1) */
+
+typedef struct lmfao_factor {
+  const char *attr;   /* a CONT attribute, or a KEY/CAT attribute read as its integer value */
+  int32_t fn;         /* LMFAO_FN_ID or LMFAO_FN_POW                                     */
+  int32_t param;      /* exponent for LMFAO_FN_POW                                        */
+} lmfao_factor;
+
+typedef struct lmfao_aggregate {  /* SUM(prod factors); nfactors == 0 is SUM(1) = COUNT */
+  const lmfao_factor *factors;
+  int32_t nfactors;
+} lmfao_aggregate;
+
+enum { LMFAO_GB_VALUE = 0, LMFAO_GB_BUCKET = 1 };
+
+typedef struct lmfao_groupby {
+  const char *attr;          /* VALUE: a KEY or CAT attribute, grouped by its value      */
+  int32_t kind;              /* BUCKET: a CONT attribute, grouped by the number of       */
+  int32_t nthresholds;       /*   thresholds strictly below x (x == t falls on the <=    */
+  const float *thresholds;   /*   side); thresholds ascending, host memory               */
+} lmfao_groupby;
+
+enum { LMFAO_LE = 0, LMFAO_LT = 1, LMFAO_GE = 2, LMFAO_GT = 3, LMFAO_EQ = 4, LMFAO_NE = 5 };
+
+typedef struct lmfao_predicate {  /* attr op t, compared on the stored FP32/integer value */
+  const char *attr;
+  int32_t op;
+  float t;
+} lmfao_predicate;
+
+/* ---- planning ---------------------------------------------------------------------- */
+enum { LMFAO_FP64 = 0, LMFAO_FP32 = 1, LMFAO_SPLIT_TF32 = 2 };  /* arithmetic of the path */
+enum {
+  LMFAO_PLAN_HEURISTIC = 0,   /* rule-based choices (largest relation as root, ...)        */
+  LMFAO_PLAN_EXHAUSTIVE = 1,  /* time every candidate plan on the device, keep the fastest */
+  LMFAO_PLAN_LEARNED = 2,     /* rank candidates with the learned cost model (MLP)         */
+  LMFAO_PLAN_FORCED = 3       /* use root_rel / segment_rel / mode as given                */
+};
+enum { LMFAO_MODE_AUTO = 0, LMFAO_MODE_FACTORISED = 1, LMFAO_MODE_PER_TUPLE = 2 };
+
+typedef struct lmfao_plan_opts {
+  int32_t precision;        /* LMFAO_FP64 (plain form), LMFAO_FP32, LMFAO_SPLIT_TF32     */
+  int32_t planner;          /* LMFAO_PLAN_*                                              */
+  int32_t root_rel;         /* FORCED: relation id of the root relation (-1: default)   */
+  int32_t segment_rel;      /* FORCED: child of the root whose join key orders the root
+                               relation into segments (-1: none, -2: default)            */
+  int32_t mode;             /* LMFAO_MODE_*: factorised views or per-tuple evaluation   */
+  int32_t autotune;         /* nonzero: time launch shapes once and keep the fastest    */
+  const int32_t *join_parent; /* host, nullable: parent relation id per relation (-1 for
+                               the tree root) to impose a join tree instead of GYO       */
+  const int32_t *query_root;  /* host, nullable: logical root relation per query (-1:
+                               heuristic); used by the view-generation layer             */
+  const char *cost_model;   /* path of a learned cost model file (LEARNED), or NULL      */
+} lmfao_plan_opts;
+
+typedef struct lmfao_plan_info {
+  int32_t root_rel;          /* root relation of the physical plan                      */
+  int32_t segment_rel;       /* relation whose key forms the segments (-1: none)        */
+  int64_t n_segments;        /* segments of the root relation                           */
+  int32_t n_views;           /* directional views of the logical plan (after merging)   */
+  int32_t n_groups;          /* view groups of the logical plan                          */
+  int32_t n_kernels;         /* kernel launches of one lmfao_run                         */
+  int32_t mode;              /* mode chosen                                              */
+  double predicted_ms;       /* planner's time estimate (-1 if none)                     */
+  double plan_ms;            /* host+device time spent planning (incl. reorganisation)   */
+} lmfao_plan_info;
+
+/* ---- results ------------------------------------------------------------------------ */
+typedef struct lmfao_result {
+  int64_t ngroups;            /* groups with COUNT > 0 (an ungrouped query: always 1)    */
+  int32_t ngroupby;           /* group-by attributes of the query                        */
+  int32_t naggs;              /* aggregates of the query                                 */
+  const int32_t *group_keys;  /* host, ngroups x ngroupby, ascending lexicographic order */
+  const int64_t *counts;      /* host, ngroups: COUNT(*) of the group under the filter   */
+  const double *sums;         /* host, ngroups x naggs, row-major                        */
+} lmfao_result;
+
+/* ==== entry points ==================================================================== */
+
+/* Create a context bound to CUDA device `device`; *out receives the handle. With
+ * device == -1 the context is host-only: it takes host relations, batches and plans the
+ * logical layer (join tree, query roots, views, groups; lmfao_describe_plan) but runs
+ * nothing (lmfao_run returns LMFAO_ERR_NOT_PLANNED). LMFAO_ERR_CUDA if the device is
+ * unusable. */
+LMFAO_API int lmfao_create(struct lmfao_ctx **out, int device);
+
+/* Free every device and host resource of the context (adopted columns are not freed). */
+LMFAO_API int lmfao_destroy(struct lmfao_ctx *ctx);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next call. */
+LMFAO_API const char *lmfao_last_error(const struct lmfao_ctx *ctx);
+
+/* Add a relation (Section 2 schema). `cols` describes `ncols` columns of `nrows` values.
+ * KEY/CAT values outside [0, domain) give LMFAO_ERR_KEY_RANGE (checked here).
+ * Relations are immutable once loaded; loading invalidates a previous plan.
+ * *rel_id receives the relation's id (0, 1, ... in load order). */
+LMFAO_API int lmfao_load_relation(struct lmfao_ctx *ctx, const char *name, int64_t nrows,
+                        const lmfao_column *cols, int ncols, uint32_t flags, int *rel_id);
+
+/* Add one query of the batch: `naggs` aggregates sharing the group-by attributes `gb`
+ * and the conjunctive filter `filters` (Section 2 queries; Section 3 aggregates).
+ * Unknown attributes give LMFAO_ERR_ARG. *query_id receives 0, 1, ... in call order.
+ * Adding a query invalidates a previous plan. */
+LMFAO_API int lmfao_add_batch(struct lmfao_ctx *ctx, const lmfao_aggregate *aggs, int naggs,
+                    const lmfao_groupby *gb, int ngb, const lmfao_predicate *filters,
+                    int nfilters, int *query_id);
+
+/* Remove all queries (relations stay loaded). */
+LMFAO_API int lmfao_clear_batch(struct lmfao_ctx *ctx);
+
+/* Build the plan for the current batch (Fig. 1 view generation and multi-output
+ * layers): join tree (GYO, LMFAO_ERR_CYCLIC when there is none), per-query roots,
+ * directional views and their merging, view groups; then the physical plan: the root
+ * relation reorganised as a trie ordered by its segment key, view layouts, kernel
+ * sequence. opts may be NULL (heuristic FP32). info may be NULL. May launch device
+ * work (reorganisation, autotuning) on the context's internal stream and waits for it. */
+LMFAO_API int lmfao_plan(struct lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *info);
+
+/* Evaluate the planned batch asynchronously on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream). All work (view kernels, root pass, contraction,
+ * finalisation) is enqueued on that stream; device-side failures are latched and
+ * reported by the next lmfao_fetch. */
+LMFAO_API int lmfao_run(struct lmfao_ctx *ctx, void *stream);
+
+/* Results of query `query_id` from the last lmfao_run: waits for that run's stream,
+ * copies the results to host memory owned by the context (valid until the next
+ * lmfao_run, lmfao_plan or lmfao_destroy) and fills *out. */
+LMFAO_API int lmfao_fetch(struct lmfao_ctx *ctx, int query_id, lmfao_result *out);
+
+/* Copy of the dense device result of query `query_id` into caller memory: counts
+ * (int64, one per dense group cell) and sums (double, cells x naggs), where the dense
+ * cells enumerate the group-by domains in mixed radix (first attribute most
+ * significant). `counts`/`sums` are device pointers (either may be NULL), filled
+ * asynchronously on `stream` after the last lmfao_run. *ncells receives the number of
+ * cells (may be queried with both pointers NULL). */
+LMFAO_API int lmfao_result_device(struct lmfao_ctx *ctx, int query_id, int64_t *counts, double *sums,
+                        int64_t *ncells, void *stream);
+
+/* Text (JSON) description of the current plan into buf (at most len bytes, NUL-
+ * terminated); *needed receives the full length + 1. The logical part lists the join
+ * tree, the root of every query, the directional views V_{u->v} after merging and the
+ * view groups with their dependencies (Fig. 2); the physical part lists the kernels. */
+LMFAO_API int lmfao_describe_plan(struct lmfao_ctx *ctx, char *buf, size_t len, size_t *needed);
+
+/* CART split variances (Section 3, decision trees) of bucketed queries, in FP64 on the
+ * device: each query q in qids (host array of n ids) must have exactly one BUCKET
+ * group-by with B = nthresholds + 1 buckets and aggregates (COUNT, SUM(y), SUM(y^2)).
+ * For every threshold k < B - 1 the left fragment is buckets 0..k and the right the
+ * rest; VARIANCE(T) = SUM(y^2) - SUM(y)^2 / |T| (0 if T is empty). `out` (device,
+ * n x (B-1) x 2 doubles: left, right) is written asynchronously on `stream`. */
+LMFAO_API int lmfao_cart_variances(struct lmfao_ctx *ctx, const int *qids, int n, double *out, void *stream);
+
+/* Timings of the last lmfao_run measured with CUDA events around each kernel (host
+ * array of at most cap doubles, milliseconds, in launch order; names via
+ * lmfao_kernel_name). Waits for the run's stream. *n receives the number of kernels. */
+LMFAO_API int lmfao_kernel_times(struct lmfao_ctx *ctx, double *ms, int cap, int *n);
+LMFAO_API const char *lmfao_kernel_name(struct lmfao_ctx *ctx, int i);
+
+/* Turn per-kernel event timing of lmfao_run on (1) or off (0, default). */
+LMFAO_API int lmfao_set_profiling(struct lmfao_ctx *ctx, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMFAO_H */

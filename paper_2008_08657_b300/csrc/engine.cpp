@@ -1,0 +1,1667 @@
+// Host side of the engine: the C ABI of include/lmfao.h, the planner (join tree, view
+// generation, multi-output plan) and the executor that enqueues the kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <sstream>
+
+#include "plan.h"
+
+using namespace lmfao;
+
+struct lmfao_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // internal stream for loading and planning
+  std::string last_error;
+  std::vector<Relation> rels;
+  std::vector<QueryIn> queries;
+  JoinTree tree;
+  LogicalPlan logical;
+  PhysPlan *plan = nullptr;
+  bool planned = false, ran = false;
+  cudaStream_t run_stream = nullptr;
+  // fetch buffers
+  std::vector<int32_t> fk;
+  std::vector<int64_t> fc;
+  std::vector<double> fs;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<std::string> ev_names;
+  std::vector<std::string> kernel_names;
+};
+
+namespace lmfao {
+
+void *DeviceArena::alloc(size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(LMFAO_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  ptrs.push_back(p);
+  return p;
+}
+
+template <typename T>
+T *DeviceArena::upload(const std::vector<T> &v, cudaStream_t s) {
+  T *p = (T *)alloc(v.size() * sizeof(T));
+  if (!v.empty()) LMFAO_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return p;
+}
+
+void DeviceArena::release() {
+  for (void *p : ptrs) cudaFree(p);
+  ptrs.clear();
+}
+
+}  // namespace lmfao
+
+namespace {
+
+int fail(lmfao_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(lmfao_ctx *ctx, F &&f) {
+  if (!ctx) return LMFAO_ERR_ARG;
+  try {
+    ctx->last_error.clear();
+    if (ctx->device >= 0) cudaSetDevice(ctx->device);
+    return f();
+  } catch (const Error &e) {
+    return fail(ctx, e.code, e.what());
+  } catch (const std::exception &e) {
+    return fail(ctx, LMFAO_ERR_ARG, e.what());
+  }
+}
+
+void drop_plan(lmfao_ctx *ctx) {
+  if (ctx->plan && ctx->device >= 0) {
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->run_stream) cudaStreamSynchronize(ctx->run_stream);
+    ctx->plan->arena.release();
+    delete ctx->plan;
+    ctx->plan = nullptr;
+  }
+  ctx->planned = ctx->ran = false;
+}
+
+// ------------------------------------------------------------------ join tree (GYO)
+std::vector<std::string> shared_attrs(const lmfao_ctx *ctx, int a, int b) {
+  std::vector<std::string> out;
+  for (const Column &c : ctx->rels[a].cols)
+    if (ctx->rels[b].col(c.attr) >= 0) out.push_back(c.attr);
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+// Parent links of a join tree by GYO ear removal: a relation whose attributes shared with
+// the remaining relations all lie in one other remaining relation is an ear and hangs
+// below it (the largest such relation). LMFAO_ERR_CYCLIC if the reduction stalls.
+std::vector<int> gyo(const lmfao_ctx *ctx) {
+  int n = (int)ctx->rels.size();
+  std::vector<int> parent(n, -1);
+  std::vector<bool> active(n, true);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctx->rels[a].nrows < ctx->rels[b].nrows; });
+  int left = n;
+  while (left > 1) {
+    bool found = false;
+    for (int e : order) {
+      if (!active[e]) continue;
+      std::vector<std::string> sh;
+      for (const Column &c : ctx->rels[e].cols) {
+        for (int f = 0; f < n; ++f)
+          if (f != e && active[f] && ctx->rels[f].col(c.attr) >= 0) { sh.push_back(c.attr); break; }
+      }
+      int best = -1;
+      for (int f = 0; f < n; ++f) {
+        if (f == e || !active[f]) continue;
+        bool all = true;
+        for (auto &a : sh) all = all && ctx->rels[f].col(a) >= 0;
+        if (!all) continue;
+        if (sh.empty() && best >= 0) continue;
+        if (best < 0 || ctx->rels[f].nrows > ctx->rels[best].nrows) best = f;
+      }
+      if (best >= 0) {
+        if (sh.empty()) throw Error(LMFAO_ERR_UNSUPPORTED, "the schema is disconnected (relation " +
+                                                           ctx->rels[e].name + " shares no attribute)");
+        parent[e] = best;
+        active[e] = false;
+        --left;
+        found = true;
+        break;
+      }
+    }
+    if (!found) throw Error(LMFAO_ERR_CYCLIC, "the schema is cyclic: GYO reduction found no ear");
+  }
+  return parent;
+}
+
+JoinTree build_tree(const lmfao_ctx *ctx, const std::vector<int> &par_in, int root) {
+  int n = (int)ctx->rels.size();
+  // undirected adjacency, then re-root
+  std::vector<std::vector<int>> adj(n);
+  for (int i = 0; i < n; ++i)
+    if (par_in[i] >= 0) { adj[i].push_back(par_in[i]); adj[par_in[i]].push_back(i); }
+  JoinTree t;
+  t.root = root;
+  t.parent.assign(n, -1);
+  t.children.assign(n, {});
+  t.depth.assign(n, 0);
+  std::vector<int> bfs{root};
+  std::vector<bool> seen(n, false);
+  seen[root] = true;
+  for (size_t i = 0; i < bfs.size(); ++i) {
+    int u = bfs[i];
+    for (int v : adj[u])
+      if (!seen[v]) {
+        seen[v] = true;
+        t.parent[v] = u;
+        t.depth[v] = t.depth[u] + 1;
+        t.children[u].push_back(v);
+        bfs.push_back(v);
+      }
+  }
+  if ((int)bfs.size() != n) throw Error(LMFAO_ERR_ARG, "join tree does not connect all relations");
+  for (int i = n - 1; i >= 1; --i) t.post.push_back(bfs[i]);
+  // running intersection: every attribute's relations form a connected subtree
+  for (int r = 0; r < n; ++r)
+    for (const Column &c : ctx->rels[r].cols) {
+      int holders = 0, linked = 0;
+      for (int s = 0; s < n; ++s)
+        if (ctx->rels[s].col(c.attr) >= 0) {
+          ++holders;
+          if (t.parent[s] >= 0 && ctx->rels[t.parent[s]].col(c.attr) >= 0) ++linked;
+        }
+      if (holders - linked != 1)
+        throw Error(LMFAO_ERR_ARG, "join tree violates the running intersection property on attribute " + c.attr);
+    }
+  return t;
+}
+
+// relation holding attribute a that is closest to the root of tree t (ties: lowest id)
+int home_of(const lmfao_ctx *ctx, const JoinTree &t, const std::string &a) {
+  int best = -1;
+  for (int r = 0; r < (int)ctx->rels.size(); ++r)
+    if (ctx->rels[r].col(a) >= 0 && (best < 0 || t.depth[r] < t.depth[best])) best = r;
+  if (best < 0) throw Error(LMFAO_ERR_ARG, "unknown attribute " + a);
+  return best;
+}
+
+// ------------------------------------------------------------------ logical plan (Section 2)
+std::string term_name(const std::vector<FactorIn> &fs) {
+  if (fs.empty()) return "1";
+  std::vector<std::string> v;
+  for (auto &f : fs) v.push_back(f.fn == LMFAO_FN_POW ? f.attr + "^" + std::to_string(f.param) : f.attr);
+  std::sort(v.begin(), v.end());
+  std::string s;
+  for (auto &x : v) s += (s.empty() ? "" : "*") + x;
+  return s;
+}
+
+LogicalPlan build_logical(const lmfao_ctx *ctx, const JoinTree &t, const int32_t *qroot) {
+  int n = (int)ctx->rels.size();
+  LogicalPlan L;
+  std::vector<std::vector<int>> adj(n);
+  for (int i = 0; i < n; ++i)
+    if (t.parent[i] >= 0) { adj[i].push_back(t.parent[i]); adj[t.parent[i]].push_back(i); }
+  std::map<std::tuple<int, int, std::vector<std::string>>, int> vmap;
+  // per query: views toward its root
+  for (int q = 0; q < (int)ctx->queries.size(); ++q) {
+    const QueryIn &Q = ctx->queries[q];
+    int rho = (qroot && qroot[q] >= 0) ? qroot[q] : -1;
+    if (rho >= n) throw Error(LMFAO_ERR_ARG, "query root out of range");
+    if (rho < 0) {  // heuristic: the relation holding the group-by attribute with the largest domain
+      int64_t bestdom = -1;
+      for (auto &g : Q.gb) {
+        int h = home_of(ctx, t, g.attr);
+        const Column &c = ctx->rels[h].cols[ctx->rels[h].col(g.attr)];
+        int64_t dom = g.kind == LMFAO_GB_BUCKET ? (int64_t)g.thr.size() + 1 : c.domain;
+        if (dom > bestdom) { bestdom = dom; rho = h; }
+      }
+      if (rho < 0) rho = t.root;
+    }
+    L.query_root.push_back(rho);
+    // orient the tree toward rho
+    std::vector<int> par(n, -1), bfs{rho};
+    std::vector<bool> seen(n, false);
+    seen[rho] = true;
+    for (size_t i = 0; i < bfs.size(); ++i)
+      for (int v : adj[bfs[i]])
+        if (!seen[v]) { seen[v] = true; par[v] = bfs[i]; bfs.push_back(v); }
+    std::vector<std::vector<int>> sub(n);  // subtree of u toward rho
+    for (int i = n - 1; i >= 0; --i) {
+      int u = bfs[i];
+      sub[u].push_back(u);
+      if (par[u] >= 0) sub[par[u]].insert(sub[par[u]].end(), sub[u].begin(), sub[u].end());
+    }
+    auto in_sub = [&](int u, const std::string &a) {
+      for (int r : sub[u]) if (ctx->rels[r].col(a) >= 0) return true;
+      return false;
+    };
+    std::vector<int> vid(n, -1);
+    for (int i = n - 1; i >= 1; --i) {  // leaves first
+      int u = bfs[i], v = par[u];
+      std::set<std::string> key;
+      for (auto &a : shared_attrs(ctx, u, v)) key.insert(a);
+      for (auto &g : Q.gb) if (in_sub(u, g.attr)) key.insert(g.attr);
+      std::vector<std::string> kv(key.begin(), key.end());
+      auto k = std::make_tuple(u, v, kv);
+      int id;
+      auto it = vmap.find(k);
+      if (it == vmap.end()) {
+        id = (int)L.views.size();
+        vmap[k] = id;
+        LogicalView lv;
+        lv.from = u; lv.to = v; lv.key = kv;
+        L.views.push_back(lv);
+      } else id = it->second;
+      vid[u] = id;
+      LogicalView &lv = L.views[id];
+      lv.queries.insert(q);
+      for (auto &agg : Q.aggs) {
+        std::vector<FactorIn> part;
+        for (auto &f : agg) if (in_sub(u, f.attr)) part.push_back(f);
+        lv.aggs.insert(term_name(part));
+      }
+      for (int w : adj[u]) if (w != v && vid[w] >= 0) lv.deps.insert(vid[w]);
+    }
+    // the query depends on the views into rho
+    (void)vid;
+  }
+  // groups by rounds: an item is computed at its node once all views it reads exist
+  int nv = (int)L.views.size(), nq = (int)ctx->queries.size();
+  std::vector<int> vgroup(nv, -1), qgroup(nq, -1);
+  std::vector<std::set<int>> qdeps(nq);
+  for (int v = 0; v < nv; ++v)
+    for (int q : L.views[v].queries)
+      if (L.views[v].to == L.query_root[q]) qdeps[q].insert(v);
+  int done = 0;
+  while (done < nv + nq) {
+    std::map<int, LogicalGroup> round;
+    for (int v = 0; v < nv; ++v) {
+      if (vgroup[v] >= 0) continue;
+      bool ok = true;
+      for (int d : L.views[v].deps) ok = ok && vgroup[d] >= 0;
+      if (ok) round[L.views[v].from].views.push_back(v);
+    }
+    for (int q = 0; q < nq; ++q) {
+      if (qgroup[q] >= 0) continue;
+      bool ok = true;
+      for (int d : qdeps[q]) ok = ok && vgroup[d] >= 0;
+      if (ok) round[L.query_root[q]].queries.push_back(q);
+    }
+    if (round.empty()) throw Error(LMFAO_ERR_ARG, "view dependencies do not resolve");
+    // number groups: views toward the leaves-to-root order, stable by node id
+    std::vector<std::pair<int, LogicalGroup>> items(round.begin(), round.end());
+    for (auto &it : items) {
+      LogicalGroup g = it.second;
+      g.node = it.first;
+      int gid = (int)L.groups.size();
+      for (int v : g.views) for (int d : L.views[v].deps) g.deps.insert(vgroup[d]);
+      for (int q : g.queries) for (int d : qdeps[q]) g.deps.insert(vgroup[d]);
+      for (int v : g.views) { vgroup[v] = gid; ++done; }
+      for (int q : g.queries) { qgroup[q] = gid; ++done; }
+      L.groups.push_back(g);
+    }
+  }
+  return L;
+}
+
+}  // namespace
+
+// ======================================================================================
+// physical planning
+// ======================================================================================
+namespace {
+
+struct Planner {
+  lmfao_ctx *ctx;
+  PhysPlan &P;
+  const JoinTree &t;
+  cudaStream_t s;
+
+  Planner(lmfao_ctx *c, PhysPlan &p, const JoinTree &tr) : ctx(c), P(p), t(tr), s(c->stream) {}
+
+  const Relation &R(int r) const { return ctx->rels[r]; }
+
+  int child_toward(int r, int h) const {  // child of r on the path to h (h in subtree(r), h != r)
+    int x = h;
+    while (t.parent[x] != r) {
+      x = t.parent[x];
+      if (x < 0) throw Error(LMFAO_ERR_ARG, "internal: relation not below");
+    }
+    return x;
+  }
+  int fac_id(const Fac &f) {
+    auto it = P.facmap.find(f);
+    if (it != P.facmap.end()) return it->second;
+    int id = (int)P.facs.size();
+    P.facs.push_back(f);
+    P.facmap[f] = id;
+    return id;
+  }
+  int gitem_id(const GroupItem &g) {
+    auto it = P.gmap.find(g);
+    if (it != P.gmap.end()) return it->second;
+    int id = (int)P.gitems.size();
+    P.gitems.push_back(g);
+    P.gmap[g] = id;
+    return id;
+  }
+
+  // ---- views
+  void init_views() {
+    int n = (int)ctx->rels.size();
+    P.views.assign(n, View{});
+    for (int r : t.post) {
+      View &v = P.views[r];
+      v.rel = r;
+      v.parent = t.parent[r];
+      for (auto &a : shared_attrs(ctx, r, v.parent)) {
+        const Column &c = R(r).cols[R(r).col(a)];
+        const Column &pc = R(v.parent).cols[R(v.parent).col(a)];
+        if (c.role != LMFAO_KEY || pc.role != LMFAO_KEY || c.dtype != LMFAO_I32)
+          throw Error(LMFAO_ERR_ARG, "join attribute " + a + " must be a KEY column in every relation");
+        if (c.domain != pc.domain)
+          throw Error(LMFAO_ERR_ARG, "join attribute " + a + " declares different domains");
+        v.keycols.push_back(R(r).col(a));
+        v.pkeycols.push_back(R(v.parent).col(a));
+        v.keydom.push_back(c.domain);
+      }
+      if ((int)v.keycols.size() > MAXK) throw Error(LMFAO_ERR_UNSUPPORTED, "join key with more than 4 attributes");
+      v.nkeys = 1;
+      for (int64_t d : v.keydom) {
+        v.nkeys *= d;
+        if (v.nkeys > (int64_t(1) << 28))
+          throw Error(LMFAO_ERR_UNSUPPORTED, "join key domain of " + R(r).name + " exceeds 2^28 cells");
+      }
+    }
+    for (int r : t.post) view_col(r, {});  // COUNT columns
+  }
+
+  int view_col(int r, const Term &term) {
+    View &v = P.views[r];
+    auto it = v.colmap.find(term);
+    if (it != v.colmap.end()) return it->second;
+    ViewCol vc;
+    std::map<int, Term> parts;
+    for (int f : term) {
+      const Fac &fc = P.facs[f];
+      if (!fc.ind) vc.integral = false;
+      if (fc.rel == r) vc.local.push_back(f);
+      else parts[child_toward(r, fc.rel)].push_back(f);
+    }
+    for (int c : t.children[r]) {
+      int cc = view_col(c, parts.count(c) ? parts[c] : Term{});
+      vc.child.push_back({c, cc});
+    }
+    View &v2 = P.views[r];  // re-fetch (recursion does not resize, but keep it explicit)
+    int id = (int)v2.cols.size();
+    v2.cols.push_back(vc);
+    v2.colmap[term] = id;
+    return id;
+  }
+
+  int view_code(int r, int gid) {
+    View &v = P.views[r];
+    auto it = v.codemap.find(gid);
+    if (it != v.codemap.end()) return it->second;
+    CodeSpec cs;
+    const GroupItem &g = P.gitems[gid];
+    if (g.rel == r) cs.group = gid;
+    else {
+      cs.child_rel = child_toward(r, g.rel);
+      cs.child_code = view_code(cs.child_rel, gid);
+    }
+    View &v2 = P.views[r];
+    int id = (int)v2.codes.size();
+    v2.codes.push_back(cs);
+    v2.codemap[gid] = id;
+    return id;
+  }
+
+  // ---- root level
+  int rowslot(int col) {
+    auto it = P.rowslot.find(col);
+    if (it != P.rowslot.end()) return it->second;
+    int id = (int)P.rowcols.size();
+    if (id >= MAXRC) throw Error(LMFAO_ERR_UNSUPPORTED, "more than 24 root columns read per tuple");
+    P.rowcols.push_back(col);
+    P.rowslot[col] = id;
+    return id;
+  }
+  int mono_id(std::vector<int> fs) {
+    std::sort(fs.begin(), fs.end());
+    auto it = P.monomap.find(fs);
+    if (it != P.monomap.end()) return it->second;
+    int id = (int)P.monos.size();
+    P.monos.push_back(fs);
+    P.monomap[fs] = id;
+    return id;
+  }
+  int rt_id(int mono, const std::vector<std::pair<int, int>> &parts, bool integral) {
+    auto k = std::make_pair(mono * 2 + (integral ? 1 : 0), parts);
+    auto it = P.rtmap.find(k);
+    if (it != P.rtmap.end()) return it->second;
+    int id = (int)P.rts.size();
+    P.rts.push_back({mono, parts, integral});
+    P.rtmap[k] = id;
+    return id;
+  }
+  int psi_id(std::vector<int> segf, const std::vector<std::pair<int, int>> &parts, bool integral) {
+    std::sort(segf.begin(), segf.end());
+    std::vector<int> key = segf;
+    key.push_back(integral ? -2 : -1);
+    auto k = std::make_pair(key, parts);
+    auto it = P.psimap.find(k);
+    if (it != P.psimap.end()) return it->second;
+    int id = (int)P.psis.size();
+    P.psis.push_back({segf, parts, integral});
+    P.psimap[k] = id;
+    return id;
+  }
+
+  int seg_digit_of(int col) const {
+    for (size_t i = 0; i < P.segcols.size(); ++i) if (P.segcols[i] == col) return (int)i;
+    return -1;
+  }
+
+  void choose_segments(const lmfao_plan_opts &o) {
+    int root = t.root;
+    int seg = -1;
+    if (o.planner == LMFAO_PLAN_FORCED && o.segment_rel != -2) {
+      seg = o.segment_rel;
+      if (seg >= 0 && t.parent[seg] != root)
+        throw Error(LMFAO_ERR_ARG, "segment relation must be a child of the root relation");
+    } else {
+      int64_t best = 0;
+      int64_t cap = std::max<int64_t>(1, R(root).nrows / 4);
+      for (int c : t.children[root]) {
+        const View &v = P.views[c];
+        if (v.nkeys > best && v.nkeys <= cap && v.nkeys <= (int64_t(1) << 26)) { best = v.nkeys; seg = c; }
+      }
+    }
+    P.segrel = seg;
+    P.nseg = 1;
+    if (seg >= 0) {
+      const View &v = P.views[seg];
+      P.segcols = v.pkeycols;
+      P.segdom = v.keydom;
+      for (int64_t d : P.segdom) P.nseg *= d;
+      if (P.segcols.size() > 8) throw Error(LMFAO_ERR_UNSUPPORTED, "segment key with more than 8 attributes");
+    }
+    P.kind.assign(ctx->rels.size(), 0);
+    P.branch.assign(ctx->rels.size(), -1);
+    for (int c : t.children[root]) {
+      bool outer = seg >= 0;
+      for (int pc : P.views[c].pkeycols) outer = outer && seg_digit_of(pc) >= 0;
+      (outer ? P.outer : P.inner).push_back(c);
+    }
+    if (P.outer.size() > MAXOUT || P.inner.size() > MAXIN)
+      throw Error(LMFAO_ERR_UNSUPPORTED, "too many children of the root relation");
+    for (int r = 0; r < (int)ctx->rels.size(); ++r) {
+      if (r == root) continue;
+      int b = r;
+      while (t.parent[b] != root) b = t.parent[b];
+      P.branch[r] = b;
+      P.kind[r] = std::find(P.outer.begin(), P.outer.end(), b) != P.outer.end() ? 1 : 2;
+    }
+  }
+
+  int outer_idx(int c) const { return (int)(std::find(P.outer.begin(), P.outer.end(), c) - P.outer.begin()); }
+  int inner_idx(int c) const { return (int)(std::find(P.inner.begin(), P.inner.end(), c) - P.inner.begin()); }
+
+  Fac make_fac(const std::string &attr, bool ind, int pow, int op, float tv) {
+    int h = home_of(ctx, t, attr);
+    Fac f;
+    f.rel = h;
+    f.col = R(h).col(attr);
+    f.ind = ind ? 1 : 0;
+    f.pow = ind ? 1 : pow;
+    f.op = ind ? op : 0;
+    f.t = ind ? tv : 0.f;
+    return f;
+  }
+
+  DGroupRef group_ref(int gid, int64_t stride) {
+    const GroupItem &g = P.gitems[gid];
+    DGroupRef r{};
+    r.stride = stride;
+    r.kind = g.kind;
+    r.thr0 = (int)P.thr.size();
+    r.nthr = (int)g.thr.size();
+    P.thr.insert(P.thr.end(), g.thr.begin(), g.thr.end());
+    if (g.rel == t.root) {
+      int d = seg_digit_of(g.col);
+      if (d >= 0 && g.kind == LMFAO_GB_VALUE) { r.src = 0; r.a = d; }
+      else { r.src = 2; r.a = rowslot(g.col); }
+    } else {
+      int b = P.branch[g.rel];
+      int code = view_code(b, gid);
+      if (P.kind[g.rel] == 1) { r.src = 1; r.a = outer_idx(b); r.b = code; }
+      else { r.src = 3; r.a = inner_idx(b); r.b = code; }
+    }
+    return r;
+  }
+
+  void build_items(int mode) {
+    int root = t.root;
+    int64_t fo = 0, io = 0;
+    for (int q = 0; q < (int)ctx->queries.size(); ++q) {
+      const QueryIn &Q = ctx->queries[q];
+      QueryOut qo;
+      qo.naggs = (int)Q.aggs.size();
+      if ((int)Q.gb.size() > MAXGR) throw Error(LMFAO_ERR_UNSUPPORTED, "more than 4 group-by attributes");
+      for (auto &g : Q.gb) {
+        int h = home_of(ctx, t, g.attr);
+        const Column &c = R(h).cols[R(h).col(g.attr)];
+        GroupItem gi;
+        gi.rel = h;
+        gi.col = R(h).col(g.attr);
+        gi.kind = g.kind;
+        if (g.kind == LMFAO_GB_VALUE) {
+          if (c.role == LMFAO_CONT) throw Error(LMFAO_ERR_ARG, "VALUE group-by on continuous attribute " + g.attr);
+          gi.dom = c.domain;
+        } else {
+          gi.thr = g.thr;
+          gi.dom = (int64_t)g.thr.size() + 1;
+        }
+        qo.gitems.push_back(gitem_id(gi));
+        qo.dom.push_back(gi.dom);
+        qo.cells *= gi.dom;
+        if (qo.cells > (int64_t(1) << 28)) throw Error(LMFAO_ERR_UNSUPPORTED, "group-by domain exceeds 2^28 cells");
+      }
+      qo.fo = fo;
+      qo.io = io;
+      fo += qo.cells * qo.naggs;
+      io += qo.cells * (1 + qo.naggs);
+      std::vector<int64_t> stride(qo.dom.size(), 1);
+      for (int i = (int)qo.dom.size() - 2; i >= 0; --i) stride[i] = stride[i + 1] * qo.dom[i + 1];
+      std::vector<int> inds;
+      for (auto &p : Q.filters) inds.push_back(fac_id(make_fac(p.attr, true, 1, p.op, p.t)));
+      for (int a = -1; a < qo.naggs; ++a) {
+        Term term = inds;
+        bool integral = true;
+        if (a >= 0)
+          for (auto &f : Q.aggs[a]) {
+            if (f.fn == LMFAO_FN_POW && f.param < 1) throw Error(LMFAO_ERR_ARG, "POW exponent must be >= 1");
+            term.push_back(fac_id(make_fac(f.attr, false, f.fn == LMFAO_FN_POW ? f.param : 1, 0, 0.f)));
+            integral = false;
+          }
+        if (a >= 0) qo.integral.push_back(integral ? 1 : 0);
+        std::sort(term.begin(), term.end());
+        // split the product by where its factors live
+        std::vector<int> segf, rowf;
+        std::map<int, Term> bparts;
+        for (int f : term) {
+          const Fac &fc = P.facs[f];
+          if (fc.rel == root) {
+            int d = seg_digit_of(fc.col);
+            if (d >= 0) segf.push_back(f);
+            else { rowslot(fc.col); rowf.push_back(f); }
+          } else bparts[P.branch[fc.rel]].push_back(f);
+        }
+        std::vector<std::pair<int, int>> opart, ipart;
+        for (int c : P.outer) {
+          int col = view_col(c, bparts.count(c) ? bparts[c] : Term{});
+          opart.push_back({outer_idx(c), col});
+        }
+        for (int c : P.inner) {
+          int col = view_col(c, bparts.count(c) ? bparts[c] : Term{});
+          ipart.push_back({inner_idx(c), col});  // float col; integral cols remapped later
+        }
+        int psi = psi_id(segf, opart, integral);
+        int rt = rt_id(mono_id(rowf), ipart, integral);
+        // groups
+        std::vector<DGroupRef> og, ig;
+        for (size_t i = 0; i < qo.gitems.size(); ++i) {
+          DGroupRef g = group_ref(qo.gitems[i], stride[i]);
+          (g.src <= 1 ? og : ig).push_back(g);
+        }
+        int64_t out = integral ? qo.io + 1 + a : qo.fo + a;
+        int64_t cellmul = integral ? 1 + qo.naggs : qo.naggs;
+        bool b0 = ig.empty() && mode != LMFAO_MODE_PER_TUPLE;
+        if (b0) {
+          auto &lst = integral ? P.b0i : P.b0f;
+          int pos = (int)(std::find(lst.begin(), lst.end(), rt) - lst.begin());
+          int cap = integral ? NI0_MAX : NB0_MAX;
+          if (pos == (int)lst.size()) {
+            if ((int)lst.size() >= cap) b0 = false;
+            else lst.push_back(rt);
+          }
+          if (b0) {
+            DCombItem it{};
+            it.psi = psi;
+            it.block = -1;
+            it.col = pos;
+            it.integral = integral;
+            it.og0 = (int)P.grefs.size();
+            it.nog = (int)og.size();
+            P.grefs.insert(P.grefs.end(), og.begin(), og.end());
+            it.out = out;
+            it.cellmul = cellmul;
+            P.comb.push_back(it);
+          }
+        }
+        if (!b0) {
+          DB2Item it{};
+          it.psi = psi;
+          it.rterm = rt;
+          it.integral = integral;
+          it.og0 = (int)P.grefs.size();
+          it.nog = (int)og.size();
+          P.grefs.insert(P.grefs.end(), og.begin(), og.end());
+          it.ig0 = (int)P.grefs.size();
+          it.nig = (int)ig.size();
+          P.grefs.insert(P.grefs.end(), ig.begin(), ig.end());
+          it.out = out;
+          it.cellmul = cellmul;
+          P.b2.push_back(it);
+        }
+      }
+      P.qout.push_back(qo);
+    }
+    P.nfsum = fo;
+    P.nicnt = io;
+  }
+};
+
+}  // namespace
+
+// ======================================================================================
+// device-side setup of a plan
+// ======================================================================================
+namespace {
+
+DViewRef view_ref(const View &v) {
+  DViewRef r{};
+  r.v64 = v.v64;
+  r.v32 = v.v32;
+  r.vint = v.vint;
+  r.codes = v.vcodes;
+  r.ncols = (int)v.cols.size();
+  r.nint = v.nint;
+  r.ncodes = (int)v.codes.size();
+  r.nk = (int)v.keycols.size();
+  int64_t st = 1;
+  for (int i = r.nk - 1; i >= 0; --i) { r.kstride[i] = st; st *= v.keydom[i]; }
+  return r;
+}
+
+DCol dcol(const Column &c) { return DCol{c.dev, c.dtype}; }
+
+void setup_views(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, bool need32) {
+  cudaStream_t s = ctx->stream;
+  for (int r : t.post) {
+    View &v = P.views[r];
+    // integral column map
+    v.intcol.assign(v.cols.size(), -1);
+    std::vector<int> ic;
+    for (size_t j = 0; j < v.cols.size(); ++j)
+      if (v.cols[j].integral) { v.intcol[j] = (int)ic.size(); ic.push_back((int)j); }
+    v.nint = (int)ic.size();
+    size_t ncols = v.cols.size();
+    v.v64 = (double *)P.arena.alloc(v.nkeys * ncols * 8);
+    if (need32) v.v32 = (float *)P.arena.alloc(v.nkeys * ncols * 4);
+    v.vint = (uint32_t *)P.arena.alloc(v.nkeys * std::max<size_t>(1, ic.size()) * 4);
+    v.vcodes = (int32_t *)P.arena.alloc(v.nkeys * std::max<size_t>(1, v.codes.size()) * 4);
+    int *icd = P.arena.upload(ic, s);
+    // unique keys?
+    {
+      std::vector<DCol> kc;
+      std::vector<int64_t> st(v.keycols.size());
+      int64_t acc = 1;
+      for (int i = (int)v.keycols.size() - 1; i >= 0; --i) { st[i] = acc; acc *= v.keydom[i]; }
+      for (int c : v.keycols) kc.push_back(dcol(ctx->rels[r].cols[c]));
+      unsigned int *hist = (unsigned int *)P.arena.alloc(v.nkeys * 4);
+      unsigned int *mx = (unsigned int *)P.arena.alloc(4);
+      int64_t *std_ = P.arena.upload(st, s);
+      LMFAO_CUDA(cudaMemsetAsync(hist, 0, v.nkeys * 4, s));
+      LMFAO_CUDA(cudaMemsetAsync(mx, 0, 4, s));
+      launch_key_multiplicity(kc.data(), (int)kc.size(), std_, ctx->rels[r].nrows, hist, s);
+      launch_max_u32(hist, v.nkeys, mx, s);
+      unsigned int h = 0;
+      LMFAO_CUDA(cudaMemcpyAsync(&h, mx, 4, cudaMemcpyDeviceToHost, s));
+      LMFAO_CUDA(cudaStreamSynchronize(s));
+      v.unique_keys = h <= 1;
+    }
+    // kernel descriptor
+    DViewKernel d{};
+    const Relation &Rr = ctx->rels[r];
+    d.nrows = Rr.nrows;
+    std::map<int, int> slot;
+    auto sl = [&](int col) {
+      auto it = slot.find(col);
+      if (it != slot.end()) return it->second;
+      int id = (int)slot.size();
+      if (id >= MAXRC) throw Error(LMFAO_ERR_UNSUPPORTED, "view kernel reads more than 24 columns");
+      slot[col] = id;
+      d.in[id] = dcol(Rr.cols[col]);
+      return id;
+    };
+    d.nk = (int)v.keycols.size();
+    {
+      int64_t st = 1;
+      for (int i = d.nk - 1; i >= 0; --i) { d.kstride[i] = st; st *= v.keydom[i]; }
+      for (int i = 0; i < d.nk; ++i) d.kcol[i] = sl(v.keycols[i]);
+    }
+    d.nchild = (int)t.children[r].size();
+    if (d.nchild > MAXCH) throw Error(LMFAO_ERR_UNSUPPORTED, "relation with more than 8 children");
+    for (int ci = 0; ci < d.nchild; ++ci) {
+      const View &cv = P.views[t.children[r][ci]];
+      d.child[ci] = view_ref(cv);
+      for (int i = 0; i < d.child[ci].nk; ++i) d.child[ci].kcol[i] = sl(cv.pkeycols[i]);
+    }
+    std::vector<int> cfo{0}, cpo{0};
+    std::vector<DFac> facs;
+    std::vector<int2> parts;
+    for (auto &vc : v.cols) {
+      for (int f : vc.local) {
+        const Fac &fc = P.facs[f];
+        facs.push_back(DFac{sl(fc.col), fc.ind, fc.pow, fc.op, fc.t});
+      }
+      cfo.push_back((int)facs.size());
+      for (auto &pc : vc.child) {
+        int ci = (int)(std::find(t.children[r].begin(), t.children[r].end(), pc.first) - t.children[r].begin());
+        parts.push_back(make_int2(ci, pc.second));
+      }
+      cpo.push_back((int)parts.size());
+    }
+    std::vector<int4> cdesc;
+    std::vector<int2> cchild;
+    std::vector<float> thr;
+    for (auto &cs : v.codes) {
+      if (cs.group >= 0) {
+        const GroupItem &g = P.gitems[cs.group];
+        cdesc.push_back(make_int4(sl(g.col), g.kind, (int)thr.size(), (int)g.thr.size()));
+        thr.insert(thr.end(), g.thr.begin(), g.thr.end());
+        cchild.push_back(make_int2(0, 0));
+      } else {
+        int ci = (int)(std::find(t.children[r].begin(), t.children[r].end(), cs.child_rel) - t.children[r].begin());
+        cdesc.push_back(make_int4(-1, 0, 0, 0));
+        cchild.push_back(make_int2(ci, cs.child_code));
+      }
+    }
+    d.ncolsin = (int)slot.size();
+    d.v64 = v.v64;
+    d.codes = v.vcodes;
+    d.ncols = (int)v.cols.size();
+    d.ncodes = (int)v.codes.size();
+    d.unique = v.unique_keys ? 1 : 0;
+    d.col_fac_off = P.arena.upload(cfo, s);
+    d.facs = P.arena.upload(facs, s);
+    d.col_part_off = P.arena.upload(cpo, s);
+    d.parts = P.arena.upload(parts, s);
+    d.code_desc = P.arena.upload(cdesc, s);
+    d.code_child = P.arena.upload(cchild, s);
+    d.thr = P.arena.upload(thr, s);
+    d.err = P.err;
+    P.vk.push_back(d);
+    P.vk_rel.push_back(r);
+    v.intcols_dev = icd;
+    P.kernel_names.push_back("view:" + Rr.name);
+  }
+}
+
+}  // namespace
+
+// ======================================================================================
+// root relation: reorganisation into segments, fact pass and combine descriptors
+// ======================================================================================
+namespace {
+
+constexpr int64_t WORK_CHUNK = 4096;  // tuples per work item (segments longer than this split)
+
+void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
+  cudaStream_t s = ctx->stream;
+  const Relation &F = ctx->rels[t.root];
+  const int64_t n = F.nrows;
+  // reorganised copies of the root columns read per tuple
+  std::vector<int64_t> hist(P.nseg, 0);
+  P.rowdev.clear();
+  if (P.segrel >= 0 && n > 0) {
+    std::vector<DCol> kc;
+    std::vector<int64_t> radix(P.segcols.size());
+    int64_t acc = 1;
+    for (int i = (int)P.segcols.size() - 1; i >= 0; --i) { radix[i] = acc; acc *= P.segdom[i]; }
+    for (int c : P.segcols) kc.push_back(dcol(F.cols[c]));
+    int *segid = (int *)P.arena.alloc(n * 4);
+    unsigned int *h = (unsigned int *)P.arena.alloc(P.nseg * 4);
+    LMFAO_CUDA(cudaMemsetAsync(h, 0, P.nseg * 4, s));
+    if (kc.size() > 4) throw Error(LMFAO_ERR_UNSUPPORTED, "segment key with more than 4 attributes");
+    launch_segment_ids(kc.data(), (int)kc.size(), radix.data(), n, segid, s);
+    launch_histogram(segid, n, h, s);
+    std::vector<unsigned int> hh(P.nseg);
+    LMFAO_CUDA(cudaMemcpyAsync(hh.data(), h, P.nseg * 4, cudaMemcpyDeviceToHost, s));
+    LMFAO_CUDA(cudaStreamSynchronize(s));
+    std::vector<unsigned long long> begin(P.nseg);
+    unsigned long long run = 0;
+    for (int64_t i = 0; i < P.nseg; ++i) { begin[i] = run; run += hh[i]; hist[i] = hh[i]; }
+    unsigned long long *cursor = P.arena.upload(begin, s);
+    std::vector<DCol> in, out;
+    std::vector<int> esz;
+    for (int c : P.rowcols) {
+      const Column &col = F.cols[c];
+      int e = col.dtype == LMFAO_U8 ? 1 : 4;
+      void *p = P.arena.alloc(n * e);
+      in.push_back(dcol(col));
+      out.push_back(DCol{p, col.dtype});
+      esz.push_back(e);
+    }
+    if (!in.empty()) launch_scatter_rows(segid, n, cursor, in.data(), out.data(), esz.data(), (int)in.size(), s);
+    P.rowdev = out;
+    LMFAO_CUDA(cudaStreamSynchronize(s));
+    cudaFree(segid);
+    P.arena.ptrs.erase(std::find(P.arena.ptrs.begin(), P.arena.ptrs.end(), (void *)segid));
+  } else {
+    hist[0] = n;
+    for (int c : P.rowcols) P.rowdev.push_back(dcol(F.cols[c]));
+  }
+  // work items: each segment in chunks of at most WORK_CHUNK tuples
+  std::vector<DWork> work;
+  long long r0 = 0;
+  for (int64_t sidx = 0; sidx < P.nseg; ++sidx) {
+    int64_t len = hist[sidx];
+    for (int64_t o = 0; o < len; o += WORK_CHUNK)
+      work.push_back(DWork{r0 + o, (int)sidx, (int)std::min<int64_t>(WORK_CHUNK, len - o)});
+    r0 += len;
+  }
+  P.nwork = (int64_t)work.size();
+  P.work = P.arena.upload(work, s);
+}
+
+void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
+  cudaStream_t s = ctx->stream;
+  // outputs and per-segment sums
+  P.fsum = (double *)P.arena.alloc(std::max<int64_t>(1, P.nfsum) * 8);
+  P.icnt = (unsigned long long *)P.arena.alloc(std::max<int64_t>(1, P.nicnt) * 8);
+  size_t ts = P.fp64 ? 8 : 4;
+  P.phi0f = P.arena.alloc(std::max<size_t>(1, P.nseg * P.b0f.size()) * ts);
+  P.phi0i = (unsigned long long *)P.arena.alloc(std::max<size_t>(1, P.nseg * P.b0i.size()) * 8);
+  P.wseg = (unsigned long long *)P.arena.alloc(P.nseg * 8);
+  // segment decoding and outer view refs
+  DSegment sg{};
+  sg.ndig = (int)P.segcols.size();
+  {
+    int64_t acc = 1;
+    for (int i = sg.ndig - 1; i >= 0; --i) { sg.radix[i] = acc; sg.dom[i] = P.segdom[i]; acc *= P.segdom[i]; }
+  }
+  std::vector<DOuter> outer;
+  for (int c : P.outer) {
+    const View &v = P.views[c];
+    DOuter o{};
+    o.v = view_ref(v);
+    for (int d = 0; d < sg.ndig; ++d) {
+      o.dstride[d] = 0;
+      for (size_t i = 0; i < v.pkeycols.size(); ++i)
+        if (v.pkeycols[i] == P.segcols[d]) o.dstride[d] = o.v.kstride[i];
+    }
+    outer.push_back(o);
+  }
+  // psi tables
+  std::vector<DPsi> psi;
+  std::vector<DSegFac> segfacs;
+  std::vector<DPart> pparts;
+  for (auto &p : P.psis) {
+    DPsi d{};
+    d.f0 = (int)segfacs.size();
+    for (int f : p.segf) {
+      const Fac &fc = P.facs[f];
+      int dg = 0;
+      for (size_t i = 0; i < P.segcols.size(); ++i) if (P.segcols[i] == fc.col) dg = (int)i;
+      segfacs.push_back(DSegFac{dg, fc.pow, fc.ind, fc.op, fc.t});
+    }
+    d.nf = (int)p.segf.size();
+    d.p0 = (int)pparts.size();
+    for (auto &pp : p.parts) {
+      const View &v = P.views[P.outer[pp.first]];
+      // integral psi reads the exact FP64 value of an integral column
+      pparts.push_back(DPart{pp.first, pp.second});
+      (void)v;
+    }
+    d.np = (int)p.parts.size();
+    d.integral = p.integral ? 1 : 0;
+    psi.push_back(d);
+  }
+  // row tables
+  std::vector<DMono> mono;
+  std::vector<DFac> rfacs;
+  for (auto &m : P.monos) {
+    DMono d{(int)rfacs.size(), (int)m.size()};
+    for (int f : m) {
+      const Fac &fc = P.facs[f];
+      rfacs.push_back(DFac{P.rowslot.at(fc.col), fc.ind, fc.pow, fc.op, fc.t});
+    }
+    mono.push_back(d);
+  }
+  std::vector<DRTerm> rts;
+  std::vector<DPart> rparts;
+  for (auto &r : P.rts) {
+    DRTerm d{r.mono, (int)rparts.size(), (int)r.parts.size(), r.integral ? 1 : 0};
+    for (auto &pp : r.parts) {
+      const View &v = P.views[P.inner[pp.first]];
+      int col = r.integral ? v.intcol[pp.second] : pp.second;
+      if (col < 0) throw Error(LMFAO_ERR_ARG, "internal: integral term on a non-integral view column");
+      rparts.push_back(DPart{pp.first, col});
+    }
+    rts.push_back(d);
+  }
+  std::vector<DViewRef> inner;
+  for (int c : P.inner) {
+    const View &v = P.views[c];
+    DViewRef r = view_ref(v);
+    for (int i = 0; i < r.nk; ++i) r.kcol[i] = P.rowslot.at(v.pkeycols[i]);
+    inner.push_back(r);
+  }
+  // key columns of inner branches must be row slots (registered now if not yet)
+  // segment weights
+  DSegWeight sw{};
+  sw.nseg = P.nseg;
+  sw.seg = sg;
+  sw.nouter = (int)outer.size();
+  for (size_t i = 0; i < outer.size(); ++i) sw.outer[i] = outer[i];
+  sw.wseg = P.wseg;
+  P.sw = sw;
+  // fact pass
+  DFactPass &fp = P.fp;
+  fp = DFactPass{};
+  fp.nwork = P.nwork;
+  fp.work = P.work;
+  fp.wseg = P.wseg;
+  fp.ncols = (int)P.rowdev.size();
+  for (size_t i = 0; i < P.rowdev.size(); ++i) fp.col[i] = P.rowdev[i];
+  fp.ninner = (int)inner.size();
+  for (size_t i = 0; i < inner.size(); ++i) fp.inner[i] = inner[i];
+  fp.nmono = (int)mono.size();
+  fp.mono = P.arena.upload(mono, s);
+  fp.facs = P.arena.upload(rfacs, s);
+  fp.nrt = (int)rts.size();
+  fp.rt = P.arena.upload(rts, s);
+  fp.parts = P.arena.upload(rparts, s);
+  fp.n0f = (int)P.b0f.size();
+  fp.n0i = (int)P.b0i.size();
+  fp.b0f = P.arena.upload(P.b0f, s);
+  fp.b0i = P.arena.upload(P.b0i, s);
+  fp.phi0f = P.phi0f;
+  fp.phi0i = P.phi0i;
+  fp.nb2 = (int)P.b2.size();
+  fp.b2 = P.arena.upload(P.b2, s);
+  fp.grefs = P.arena.upload(P.grefs, s);
+  fp.thr = P.arena.upload(P.thr, s);
+  fp.seg = sg;
+  fp.nouter = (int)outer.size();
+  for (size_t i = 0; i < outer.size(); ++i) fp.outer[i] = outer[i];
+  fp.npsi = (int)psi.size();
+  fp.psi = P.arena.upload(psi, s);
+  fp.segfacs = P.arena.upload(segfacs, s);
+  fp.psiparts = P.arena.upload(pparts, s);
+  fp.fsum = P.fsum;
+  fp.icnt = P.icnt;
+  fp.b2_smem_items = std::max(1, (int)P.b2.size());
+  P.nb0 = 4;
+  while (P.nb0 < (int)P.b0f.size()) P.nb0 *= 2;
+  if (P.nb0 > NB0_MAX) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: too many per-segment sums");
+  P.fp_block = 256;
+  size_t fsm = fact_pass_smem(fp, P.fp64, P.fp_block);
+  if (fsm > 200 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "per-tuple items need more shared memory than available");
+  int blocks_per_sm = 4;
+  P.fp_grid = (int)std::max<int64_t>(1, std::min<int64_t>(148 * blocks_per_sm, (P.nwork + 7) / 8));
+  // combine
+  DCombine &cb = P.cb;
+  cb = DCombine{};
+  cb.nseg = P.nseg;
+  cb.wseg = P.wseg;
+  cb.seg = sg;
+  cb.nouter = (int)outer.size();
+  for (size_t i = 0; i < outer.size(); ++i) cb.outer[i] = outer[i];
+  cb.npsi = (int)psi.size();
+  cb.psi = fp.psi;
+  cb.segfacs = fp.segfacs;
+  cb.psiparts = fp.psiparts;
+  cb.n0f = fp.n0f;
+  cb.n0i = fp.n0i;
+  cb.phi0f = P.phi0f;
+  cb.phi0i = P.phi0i;
+  cb.nitems = (int)P.comb.size();
+  cb.items = P.arena.upload(P.comb, s);
+  cb.grefs = fp.grefs;
+  cb.thr = fp.thr;
+  cb.fsum = P.fsum;
+  cb.icnt = P.icnt;
+  // mirror outputs of queries with outer-grouped items in shared memory while they fit
+  std::vector<int> item_smem(P.comb.size(), -1);
+  std::vector<DMirror> mirrors;
+  std::map<int64_t, int> fmir, imir;  // query output base -> smem offset
+  int fcells = 0, icells = 0;
+  const int budget_cells = 12 * 1024;
+  for (size_t i = 0; i < P.comb.size(); ++i) {
+    const DCombItem &it = P.comb[i];
+    if (it.nog == 0) continue;
+    // find the query owning this output
+    for (auto &q : P.qout) {
+      int64_t base = it.integral ? q.io : q.fo;
+      int64_t len = it.integral ? q.cells * (1 + q.naggs) : q.cells * q.naggs;
+      if (it.out < base || it.out >= base + len) continue;
+      auto &mp = it.integral ? imir : fmir;
+      int &cells = it.integral ? icells : fcells;
+      auto f = mp.find(base);
+      if (f == mp.end()) {
+        if (cells + len > budget_cells) break;
+        mp[base] = cells;
+        mirrors.push_back(DMirror{base, cells, (int)len, it.integral, 0});
+        f = mp.find(base);
+        cells += (int)len;
+      }
+      item_smem[i] = f->second + (int)(it.out - base);
+      break;
+    }
+  }
+  cb.item_smem = P.arena.upload(item_smem, s);
+  cb.smem_fcells = fcells;
+  cb.smem_icells = icells;
+  cb.nmirror = (int)mirrors.size();
+  cb.mirror = P.arena.upload(mirrors, s);
+  cb.tile = 32;
+  while (cb.tile > 1 && combine_smem(cb, P.fp64) > 200 * 1024) cb.tile /= 2;
+  if (combine_smem(cb, P.fp64) > 200 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "combine needs too much shared memory");
+  P.cb_smem = combine_smem(cb, P.fp64);
+  P.cb_block = 256;
+  int64_t ntiles = (P.nseg + cb.tile - 1) / cb.tile;
+  P.cb_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 2));
+  (void)t;
+}
+
+// Enqueue one evaluation of the batch on stream s.
+void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s) {
+  ctx->ev_names.clear();
+  int ev = 0;
+  auto mark = [&](const std::string &name) {
+    if (!ctx->profiling) return;
+    if ((int)ctx->events.size() <= ev) {
+      cudaEvent_t e;
+      LMFAO_CUDA(cudaEventCreate(&e));
+      ctx->events.push_back(e);
+    }
+    LMFAO_CUDA(cudaEventRecord(ctx->events[ev++], s));
+    ctx->ev_names.push_back(name);
+  };
+  mark("start");
+  LMFAO_CUDA(cudaMemsetAsync(P.err, 0, 4, s));
+  if (P.nfsum) LMFAO_CUDA(cudaMemsetAsync(P.fsum, 0, P.nfsum * 8, s));
+  if (P.nicnt) LMFAO_CUDA(cudaMemsetAsync(P.icnt, 0, P.nicnt * 8, s));
+  if (!P.b0f.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * P.b0f.size() * (P.fp64 ? 8 : 4), s));
+  if (!P.b0i.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * P.b0i.size() * 8, s));
+  mark("memset");
+  for (size_t i = 0; i < P.vk.size(); ++i) {
+    int r = P.vk_rel[i];
+    View &v = P.views[r];
+    LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
+    if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+    launch_view_kernel(P.vk[i], s);
+    launch_view_finish(v.v64, v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint, v.nkeys, P.err, s);
+    mark("view:" + ctx->rels[r].name);
+  }
+  launch_segment_weights(P.sw, s);
+  mark("segment_weights");
+  launch_fact_pass(P.fp, P.fp64, P.nb0, P.fp_grid, P.fp_block, s);
+  mark("fact_pass");
+  if (!P.comb.empty()) launch_combine(P.cb, P.fp64, P.cb_grid, P.cb_block, P.cb_smem, s);
+  mark("combine");
+  LMFAO_CUDA(cudaGetLastError());
+  (void)t;
+}
+
+// Bytes the fact pass must move per launch: the reorganised root columns it reads once,
+// the work list, the segment weights, the inner views (read once; cache-resident after)
+// and the per-segment sums it writes.
+int64_t fact_pass_bytes(const lmfao_ctx *ctx, const PhysPlan &P) {
+  const Relation &F = ctx->rels[P.root];
+  int64_t b = 0;
+  for (int c : P.rowcols) b += F.nrows * (F.cols[c].dtype == LMFAO_U8 ? 1 : 4);
+  b += P.nwork * (int64_t)sizeof(DWork) + P.nseg * 8;
+  int64_t ts = P.fp64 ? 8 : 4;
+  for (int c : P.inner) {
+    const View &v = P.views[c];
+    b += v.nkeys * ((int64_t)v.cols.size() * ts + v.nint * 4 + (int64_t)v.codes.size() * 4);
+  }
+  b += P.nseg * ((int64_t)P.b0f.size() * ts + (int64_t)P.b0i.size() * 8);
+  return b;
+}
+
+std::string json_escape(const std::string &x) {
+  std::string o;
+  for (char c : x) {
+    if (c == '"' || c == '\\') o += '\\';
+    o += c;
+  }
+  return o;
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+int lmfao_create(lmfao_ctx **out, int device) {
+  if (!out) return LMFAO_ERR_ARG;
+  *out = nullptr;
+  if (device == -1) {  // host-only context: schema, batch and logical plan, no device work
+    lmfao_ctx *ctx = new lmfao_ctx();
+    ctx->device = -1;
+    *out = ctx;
+    return LMFAO_OK;
+  }
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return LMFAO_ERR_CUDA;
+  }
+  lmfao_ctx *ctx = new lmfao_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return LMFAO_ERR_CUDA;
+  }
+  *out = ctx;
+  return LMFAO_OK;
+}
+
+int lmfao_destroy(lmfao_ctx *ctx) {
+  if (!ctx) return LMFAO_ERR_ARG;
+  if (ctx->device >= 0) cudaSetDevice(ctx->device);
+  drop_plan(ctx);
+  for (auto &R : ctx->rels)
+    for (auto &c : R.cols)
+      if (c.owned && c.dev) cudaFree(c.dev);
+  for (auto e : ctx->events) cudaEventDestroy(e);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return LMFAO_OK;
+}
+
+const char *lmfao_last_error(const lmfao_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int lmfao_load_relation(lmfao_ctx *ctx, const char *name, int64_t nrows, const lmfao_column *cols, int ncols,
+                        uint32_t flags, int *rel_id) {
+  return guarded(ctx, [&]() -> int {
+    if (!name || nrows < 0 || (ncols > 0 && !cols) || ncols <= 0 || flags > LMFAO_ADOPT_DEVICE)
+      return fail(ctx, LMFAO_ERR_ARG, "bad relation arguments");
+    if (nrows > (int64_t(1) << 31) - 1) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "relations are limited to 2^31-1 tuples");
+    for (auto &R : ctx->rels)
+      if (R.name == name) return fail(ctx, LMFAO_ERR_ARG, std::string("relation ") + name + " already loaded");
+    Relation R;
+    R.name = name;
+    R.nrows = nrows;
+    for (int i = 0; i < ncols; ++i) {
+      const lmfao_column &c = cols[i];
+      if (!c.attr || (!c.data && nrows > 0)) return fail(ctx, LMFAO_ERR_ARG, "column without name or data");
+      for (auto &o : R.cols)
+        if (o.attr == c.attr) return fail(ctx, LMFAO_ERR_ARG, std::string("duplicate attribute ") + c.attr);
+      if (c.role < LMFAO_KEY || c.role > LMFAO_CONT) return fail(ctx, LMFAO_ERR_ARG, "bad column role");
+      bool ok = (c.role == LMFAO_CONT) ? (c.dtype == LMFAO_F32 || c.dtype == LMFAO_U8) : c.dtype == LMFAO_I32;
+      if (!ok) return fail(ctx, LMFAO_ERR_DTYPE, std::string("dtype not allowed for column ") + c.attr);
+      if (c.role != LMFAO_CONT && (c.domain <= 0 || c.domain > (int64_t(1) << 31)))
+        return fail(ctx, LMFAO_ERR_ARG, std::string("column ") + c.attr + " needs a domain in [1, 2^31]");
+    }
+    if (ctx->device < 0) {  // host-only: keep the schema and cardinalities, validate keys
+      if (flags != LMFAO_HOST) return fail(ctx, LMFAO_ERR_ARG, "a host-only context takes host columns");
+      for (int i = 0; i < ncols; ++i) {
+        const lmfao_column &c = cols[i];
+        if (c.role != LMFAO_CONT) {
+          const int32_t *v = (const int32_t *)c.data;
+          for (int64_t r = 0; r < nrows; ++r)
+            if (v[r] < 0 || v[r] >= c.domain)
+              return fail(ctx, LMFAO_ERR_KEY_RANGE, std::string("value of ") + c.attr + " outside its domain");
+        }
+        Column col;
+        col.attr = c.attr;
+        col.dtype = c.dtype;
+        col.role = c.role;
+        col.domain = c.domain;
+        R.cols.push_back(col);
+      }
+      drop_plan(ctx);
+      ctx->rels.push_back(R);
+      if (rel_id) *rel_id = (int)ctx->rels.size() - 1;
+      return LMFAO_OK;
+    }
+    std::vector<void *> mine;
+    try {
+      for (int i = 0; i < ncols; ++i) {
+        const lmfao_column &c = cols[i];
+        Column col;
+        col.attr = c.attr;
+        col.dtype = c.dtype;
+        col.role = c.role;
+        col.domain = c.domain;
+        size_t esz = c.dtype == LMFAO_U8 ? 1 : 4;
+        if (c.role != LMFAO_CONT && flags == LMFAO_HOST) {
+          const int32_t *v = (const int32_t *)c.data;
+          for (int64_t r = 0; r < nrows; ++r)
+            if (v[r] < 0 || v[r] >= c.domain)
+              throw Error(LMFAO_ERR_KEY_RANGE, std::string("value ") + std::to_string(v[r]) + " of " + c.attr +
+                                                   " outside [0, " + std::to_string(c.domain) + ")");
+        }
+        if (flags == LMFAO_ADOPT_DEVICE) {
+          col.dev = const_cast<void *>(c.data);
+          col.owned = false;
+        } else {
+          LMFAO_CUDA(cudaMalloc(&col.dev, std::max<size_t>(16, nrows * esz)));
+          mine.push_back(col.dev);
+          col.owned = true;
+          if (nrows)
+            LMFAO_CUDA(cudaMemcpyAsync(col.dev, c.data, nrows * esz,
+                                       flags == LMFAO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+        }
+        if (c.role != LMFAO_CONT && flags != LMFAO_HOST && nrows) {
+          int *bad = nullptr;
+          LMFAO_CUDA(cudaMalloc(&bad, 4));
+          mine.push_back(bad);
+          LMFAO_CUDA(cudaMemsetAsync(bad, 0, 4, ctx->stream));
+          launch_range_check(col.dev, c.dtype, nrows, c.domain, bad, ctx->stream);
+          int hb = 0;
+          LMFAO_CUDA(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, ctx->stream));
+          LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+          cudaFree(bad);
+          mine.pop_back();
+          if (hb) throw Error(LMFAO_ERR_KEY_RANGE, std::string("a value of ") + c.attr + " lies outside its domain");
+        }
+        R.cols.push_back(col);
+      }
+      LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+      for (void *p : mine) cudaFree(p);
+      throw;
+    }
+    drop_plan(ctx);
+    ctx->rels.push_back(R);
+    if (rel_id) *rel_id = (int)ctx->rels.size() - 1;
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_add_batch(lmfao_ctx *ctx, const lmfao_aggregate *aggs, int naggs, const lmfao_groupby *gb, int ngb,
+                    const lmfao_predicate *filters, int nfilters, int *query_id) {
+  return guarded(ctx, [&]() -> int {
+    if (naggs < 0 || ngb < 0 || nfilters < 0 || (naggs && !aggs) || (ngb && !gb) || (nfilters && !filters))
+      return fail(ctx, LMFAO_ERR_ARG, "bad batch arguments");
+    auto find_attr = [&](const char *a) -> const Column * {
+      if (!a) return nullptr;
+      for (auto &R : ctx->rels) {
+        int c = R.col(a);
+        if (c >= 0) return &R.cols[c];
+      }
+      return nullptr;
+    };
+    QueryIn q;
+    for (int i = 0; i < naggs; ++i) {
+      std::vector<FactorIn> fs;
+      if (aggs[i].nfactors < 0 || (aggs[i].nfactors && !aggs[i].factors)) return fail(ctx, LMFAO_ERR_ARG, "bad aggregate");
+      for (int j = 0; j < aggs[i].nfactors; ++j) {
+        const lmfao_factor &f = aggs[i].factors[j];
+        if (!find_attr(f.attr)) return fail(ctx, LMFAO_ERR_ARG, std::string("unknown attribute ") + (f.attr ? f.attr : "(null)"));
+        if (f.fn != LMFAO_FN_ID && f.fn != LMFAO_FN_POW) return fail(ctx, LMFAO_ERR_ARG, "unknown factor function");
+        if (f.fn == LMFAO_FN_POW && (f.param < 1 || f.param > 16)) return fail(ctx, LMFAO_ERR_ARG, "POW exponent must be in [1, 16]");
+        fs.push_back(FactorIn{f.attr, f.fn, f.fn == LMFAO_FN_POW ? f.param : 1});
+      }
+      q.aggs.push_back(fs);
+    }
+    for (int i = 0; i < ngb; ++i) {
+      const Column *c = find_attr(gb[i].attr);
+      if (!c) return fail(ctx, LMFAO_ERR_ARG, std::string("unknown group-by attribute ") + (gb[i].attr ? gb[i].attr : "(null)"));
+      GroupIn g{gb[i].attr, gb[i].kind, {}};
+      if (g.kind == LMFAO_GB_VALUE) {
+        if (c->role == LMFAO_CONT) return fail(ctx, LMFAO_ERR_ARG, "VALUE group-by needs a KEY or CAT attribute");
+      } else if (g.kind == LMFAO_GB_BUCKET) {
+        if (gb[i].nthresholds < 0 || (gb[i].nthresholds && !gb[i].thresholds)) return fail(ctx, LMFAO_ERR_ARG, "bad thresholds");
+        g.thr.assign(gb[i].thresholds, gb[i].thresholds + gb[i].nthresholds);
+        for (size_t k = 1; k < g.thr.size(); ++k)
+          if (!(g.thr[k - 1] < g.thr[k])) return fail(ctx, LMFAO_ERR_ARG, "thresholds must be strictly ascending");
+      } else return fail(ctx, LMFAO_ERR_ARG, "unknown group-by kind");
+      for (auto &o : q.gb) if (o.attr == g.attr && o.kind == g.kind && o.thr == g.thr) return fail(ctx, LMFAO_ERR_ARG, "repeated group-by");
+      q.gb.push_back(g);
+    }
+    for (int i = 0; i < nfilters; ++i) {
+      if (!find_attr(filters[i].attr)) return fail(ctx, LMFAO_ERR_ARG, std::string("unknown filter attribute ") + (filters[i].attr ? filters[i].attr : "(null)"));
+      if (filters[i].op < LMFAO_LE || filters[i].op > LMFAO_NE) return fail(ctx, LMFAO_ERR_ARG, "unknown predicate");
+      q.filters.push_back(PredIn{filters[i].attr, filters[i].op, filters[i].t});
+    }
+    drop_plan(ctx);
+    ctx->queries.push_back(q);
+    if (query_id) *query_id = (int)ctx->queries.size() - 1;
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_clear_batch(lmfao_ctx *ctx) {
+  return guarded(ctx, [&]() -> int {
+    drop_plan(ctx);
+    ctx->queries.clear();
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *info) {
+  return guarded(ctx, [&]() -> int {
+    auto t0 = std::chrono::steady_clock::now();
+    drop_plan(ctx);
+    if (ctx->rels.empty()) return fail(ctx, LMFAO_ERR_ARG, "no relations loaded");
+    lmfao_plan_opts o{};
+    o.precision = LMFAO_FP32;
+    o.planner = LMFAO_PLAN_HEURISTIC;
+    o.root_rel = -1;
+    o.segment_rel = -2;
+    o.mode = LMFAO_MODE_AUTO;
+    if (opts) o = *opts;
+    int n = (int)ctx->rels.size();
+    std::vector<int> par;
+    if (o.join_parent) {
+      par.assign(o.join_parent, o.join_parent + n);
+      for (int p : par) if (p < -1 || p >= n) return fail(ctx, LMFAO_ERR_ARG, "join_parent out of range");
+    } else if (n == 1) {
+      par.assign(1, -1);
+    } else {
+      par = gyo(ctx);
+    }
+    int root = o.root_rel;
+    if (root < 0 || o.planner != LMFAO_PLAN_FORCED) {
+      if (root < 0 || root >= n) {
+        root = 0;
+        for (int r = 1; r < n; ++r) if (ctx->rels[r].nrows > ctx->rels[root].nrows) root = r;
+      }
+    }
+    if (root >= n) return fail(ctx, LMFAO_ERR_ARG, "root_rel out of range");
+    ctx->tree = build_tree(ctx, par, root);
+    ctx->logical = build_logical(ctx, ctx->tree, o.query_root);
+    if (ctx->device < 0) {  // host-only: the logical plan of Section 2 only
+      ctx->planned = true;
+      if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->root_rel = root;
+        info->segment_rel = -1;
+        info->n_views = (int)ctx->logical.views.size();
+        info->n_groups = (int)ctx->logical.groups.size();
+        info->predicted_ms = -1;
+      }
+      return LMFAO_OK;
+    }
+    PhysPlan *P = new PhysPlan();
+    ctx->plan = P;
+    P->fp64 = o.precision == LMFAO_FP64;
+    P->mode = o.mode == LMFAO_MODE_PER_TUPLE ? LMFAO_MODE_PER_TUPLE : LMFAO_MODE_FACTORISED;
+    P->root = root;
+    P->err = (int *)P->arena.alloc(16);
+    Planner pl(ctx, *P, ctx->tree);
+    pl.init_views();
+    pl.choose_segments(o);
+    pl.build_items(P->mode);
+    // inner branch keys are read per tuple
+    for (int c : P->inner)
+      for (int pc : P->views[c].pkeycols) pl.rowslot(pc);
+    setup_views(ctx, *P, ctx->tree, !P->fp64);
+    setup_root(ctx, *P, ctx->tree);
+    setup_passes(ctx, *P, ctx->tree);
+    LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->planned = true;
+    P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) {
+      info->root_rel = root;
+      info->segment_rel = P->segrel;
+      info->n_segments = P->nseg;
+      info->n_views = (int)ctx->logical.views.size();
+      info->n_groups = (int)ctx->logical.groups.size();
+      info->n_kernels = (int)P->vk.size() * 2 + 2 + (P->comb.empty() ? 0 : 1);
+      info->mode = P->mode;
+      info->predicted_ms = -1;
+      info->plan_ms = P->plan_ms;
+    }
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_run(lmfao_ctx *ctx, void *stream) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->planned || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "lmfao_run before lmfao_plan (or on a host-only context)");
+    cudaStream_t s = (cudaStream_t)stream;
+    enqueue_run(ctx, *ctx->plan, ctx->tree, s);
+    ctx->run_stream = s;
+    ctx->ran = true;
+    return LMFAO_OK;
+  });
+}
+
+static void check_device_flags(lmfao_ctx *ctx) {
+  int e = 0;
+  LMFAO_CUDA(cudaStreamSynchronize(ctx->run_stream));
+  LMFAO_CUDA(cudaMemcpy(&e, ctx->plan->err, 4, cudaMemcpyDeviceToHost));
+  if (e & 1)
+    throw Error(LMFAO_ERR_UNSUPPORTED,
+                "a group-by attribute of a non-root relation is not determined by that relation's join key");
+  if (e & 2) throw Error(LMFAO_ERR_UNSUPPORTED, "an exact count in a view exceeds 2^32");
+}
+
+int lmfao_fetch(lmfao_ctx *ctx, int query_id, lmfao_result *out) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->ran || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "lmfao_fetch before lmfao_run");
+    if (query_id < 0 || query_id >= (int)ctx->queries.size() || !out) return fail(ctx, LMFAO_ERR_ARG, "bad query id");
+    check_device_flags(ctx);
+    PhysPlan &P = *ctx->plan;
+    const QueryOut &q = P.qout[query_id];
+    std::vector<unsigned long long> ic(q.cells * (1 + q.naggs));
+    std::vector<double> fs(q.cells * q.naggs);
+    LMFAO_CUDA(cudaMemcpy(ic.data(), P.icnt + q.io, ic.size() * 8, cudaMemcpyDeviceToHost));
+    if (!fs.empty()) LMFAO_CUDA(cudaMemcpy(fs.data(), P.fsum + q.fo, fs.size() * 8, cudaMemcpyDeviceToHost));
+    int ng = (int)q.dom.size();
+    ctx->fk.clear();
+    ctx->fc.clear();
+    ctx->fs.clear();
+    int64_t groups = 0;
+    for (int64_t c = 0; c < q.cells; ++c) {
+      unsigned long long cnt = ic[c * (1 + q.naggs)];
+      if (ng > 0 && cnt == 0) continue;
+      ++groups;
+      int64_t rem = c;
+      std::vector<int32_t> key(ng);
+      for (int i = ng - 1; i >= 0; --i) { key[i] = (int32_t)(rem % q.dom[i]); rem /= q.dom[i]; }
+      ctx->fk.insert(ctx->fk.end(), key.begin(), key.end());
+      ctx->fc.push_back((int64_t)cnt);
+      for (int a = 0; a < q.naggs; ++a)
+        ctx->fs.push_back(q.integral[a] ? (double)ic[c * (1 + q.naggs) + 1 + a] : fs[c * q.naggs + a]);
+    }
+    out->ngroups = groups;
+    out->ngroupby = ng;
+    out->naggs = q.naggs;
+    out->group_keys = ctx->fk.data();
+    out->counts = ctx->fc.data();
+    out->sums = ctx->fs.data();
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_result_device(lmfao_ctx *ctx, int query_id, int64_t *counts, double *sums, int64_t *ncells, void *stream) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->planned || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
+    if (query_id < 0 || query_id >= (int)ctx->queries.size()) return fail(ctx, LMFAO_ERR_ARG, "bad query id");
+    PhysPlan &P = *ctx->plan;
+    const QueryOut &q = P.qout[query_id];
+    if (ncells) *ncells = q.cells;
+    if (!counts && !sums) return LMFAO_OK;
+    if (!ctx->ran) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
+    cudaStream_t s = (cudaStream_t)stream;
+    // integral flags of the query, uploaded once per plan
+    static thread_local std::map<std::pair<const void *, int>, int *> flags;
+    auto key = std::make_pair((const void *)&P, query_id);
+    int *fl;
+    auto it = flags.find(key);
+    if (it == flags.end()) {
+      fl = P.arena.upload(q.integral.empty() ? std::vector<int>{0} : q.integral, ctx->stream);
+      LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+      flags[key] = fl;
+    } else fl = it->second;
+    launch_results(P.icnt + q.io, P.fsum + q.fo, q.cells, q.naggs, fl, counts, sums, s);
+    LMFAO_CUDA(cudaGetLastError());
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->planned) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
+    std::ostringstream o;
+    const JoinTree &t = ctx->tree;
+    const LogicalPlan &L = ctx->logical;
+    auto nm = [&](int r) { return "\"" + json_escape(ctx->rels[r].name) + "\""; };
+    o << "{\"relations\":[";
+    for (size_t r = 0; r < ctx->rels.size(); ++r) o << (r ? "," : "") << nm((int)r);
+    o << "],\"join_tree\":{\"root\":" << nm(t.root) << ",\"parent\":{";
+    bool first = true;
+    for (size_t r = 0; r < ctx->rels.size(); ++r) {
+      if (t.parent[r] < 0) continue;
+      o << (first ? "" : ",") << nm((int)r) << ":" << nm(t.parent[r]);
+      first = false;
+    }
+    o << "}},\"query_roots\":[";
+    for (size_t q = 0; q < L.query_root.size(); ++q) o << (q ? "," : "") << nm(L.query_root[q]);
+    o << "],\"views\":[";
+    for (size_t v = 0; v < L.views.size(); ++v) {
+      const LogicalView &lv = L.views[v];
+      o << (v ? "," : "") << "{\"from\":" << nm(lv.from) << ",\"to\":" << nm(lv.to) << ",\"key\":[";
+      for (size_t i = 0; i < lv.key.size(); ++i) o << (i ? "," : "") << "\"" << json_escape(lv.key[i]) << "\"";
+      o << "],\"aggregates\":[";
+      size_t i = 0;
+      for (auto &a : lv.aggs) o << (i++ ? "," : "") << "\"" << json_escape(a) << "\"";
+      o << "],\"queries\":[";
+      i = 0;
+      for (int q : lv.queries) o << (i++ ? "," : "") << q;
+      o << "],\"deps\":[";
+      i = 0;
+      for (int d : lv.deps) o << (i++ ? "," : "") << d;
+      o << "]}";
+    }
+    o << "],\"groups\":[";
+    for (size_t g = 0; g < L.groups.size(); ++g) {
+      const LogicalGroup &lg = L.groups[g];
+      o << (g ? "," : "") << "{\"node\":" << nm(lg.node) << ",\"views\":[";
+      for (size_t i = 0; i < lg.views.size(); ++i) o << (i ? "," : "") << lg.views[i];
+      o << "],\"queries\":[";
+      for (size_t i = 0; i < lg.queries.size(); ++i) o << (i ? "," : "") << lg.queries[i];
+      o << "],\"deps\":[";
+      size_t i = 0;
+      for (int d : lg.deps) o << (i++ ? "," : "") << d;
+      o << "]}";
+    }
+    if (!ctx->plan) {
+      o << "],\"physical\":null}";
+      std::string str = o.str();
+      if (needed) *needed = str.size() + 1;
+      if (buf && len) {
+        size_t m = std::min(len - 1, str.size());
+        std::memcpy(buf, str.data(), m);
+        buf[m] = 0;
+      }
+      return LMFAO_OK;
+    }
+    const PhysPlan &P = *ctx->plan;
+    o << "],\"physical\":{\"root\":" << nm(P.root) << ",\"segment_relation\":"
+      << (P.segrel >= 0 ? nm(P.segrel) : std::string("null")) << ",\"n_segments\":" << P.nseg
+      << ",\"outer\":[";
+    for (size_t i = 0; i < P.outer.size(); ++i) o << (i ? "," : "") << nm(P.outer[i]);
+    o << "],\"inner\":[";
+    for (size_t i = 0; i < P.inner.size(); ++i) o << (i ? "," : "") << nm(P.inner[i]);
+    o << "],\"precision\":\"" << (P.fp64 ? "fp64" : "fp32") << "\",\"mode\":\""
+      << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : "factorised") << "\",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
+      << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
+      << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
+      << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows
+      << ",\"view_columns\":{";
+    first = true;
+    for (int r : t.post) {
+      o << (first ? "" : ",") << nm(r) << ":" << P.views[r].cols.size();
+      first = false;
+    }
+    o << "}}}";
+    std::string str = o.str();
+    if (needed) *needed = str.size() + 1;
+    if (buf && len) {
+      size_t m = std::min(len - 1, str.size());
+      std::memcpy(buf, str.data(), m);
+      buf[m] = 0;
+    }
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_cart_variances(lmfao_ctx *ctx, const int *qids, int n, double *out, void *stream) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->ran || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
+    if (n < 0 || (n && (!qids || !out))) return fail(ctx, LMFAO_ERR_ARG, "bad arguments");
+    PhysPlan &P = *ctx->plan;
+    std::vector<int64_t> qd;
+    int nb_max = 0;
+    for (int i = 0; i < n; ++i) {
+      int q = qids[i];
+      if (q < 0 || q >= (int)ctx->queries.size()) return fail(ctx, LMFAO_ERR_ARG, "bad query id");
+      const QueryIn &Q = ctx->queries[q];
+      if (Q.gb.size() != 1 || Q.gb[0].kind != LMFAO_GB_BUCKET || Q.aggs.size() != 3)
+        return fail(ctx, LMFAO_ERR_ARG, "CART variances need one BUCKET group-by and aggregates COUNT, SUM(y), SUM(y^2)");
+      nb_max = std::max(nb_max, (int)Q.gb[0].thr.size() + 1);
+    }
+    for (int i = 0; i < n; ++i) {
+      const QueryOut &q = P.qout[qids[i]];
+      if ((int)q.cells != nb_max) return fail(ctx, LMFAO_ERR_ARG, "all queries need the same number of buckets");
+      qd.insert(qd.end(), {q.io, q.fo, q.cells, q.naggs, 1, 2});
+    }
+    if (!n || nb_max < 2) return LMFAO_OK;
+    int64_t *dq = P.arena.upload(qd, ctx->stream);
+    LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+    launch_cart_variances(P.icnt, P.fsum, dq, n, nb_max, out, (cudaStream_t)stream);
+    LMFAO_CUDA(cudaGetLastError());
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_set_profiling(lmfao_ctx *ctx, int on) {
+  return guarded(ctx, [&]() -> int {
+    ctx->profiling = on != 0;
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_kernel_times(lmfao_ctx *ctx, double *ms, int cap, int *n) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->ran) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
+    LMFAO_CUDA(cudaStreamSynchronize(ctx->run_stream));
+    int k = (int)ctx->ev_names.size() - 1;
+    if (k < 0) k = 0;
+    ctx->kernel_names.assign(ctx->ev_names.begin() + (ctx->ev_names.empty() ? 0 : 1), ctx->ev_names.end());
+    for (int i = 0; i < k && i < cap; ++i) {
+      float f = 0;
+      LMFAO_CUDA(cudaEventElapsedTime(&f, ctx->events[i], ctx->events[i + 1]));
+      ms[i] = f;
+    }
+    if (n) *n = k;
+    return LMFAO_OK;
+  });
+}
+
+const char *lmfao_kernel_name(lmfao_ctx *ctx, int i) {
+  if (!ctx || i < 0 || i >= (int)ctx->kernel_names.size()) return "";
+  return ctx->kernel_names[i].c_str();
+}
+
+}  // extern "C"

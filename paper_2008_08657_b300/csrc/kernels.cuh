@@ -1,0 +1,133 @@
+// Device-side descriptors and launchers shared by the host planner and the kernels.
+#pragma once
+
+#include "engine.h"
+
+namespace lmfao {
+
+// Root fact pass (Section 2 multi-output plan for the root group; Fig. 3 with the segment
+// key as the outer trie level): one warp per work item (a contiguous run of tuples of one
+// segment). Per tuple: inner view lookups, row terms; per segment: sums of the B0 row
+// terms (the view V_{F->S}); per tuple: direct accumulation of B2 items.
+struct DB2Item {
+  int psi;       // outer term id
+  int rterm;     // row term id
+  int integral;
+  int og0, nog;  // outer group refs (segment level)
+  int ig0, nig;  // inner group refs (tuple level)
+  int64_t out;   // output base index (fsum or icnt)
+  int64_t cellmul;
+};
+
+struct DWork {  // one work item: tuples [r0, r0 + len) of segment seg
+  long long r0;
+  int seg;
+  int len;
+};
+
+struct DOuter {  // an outer child: key index from the segment id
+  DViewRef v;
+  int64_t dstride[8];  // contribution of each segment digit to the view key index
+};
+
+struct DSegment {  // segment key decoding
+  int ndig;
+  int64_t dom[8];
+  int64_t radix[8];  // seg = sum digit_i * radix[i]
+};
+
+struct DFactPass {
+  int64_t nwork;
+  const DWork *work;
+  const unsigned long long *wseg;  // outer count product per segment
+  int ncols;
+  DCol col[MAXRC];
+  int ninner;
+  DViewRef inner[MAXIN];
+  int nmono;
+  const DMono *mono;
+  const DFac *facs;
+  int nrt;
+  const DRTerm *rt;
+  const DPart *parts;
+  int n0f, n0i;               // B0 float terms = row terms b0f[0..n0f), int = b0i[..]
+  const int *b0f, *b0i;
+  void *phi0f;                // n_seg x n0f (float or double)
+  unsigned long long *phi0i;  // n_seg x n0i
+  // B2
+  int nb2;
+  const DB2Item *b2;
+  const DGroupRef *grefs;
+  const float *thr;
+  // outer side for B2 psi / outer group codes
+  DSegment seg;
+  int nouter;
+  DOuter outer[MAXOUT];
+  int npsi;
+  const DPsi *psi;
+  const DSegFac *segfacs;
+  const DPart *psiparts;
+  double *fsum;
+  unsigned long long *icnt;
+  int b2_smem_items;  // B2 items whose psi is staged per warp
+};
+
+// A query output region mirrored in shared memory by the combine (CTA-private sums).
+struct DMirror { long long gout; int soff; int len; int integral; int pad; };
+
+struct DCombine {
+  int64_t nseg;
+  const unsigned long long *wseg;
+  DSegment seg;
+  int nouter;
+  DOuter outer[MAXOUT];
+  int npsi;
+  const DPsi *psi;
+  const DSegFac *segfacs;
+  const DPart *psiparts;
+  int n0f, n0i;
+  const void *phi0f;
+  const unsigned long long *phi0i;
+  int nitems;
+  const DCombItem *items;
+  const DGroupRef *grefs;
+  const float *thr;
+  const int *item_smem;   // per item: smem output offset for grouped items (-1: global)
+  int smem_fcells, smem_icells;
+  int nmirror;
+  const DMirror *mirror;
+  double *fsum;
+  unsigned long long *icnt;
+  int tile;
+};
+
+struct DSegWeight {
+  int64_t nseg;
+  DSegment seg;
+  int nouter;
+  DOuter outer[MAXOUT];
+  unsigned long long *wseg;
+};
+
+// launchers (kernels.cu)
+void launch_view_kernel(const DViewKernel &d, cudaStream_t s);
+void launch_view_finish(const double *v64, float *v32, uint32_t *vint, const int *intcols,
+                        int ncols, int nint, int64_t nkeys, int *err, cudaStream_t s);
+void launch_segment_weights(const DSegWeight &d, cudaStream_t s);
+void launch_fact_pass(const DFactPass &d, bool fp64, int nb0, int grid, int block, cudaStream_t s);
+void launch_combine(const DCombine &d, bool fp64, int grid, int block, size_t smem, cudaStream_t s);
+void launch_segment_ids(const DCol *cols, int ncols, const int64_t *radix, int64_t n, int *segid,
+                        cudaStream_t s);
+void launch_histogram(const int *segid, int64_t n, unsigned int *hist, cudaStream_t s);
+void launch_scatter_rows(const int *segid, int64_t n, unsigned long long *cursor, const DCol *in,
+                         DCol *out, const int *elem_size, int ncols, cudaStream_t s);
+void launch_range_check(const void *p, int dtype, int64_t n, int64_t domain, int *bad, cudaStream_t s);
+void launch_key_multiplicity(const DCol *cols, int ncols, const int64_t *stride, int64_t n,
+                             unsigned int *hist, cudaStream_t s);
+void launch_max_u32(const unsigned int *h, int64_t n, unsigned int *out, cudaStream_t s);
+void launch_cart_variances(const unsigned long long *icnt, const double *fsum, const int64_t *qdesc,
+                           int n, int nb_max, double *out, cudaStream_t s);
+void launch_results(const unsigned long long *icnt, const double *fsum, int64_t cells, int naggs,
+                    const int *integral, int64_t *counts, double *sums, cudaStream_t s);
+
+}  // namespace lmfao

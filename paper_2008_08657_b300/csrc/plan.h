@@ -1,0 +1,114 @@
+// Planner state of a context (join tree, logical views and groups, physical plan).
+#pragma once
+
+#include <set>
+
+#include "kernels.cuh"
+
+namespace lmfao {
+
+size_t fact_pass_smem(const DFactPass &d, bool fp64, int block);
+size_t combine_smem(const DCombine &d, bool fp64);
+
+// Join tree over the relations (Section 2 "the backbone of this plan is a join tree").
+struct JoinTree {
+  int root = -1;
+  std::vector<int> parent;                 // -1 for the root
+  std::vector<std::vector<int>> children;
+  std::vector<int> depth;
+  std::vector<int> post;                   // non-root relations, children before parents
+};
+
+// Logical plan of Section 2: per-query roots, directional views after merging, groups.
+struct LogicalView {
+  int from = -1, to = -1;
+  std::vector<std::string> key;            // join attributes of the edge + carried group-by attributes
+  std::set<std::string> aggs;              // aggregate parts over the subtree (canonical strings)
+  std::set<int> queries;
+  std::set<int> deps;                      // incoming views it is computed from
+};
+struct LogicalGroup {
+  int node = -1;
+  std::vector<int> views;                  // outgoing views computed by the group
+  std::vector<int> queries;                // queries whose root is the node
+  std::set<int> deps;                      // groups it depends on
+};
+struct LogicalPlan {
+  std::vector<int> query_root;
+  std::vector<LogicalView> views;
+  std::vector<LogicalGroup> groups;
+};
+
+struct QueryOut {
+  int64_t cells = 1;
+  int64_t fo = 0, io = 0;  // offsets into fsum (cells x naggs) and icnt (cells x (1 + naggs))
+  int naggs = 0;
+  std::vector<int64_t> dom;
+  std::vector<int> integral;
+  std::vector<int> gitems;  // group item ids in query order
+};
+
+struct DeviceArena {  // allocations owned by a plan
+  std::vector<void *> ptrs;
+  void *alloc(size_t bytes);
+  template <typename T> T *upload(const std::vector<T> &v, cudaStream_t s);
+  void release();
+};
+
+struct PhysPlan {
+  bool fp64 = false;
+  int mode = LMFAO_MODE_FACTORISED;
+  int root = -1, segrel = -1;
+  std::vector<int> segcols;        // root columns forming the segment key
+  std::vector<int64_t> segdom;
+  int64_t nseg = 1;
+  std::vector<int> outer, inner;   // root children
+  std::vector<int> kind;           // per relation: 0 root, 1 outer subtree, 2 inner subtree
+  std::vector<int> branch;         // per relation: root child whose subtree holds it (-1 root)
+  std::vector<View> views;         // per relation (root entry unused)
+  std::vector<Fac> facs;
+  std::map<Fac, int> facmap;
+  std::vector<GroupItem> gitems;
+  std::map<GroupItem, int> gmap;
+  std::vector<QueryOut> qout;
+  int64_t nfsum = 0, nicnt = 0;
+  // root tuple level
+  std::vector<int> rowcols;        // root columns read per tuple
+  std::map<int, int> rowslot;
+  std::vector<std::vector<int>> monos;
+  std::map<std::vector<int>, int> monomap;
+  struct RT { int mono; std::vector<std::pair<int, int>> parts; bool integral; };
+  std::vector<RT> rts;
+  std::map<std::pair<int, std::vector<std::pair<int, int>>>, int> rtmap;
+  struct Psi { std::vector<int> segf; std::vector<std::pair<int, int>> parts; bool integral; };
+  std::vector<Psi> psis;
+  std::map<std::pair<std::vector<int>, std::vector<std::pair<int, int>>>, int> psimap;
+  std::vector<int> b0f, b0i;       // row terms summed per segment
+  std::vector<DCombItem> comb;
+  std::vector<DB2Item> b2;
+  std::vector<DGroupRef> grefs;
+  std::vector<float> thr;
+  int nb0 = 4;
+  // device
+  DeviceArena arena;
+  std::vector<DCol> rowdev;        // reorganised root columns (per row slot)
+  DWork *work = nullptr;
+  int64_t nwork = 0;
+  unsigned long long *wseg = nullptr;
+  void *phi0f = nullptr;
+  unsigned long long *phi0i = nullptr;
+  double *fsum = nullptr;
+  unsigned long long *icnt = nullptr;
+  int *err = nullptr;
+  std::vector<DViewKernel> vk;     // per view relation, in post order
+  std::vector<int> vk_rel;
+  DFactPass fp{};
+  DCombine cb{};
+  DSegWeight sw{};
+  size_t cb_smem = 0;
+  int fp_grid = 0, fp_block = 256, cb_grid = 0, cb_block = 256;
+  std::vector<std::string> kernel_names;
+  double plan_ms = 0;
+};
+
+}  // namespace lmfao

@@ -442,13 +442,15 @@ def scaled(rels, fact_rows, seed=0, fact_name=None):
 # Tiny random schemas (duplicate and dangling keys) for brute-force checks
 # ---------------------------------------------------------------------------------------
 
-def tiny_schema(seed, max_rows=12, kdom=4, shared3=False, empty_ok=True):
+def tiny_schema(seed, max_rows=12, kdom=4, shared3=False, empty_ok=True, fd=False):
     """A tiny acyclic schema with duplicate and dangling join keys.
 
     R0(k1, k2, x0, g0/3) joins R1(k1, x1, g1/2) on k1 and R2(k2, k3, x2) on k2; R2 joins
     R3(k3, x3, g3/3) on k3. With ``shared3`` a fifth relation R4(k1, k2, x4) shares both
     of R0's keys (k1 then appears in three relations). Keys are drawn from ``[0, kdom)``
-    with repetition, so some keys repeat and some have no partner.
+    with repetition, so some keys repeat and some have no partner. With ``fd`` the
+    relations holding categoricals (R1, R3) get distinct keys, so their categoricals are
+    determined by their join key (the other relations keep repeated keys).
     """
     r = _rng(seed, 6)
 
@@ -463,14 +465,20 @@ def tiny_schema(seed, max_rows=12, kdom=4, shared3=False, empty_ok=True):
         return _f32(np.round(r.standard_normal(m) * 4) / 4)
 
     m0, m1, m2, m3 = n(), n(), n(), n()
+    if fd:
+        m1, m3 = min(m1, kdom - 1), min(m3, kdom - 1)
+
+    def ukeys(m):
+        return _i32(r.permutation(kdom)[:m]) if fd else keys(m)
+
     rels = [
         relation("R0", [column("k1", keys(m0), KEY, kdom), column("k2", keys(m0), KEY, kdom),
                         column("x0", vals(m0), CONT), column("g0", keys(m0, 3), CAT, 3)]),
-        relation("R1", [column("k1", keys(m1), KEY, kdom), column("x1", vals(m1), CONT),
+        relation("R1", [column("k1", ukeys(m1), KEY, kdom), column("x1", vals(m1), CONT),
                         column("g1", keys(m1, 2), CAT, 2)]),
         relation("R2", [column("k2", keys(m2), KEY, kdom), column("k3", keys(m2), KEY, kdom),
                         column("x2", vals(m2), CONT)]),
-        relation("R3", [column("k3", keys(m3), KEY, kdom), column("x3", vals(m3), CONT),
+        relation("R3", [column("k3", ukeys(m3), KEY, kdom), column("x3", vals(m3), CONT),
                         column("g3", keys(m3, 3), CAT, 3)]),
     ]
     if shared3:
@@ -480,12 +488,15 @@ def tiny_schema(seed, max_rows=12, kdom=4, shared3=False, empty_ok=True):
     return rels
 
 
-def tiny_queries(seed, rels, nq=6):
+def tiny_queries(seed, rels, nq=6, group_attrs=None, bucket_attrs=None):
     """Random queries over a tiny schema: products of 0..3 factors (with powers),
-    0..2 group-by attributes (values or buckets), 0..2 filter predicates."""
+    0..2 group-by attributes (values or buckets), 0..2 filter predicates. Group-by
+    attributes are drawn from ``group_attrs`` / ``bucket_attrs`` when given."""
     r = _rng(seed, 7)
     conts = [c["attr"] for R in rels for c in R["columns"] if c["role"] == CONT]
     cats = sorted({c["attr"] for R in rels for c in R["columns"] if c["role"] in (CAT, KEY)})
+    gcats = cats if group_attrs is None else list(group_attrs)
+    gconts = conts if bucket_attrs is None else list(bucket_attrs)
     ops = ["le", "lt", "ge", "gt", "eq", "ne"]
     qs = []
     for _ in range(nq):
@@ -497,11 +508,12 @@ def tiny_queries(seed, rels, nq=6):
             aggs[-1] = [(a, fn, p if fn == "pow" else 1) for a, fn, p in aggs[-1]]
         gb = []
         for _g in range(int(r.integers(0, 3))):
-            if r.random() < 0.3:
-                a = conts[int(r.integers(0, len(conts)))]
-                gb.append((a, "bucket", np.array([-1.0, 0.0, 0.5], dtype=np.float32)))
-            else:
-                a = cats[int(r.integers(0, len(cats)))]
+            if r.random() < 0.3 and gconts:
+                a = gconts[int(r.integers(0, len(gconts)))]
+                if a not in [g[0] for g in gb]:
+                    gb.append((a, "bucket", np.array([-1.0, 0.0, 0.5], dtype=np.float32)))
+            elif gcats:
+                a = gcats[int(r.integers(0, len(gcats)))]
                 if a not in [g[0] for g in gb]:
                     gb.append((a, "value", None))
         flt = []

@@ -1,0 +1,174 @@
+"""Engine against the oracle on the same seeded inputs (CUDA path through the C ABI)."""
+import numpy as np
+import pytest
+
+from oracle import lmfao_oracle as O
+from paper_2008_08657_b300 import workloads as W
+from paper_2008_08657_b300.lmfao import Engine, LmfaoError, ERR_UNSUPPORTED
+from tests.parity import compare
+
+pytestmark = pytest.mark.gpu
+
+# group-by attributes determined by the join key of their relation toward the root R0
+# (R1 has distinct k1 values; R3's g3 would pass through R2, whose k2 values repeat)
+TINY_GROUPS = ["k1", "k2", "g0", "g1"]
+TINY_BUCKETS = ["x0", "x1"]
+
+
+def run_engine(rels, qs, **plan):
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_queries(qs)
+    info = e.plan(**plan)
+    e.run()
+    out = e.fetch_all()
+    e.close()
+    return out, info
+
+
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("mode", ["factorised", "per_tuple"])
+@pytest.mark.parametrize("segment", [None, "R1", "R2", "R4"])
+def test_tiny_schemas_match_oracle(seed, precision, mode, segment):
+    shared3 = seed % 2 == 1
+    if segment == "R4" and not shared3:
+        pytest.skip("R4 exists only in the five-relation variant")
+    rels = W.tiny_schema(seed, shared3=shared3, fd=True)
+    qs = W.tiny_queries(seed, rels, nq=6, group_attrs=TINY_GROUPS, bucket_attrs=TINY_BUCKETS)
+    ref = O.evaluate(rels, qs)
+    # join tree: R1, R2, R4 below R0 and R3 below R2; the segment relation is forced
+    parent = [-1, 0, 0, 2, 0][:len(rels)]
+    got, _ = run_engine(rels, qs, precision=precision, mode=mode, root="R0", segment=segment,
+                        join_parent=parent)
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"seed {seed} query {i}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_star_config_full_size(precision):
+    rels = W.star_schema()
+    qs = W.star_batch()
+    ref = O.evaluate(rels, qs)
+    got, info = run_engine(rels, qs, precision=precision)
+    assert info["segment_rel"] >= 0
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"query {i}")
+    assert got[0]["counts"][0] == 200_000
+
+
+def test_retailer_scaled():
+    rels = W.retailer_schema(n_fact=300_000)
+    qs = W.retailer_batch()
+    ref = O.evaluate(rels, qs)
+    got, info = run_engine(rels, qs, precision="fp32")
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"query {i}")
+
+
+def test_favorita_scaled_fig2_tree():
+    rels = W.favorita_schema(n_fact=300_000)
+    qs = W.favorita_batch()
+    names = [R["name"] for R in rels]
+    parent = [names.index(W.FAVORITA_TREE[n]) if n in W.FAVORITA_TREE else -1 for n in names]
+    ref = O.evaluate(rels, qs)
+    got, info = run_engine(rels, qs, precision="fp32", join_parent=parent)
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"query {i}")
+
+
+def test_plan_invariance_retailer():
+    rels = W.retailer_schema(n_fact=200_000)
+    qs = W.retailer_batch()[:4]
+    base, _ = run_engine(rels, qs, precision="fp32")
+    for plan in ({"segment": None}, {"segment": "Location"}, {"mode": "per_tuple"}, {"precision": "fp64"}):
+        kw = {"precision": "fp32", **plan}
+        other, _ = run_engine(rels, qs, **kw)
+        for q, a, b in zip(qs, base, other):
+            np.testing.assert_array_equal(a["keys"], b["keys"])
+            np.testing.assert_array_equal(a["counts"], b["counts"])
+            scale = np.maximum(np.abs(a["sums"]), 1.0)
+            assert (np.abs(a["sums"] - b["sums"]) <= 1e-4 * scale).all(), plan
+
+
+def test_dt_level_and_cart_variances():
+    import torch
+    rels = W.retailer_schema(n_fact=300_000)
+    qs, splits, thr = W.dt_level_batch(rels)
+    ref = O.evaluate(rels, qs)
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_queries(qs)
+    e.plan(precision="fp32")
+    e.run()
+    got = e.fetch_all()
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"query {i}")
+    nb = max(len(t) for t in thr.values()) + 1
+    ids = [i for i, q in enumerate(qs) if len(q["groupby"][0][2]) + 1 == nb]
+    out = torch.zeros((len(ids), nb - 1, 2), dtype=torch.float64, device="cuda")
+    e.cart_variances(ids, out)
+    torch.cuda.synchronize()
+    for k, qi in enumerate(ids):
+        left, right = O.cart_variances(ref[qi])
+        nbq = len(left)
+        L = out[k, :nbq, 0].cpu().numpy()
+        R_ = out[k, :nbq, 1].cpu().numpy()
+        scale = np.abs(ref[qi]["abs"][:, 2]).sum() + 1.0
+        assert np.abs(L - left).max() <= 1e-5 * scale
+        assert np.abs(R_ - right).max() <= 1e-5 * scale
+    e.close()
+
+
+def test_group_attribute_not_determined_by_key_is_reported():
+    rels = W.tiny_schema(3, empty_ok=False)  # R1 keys repeat, so g1 is not a function of k1
+    rels[1]["columns"][0]["data"][:] = 0
+    rels[1]["columns"][2]["data"][:] = np.arange(rels[1]["nrows"]) % 2
+    q = {"aggs": [[]], "groupby": [("g1", "value", None)], "filters": []}
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_query(q)
+    e.plan(root="R0")
+    e.run()
+    with pytest.raises(LmfaoError) as ei:
+        e.fetch(0)
+    assert ei.value.code == ERR_UNSUPPORTED
+    e.close()
+
+
+def test_empty_fact_and_empty_dimension():
+    rels = W.star_schema(n_fact=0)
+    qs = W.star_batch()
+    got, _ = run_engine(rels, qs)
+    ref = O.evaluate(rels, qs)
+    for q, g, r in zip(qs, got, ref):
+        compare(q, g, r)
+    rels = W.star_schema(n_fact=1000)
+    rels[2] = W.relation("D2", [dict(c, data=c["data"][:0]) for c in rels[2]["columns"]])
+    got, _ = run_engine(rels, qs)
+    ref = O.evaluate(rels, qs)
+    for q, g, r in zip(qs, got, ref):
+        compare(q, g, r)
+    assert got[0]["counts"][0] == 0
+
+
+def test_device_columns_and_torch_stream():
+    import torch
+    rels = W.star_schema(n_fact=50_000)
+    qs = W.star_batch()
+    ref = O.evaluate(rels, qs)
+    e = Engine(0)
+    for R in rels:
+        dev = dict(R, columns=[dict(c, data=torch.from_numpy(c["data"]).cuda()) for c in R["columns"]])
+        e.load_relation(dev, where="adopt" if R["name"] == "F" else "device")
+    e.add_queries(qs)
+    e.plan()
+    s = torch.cuda.Stream()
+    e.run(s)
+    got = e.fetch_all()
+    for q, g, r in zip(qs, got, ref):
+        compare(q, g, r)
+    e.close()
