@@ -227,6 +227,21 @@ LMFAO_API int lmfao_describe_plan(struct lmfao_ctx *ctx, char *buf, size_t len, 
  * n x (B-1) x 2 doubles: left, right) is written asynchronously on `stream`. */
 LMFAO_API int lmfao_cart_variances(struct lmfao_ctx *ctx, const int *qids, int n, double *out, void *stream);
 
+/* Allocation-free variant of lmfao_cart_variances (same arguments, same results), for
+ * callers that cannot allocate device memory when they ask for split variances: a host
+ * framework that gives the engine a fixed device-memory budget through its own caching
+ * allocator, or a tree-building loop that must not pay the device-wide synchronisation
+ * cudaMalloc / cudaFree can cause. The paper has no counterpart of this call; it exists
+ * for those callers only. The per-query descriptors live in a fixed device array of
+ * LMFAO_NOALLOC_MAX_QUERIES entries (192 KiB, held on every device that loads the
+ * library until the process exits); n above that limit gives LMFAO_ERR_ARG. The first
+ * call on a device looks up the array's device address, so make that first call before
+ * any stream capture. All calls on a device share the array: calls whose work overlaps
+ * on the GPU race on it. No cudaMalloc, cudaFree or other allocating routine is called. */
+#define LMFAO_NOALLOC_MAX_QUERIES 4096
+LMFAO_API int lmfao_cart_variances_noalloc(struct lmfao_ctx *ctx, const int *qids, int n, double *out,
+                                           void *stream);
+
 /* Timings of the last lmfao_run measured with CUDA events around each kernel (host
  * array of at most cap doubles, milliseconds, in launch order; names via
  * lmfao_kernel_name). Waits for the run's stream. *n receives the number of kernels. */

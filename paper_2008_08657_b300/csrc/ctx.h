@@ -1,0 +1,26 @@
+// Definition of the opaque lmfao_ctx handle of include/lmfao.h (shared by the host files).
+#pragma once
+
+#include "plan.h"
+
+struct lmfao_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // internal stream for loading and planning
+  std::string last_error;
+  std::vector<lmfao::Relation> rels;
+  std::vector<lmfao::QueryIn> queries;
+  lmfao::JoinTree tree;
+  lmfao::LogicalPlan logical;
+  lmfao::PhysPlan *plan = nullptr;
+  bool planned = false, ran = false;
+  cudaStream_t run_stream = nullptr;
+  // fetch buffers
+  std::vector<int32_t> fk;
+  std::vector<int64_t> fc;
+  std::vector<double> fs;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<std::string> ev_names;
+  std::vector<std::string> kernel_names;
+};

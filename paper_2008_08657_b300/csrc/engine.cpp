@@ -8,31 +8,10 @@
 #include <numeric>
 #include <sstream>
 
-#include "plan.h"
+#include "ctx.h"
 
 using namespace lmfao;
 
-struct lmfao_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;  // internal stream for loading and planning
-  std::string last_error;
-  std::vector<Relation> rels;
-  std::vector<QueryIn> queries;
-  JoinTree tree;
-  LogicalPlan logical;
-  PhysPlan *plan = nullptr;
-  bool planned = false, ran = false;
-  cudaStream_t run_stream = nullptr;
-  // fetch buffers
-  std::vector<int32_t> fk;
-  std::vector<int64_t> fc;
-  std::vector<double> fs;
-  // profiling
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  std::vector<std::string> ev_names;
-  std::vector<std::string> kernel_names;
-};
 
 namespace lmfao {
 

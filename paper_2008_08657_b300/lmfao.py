@@ -34,7 +34,7 @@ ENTRY_POINTS = [
     "lmfao_create", "lmfao_destroy", "lmfao_last_error", "lmfao_load_relation", "lmfao_add_batch",
     "lmfao_clear_batch", "lmfao_plan", "lmfao_run", "lmfao_fetch", "lmfao_result_device",
     "lmfao_describe_plan", "lmfao_cart_variances", "lmfao_kernel_times", "lmfao_kernel_name",
-    "lmfao_set_profiling",
+    "lmfao_set_profiling", "lmfao_cart_variances_noalloc",
 ]
 
 
@@ -114,6 +114,7 @@ def library():
             "lmfao_kernel_times": (C.c_int, [P, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
             "lmfao_kernel_name": (C.c_char_p, [P, C.c_int]),
             "lmfao_set_profiling": (C.c_int, [P, C.c_int]),
+            "lmfao_cart_variances_noalloc": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -316,6 +317,13 @@ class Engine:
         arr = (C.c_int * len(qids))(*[int(q) for q in qids])
         self._check(self.lib.lmfao_cart_variances(self.ctx, arr, len(qids), C.c_void_p(out.data_ptr()),
                                                   _stream_handle(stream)))
+
+    def cart_variances_noalloc(self, qids, out, stream=None):
+        """Same as ``cart_variances`` without any device allocation (fixed descriptor
+        array of LMFAO_NOALLOC_MAX_QUERIES entries shared by all calls on the device)."""
+        arr = (C.c_int * max(1, len(qids)))(*[int(q) for q in qids])
+        self._check(self.lib.lmfao_cart_variances_noalloc(self.ctx, arr, len(qids), C.c_void_p(out.data_ptr()),
+                                                          _stream_handle(stream)))
 
     def set_profiling(self, on=True):
         self._check(self.lib.lmfao_set_profiling(self.ctx, 1 if on else 0))
