@@ -126,6 +126,9 @@ def bench_lmfao(args):
     eng.set_profiling(True)
     eng._profiling = True
     _, fact_ms = time_runs(eng, torch, stream, max(3, args.steps // 2), 2)
+    kernel_ms = {}
+    for name, ms_k in eng.kernel_times():
+        kernel_ms[name] = round(ms_k, 4)
     eng.set_profiling(False)
     eng._profiling = False
     # the timed region proper
@@ -178,6 +181,7 @@ def bench_lmfao(args):
         "vs_plain_fp64_gpu": (fp64_ms / ms_step) if fp64_ms else None,
         "plain_fp64_ms_per_step": fp64_ms,
         "plan_ms": info["plan_ms"],
+        "kernel_ms": kernel_ms,
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": info["n_kernels"] * args.steps,

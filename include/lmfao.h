@@ -113,7 +113,11 @@ enum {
   LMFAO_PLAN_LEARNED = 2,     /* rank candidates with the learned cost model (MLP)         */
   LMFAO_PLAN_FORCED = 3       /* use root_rel / segment_rel / mode as given                */
 };
-enum { LMFAO_MODE_AUTO = 0, LMFAO_MODE_FACTORISED = 1, LMFAO_MODE_PER_TUPLE = 2 };
+/* Root-pass modes: AUTO and FACTORISED use the specialised pass when the plan has at most
+ * one inner child of the root (else the generic pass); GENERIC forces the generic pass
+ * (per-segment sums, per-tuple accumulation of inner-grouped items); PER_TUPLE evaluates
+ * every item per tuple of the root relation. All modes give the same results. */
+enum { LMFAO_MODE_AUTO = 0, LMFAO_MODE_FACTORISED = 1, LMFAO_MODE_PER_TUPLE = 2, LMFAO_MODE_GENERIC = 3 };
 
 typedef struct lmfao_plan_opts {
   int32_t precision;        /* LMFAO_FP64 (plain form), LMFAO_FP32, LMFAO_SPLIT_TF32     */

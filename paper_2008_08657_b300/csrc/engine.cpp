@@ -9,6 +9,7 @@
 #include <sstream>
 
 #include "ctx.h"
+#include "fastpass.cuh"
 
 using namespace lmfao;
 
@@ -534,9 +535,24 @@ struct Planner {
     return r;
   }
 
-  void build_items(int mode) {
+  // One output item: aggregate a of query q (a = -1: the query's COUNT(*)), split into
+  // its outer part psi (segment level), its row factors, its inner view columns and its
+  // outer / inner group references.
+  struct ItemD {
+    int q = 0, a = 0;
+    bool integral = true;
+    int psi = 0;
+    std::vector<int> rowf;
+    std::vector<std::pair<int, int>> ipart;
+    std::vector<DGroupRef> og, ig;
+    int64_t out = 0, cellmul = 1;
+    bool outer_dep = false;
+  };
+
+  std::vector<ItemD> decompose() {
     int root = t.root;
     int64_t fo = 0, io = 0;
+    std::vector<ItemD> items;
     for (int q = 0; q < (int)ctx->queries.size(); ++q) {
       const QueryIn &Q = ctx->queries[q];
       QueryOut qo;
@@ -570,89 +586,270 @@ struct Planner {
       std::vector<int> inds;
       for (auto &p : Q.filters) inds.push_back(fac_id(make_fac(p.attr, true, 1, p.op, p.t)));
       for (int a = -1; a < qo.naggs; ++a) {
+        ItemD it;
+        it.q = q;
+        it.a = a;
         Term term = inds;
-        bool integral = true;
         if (a >= 0)
           for (auto &f : Q.aggs[a]) {
-            if (f.fn == LMFAO_FN_POW && f.param < 1) throw Error(LMFAO_ERR_ARG, "POW exponent must be >= 1");
             term.push_back(fac_id(make_fac(f.attr, false, f.fn == LMFAO_FN_POW ? f.param : 1, 0, 0.f)));
-            integral = false;
+            it.integral = false;
           }
-        if (a >= 0) qo.integral.push_back(integral ? 1 : 0);
+        if (a >= 0) qo.integral.push_back(it.integral ? 1 : 0);
         std::sort(term.begin(), term.end());
         // split the product by where its factors live
-        std::vector<int> segf, rowf;
+        std::vector<int> segf;
         std::map<int, Term> bparts;
         for (int f : term) {
           const Fac &fc = P.facs[f];
           if (fc.rel == root) {
             int d = seg_digit_of(fc.col);
             if (d >= 0) segf.push_back(f);
-            else { rowslot(fc.col); rowf.push_back(f); }
+            else { rowslot(fc.col); it.rowf.push_back(f); }
           } else bparts[P.branch[fc.rel]].push_back(f);
         }
-        std::vector<std::pair<int, int>> opart, ipart;
+        std::vector<std::pair<int, int>> opart;
+        it.outer_dep = !segf.empty();
         for (int c : P.outer) {
           int col = view_col(c, bparts.count(c) ? bparts[c] : Term{});
           opart.push_back({outer_idx(c), col});
+          if (col != 0) it.outer_dep = true;
         }
         for (int c : P.inner) {
           int col = view_col(c, bparts.count(c) ? bparts[c] : Term{});
-          ipart.push_back({inner_idx(c), col});  // float col; integral cols remapped later
+          it.ipart.push_back({inner_idx(c), col});
         }
-        int psi = psi_id(segf, opart, integral);
-        int rt = rt_id(mono_id(rowf), ipart, integral);
-        // groups
-        std::vector<DGroupRef> og, ig;
+        it.psi = psi_id(segf, opart, it.integral);
         for (size_t i = 0; i < qo.gitems.size(); ++i) {
           DGroupRef g = group_ref(qo.gitems[i], stride[i]);
-          (g.src <= 1 ? og : ig).push_back(g);
+          (g.src <= 1 ? it.og : it.ig).push_back(g);
         }
-        int64_t out = integral ? qo.io + 1 + a : qo.fo + a;
-        int64_t cellmul = integral ? 1 + qo.naggs : qo.naggs;
-        bool b0 = ig.empty() && mode != LMFAO_MODE_PER_TUPLE;
-        if (b0) {
-          auto &lst = integral ? P.b0i : P.b0f;
-          int pos = (int)(std::find(lst.begin(), lst.end(), rt) - lst.begin());
-          int cap = integral ? NI0_MAX : NB0_MAX;
-          if (pos == (int)lst.size()) {
-            if ((int)lst.size() >= cap) b0 = false;
-            else lst.push_back(rt);
-          }
-          if (b0) {
-            DCombItem it{};
-            it.psi = psi;
-            it.block = -1;
-            it.col = pos;
-            it.integral = integral;
-            it.og0 = (int)P.grefs.size();
-            it.nog = (int)og.size();
-            P.grefs.insert(P.grefs.end(), og.begin(), og.end());
-            it.out = out;
-            it.cellmul = cellmul;
-            P.comb.push_back(it);
-          }
-        }
-        if (!b0) {
-          DB2Item it{};
-          it.psi = psi;
-          it.rterm = rt;
-          it.integral = integral;
-          it.og0 = (int)P.grefs.size();
-          it.nog = (int)og.size();
-          P.grefs.insert(P.grefs.end(), og.begin(), og.end());
-          it.ig0 = (int)P.grefs.size();
-          it.nig = (int)ig.size();
-          P.grefs.insert(P.grefs.end(), ig.begin(), ig.end());
-          it.out = out;
-          it.cellmul = cellmul;
-          P.b2.push_back(it);
-        }
+        if (!it.og.empty()) it.outer_dep = true;
+        it.out = it.integral ? qo.io + 1 + a : qo.fo + a;
+        it.cellmul = it.integral ? 1 + qo.naggs : qo.naggs;
+        items.push_back(it);
       }
       P.qout.push_back(qo);
     }
     P.nfsum = fo;
     P.nicnt = io;
+    return items;
+  }
+
+  int add_grefs(const std::vector<DGroupRef> &g) {
+    int at = (int)P.grefs.size();
+    P.grefs.insert(P.grefs.end(), g.begin(), g.end());
+    return at;
+  }
+
+  // Generic routing: per-segment sums (B0) where the item has no inner group, per-tuple
+  // accumulation (B2) otherwise.
+  void route_generic(const std::vector<ItemD> &items, int mode) {
+    for (const ItemD &it : items) {
+      int rt = rt_id(mono_id(it.rowf), it.ipart, it.integral);
+      bool b0 = it.ig.empty() && mode != LMFAO_MODE_PER_TUPLE;
+      if (b0) {
+        auto &lst = it.integral ? P.b0i : P.b0f;
+        int pos = (int)(std::find(lst.begin(), lst.end(), rt) - lst.begin());
+        int cap = it.integral ? NI0_MAX : NB0_MAX;
+        if (pos == (int)lst.size()) {
+          if ((int)lst.size() >= cap) b0 = false;
+          else lst.push_back(rt);
+        }
+        if (b0) {
+          DCombItem c{};
+          c.psi = it.psi;
+          c.block = -1;
+          c.col = pos;
+          c.integral = it.integral;
+          c.og0 = add_grefs(it.og);
+          c.nog = (int)it.og.size();
+          c.out = it.out;
+          c.cellmul = it.cellmul;
+          P.comb.push_back(c);
+        }
+      }
+      if (!b0) {
+        DB2Item c{};
+        c.psi = it.psi;
+        c.rterm = rt;
+        c.integral = it.integral;
+        c.og0 = add_grefs(it.og);
+        c.nog = (int)it.og.size();
+        c.ig0 = add_grefs(it.ig);
+        c.nig = (int)it.ig.size();
+        c.out = it.out;
+        c.cellmul = it.cellmul;
+        P.b2.push_back(c);
+      }
+    }
+  }
+
+  // Routing of the specialised root pass (at most one inner child): B0 as the outer product
+  // of monomials and inner view columns, B1 per-segment group histograms, B3 partial view
+  // from the root to the inner relation. Returns false when the batch needs the generic pass.
+  bool route_fast(const std::vector<ItemD> &items) {
+    if (P.inner.size() > 1) return false;
+    if (P.inner.size() == 1) {
+      const View &v = P.views[P.inner[0]];
+      if (v.keycols.size() > 2) return false;
+      if (v.count_bound * 4096.0 >= 16777216.0) return false;  // exact integral sums in FP32
+    }
+    auto &F = P.fast;
+    F = PhysPlan::Fast{};
+    F.wcols.push_back(0);
+    auto mono_of = [&](std::vector<int> fs) -> int {
+      std::sort(fs.begin(), fs.end());
+      for (size_t j = 0; j < F.monos.size(); ++j) if (F.monos[j] == fs) return (int)j;
+      F.monos.push_back(fs);
+      return (int)F.monos.size() - 1;
+    };
+    auto wcol_of = [&](int c) -> int {
+      for (size_t w = 0; w < F.wcols.size(); ++w) if (F.wcols[w] == c) return (int)w;
+      F.wcols.push_back(c);
+      return (int)F.wcols.size() - 1;
+    };
+    struct Pending { ItemD it; int j, w; int kind; int set; };
+    std::vector<Pending> pend;
+    for (const ItemD &it : items) {
+      int j = mono_of(it.rowf);
+      int vcol = it.ipart.empty() ? 0 : it.ipart[0].second;
+      bool all_view = true;
+      for (auto &g : it.ig) all_view = all_view && g.src == 3;
+      // Items that do not depend on the outer side and read inner view columns (or group by
+      // inner codes) go to the view from the root to the inner relation (B3); the rest of the
+      // ungrouped items are per-segment sums (B0).
+      if (!it.outer_dep && all_view && !it.ipart.empty() && (vcol != 0 || !it.ig.empty())) {
+        pend.push_back({it, j, vcol, 3, -1});
+        continue;
+      }
+      if (it.ig.empty()) {
+        pend.push_back({it, j, wcol_of(vcol), 0, -1});
+        continue;
+      }
+      if (it.ig.size() > 2) return false;
+      // B1 set keyed by its group references (without the query strides)
+      std::vector<DGroupRef> key = it.ig;
+      int64_t G = 1;
+      std::vector<int64_t> dom;
+      for (auto &g : key) {
+        int64_t d = g.src == 3 ? P.gitems[code_group(P.inner[0], g.b)].dom
+                               : (g.kind == LMFAO_GB_BUCKET ? g.nthr + 1 : gdom_of_slot(g));
+        dom.push_back(d);
+        G *= d;
+      }
+      if (G > 4096) return false;
+      int set = -1;
+      for (size_t s2 = 0; s2 < F.b1.size(); ++s2) {
+        auto &S = F.b1[s2];
+        if (S.refs.size() != key.size()) continue;
+        bool same = true;
+        for (size_t i = 0; i < key.size(); ++i)
+          same = same && S.refs[i].src == key[i].src && S.refs[i].a == key[i].a && S.refs[i].b == key[i].b &&
+                 S.refs[i].kind == key[i].kind && S.thrs[i] == thr_of(key[i]);
+        if (same) { set = (int)s2; break; }
+      }
+      if (set < 0) {
+        if (F.b1.size() >= FMAXB1) return false;
+        PhysPlan::Fast::B1 S;
+        S.refs = key;
+        for (auto &g : key) S.thrs.push_back(thr_of(g));
+        S.dom = dom;
+        S.G = G;
+        F.b1.push_back(S);
+        set = (int)F.b1.size() - 1;
+      }
+      pend.push_back({it, j, wcol_of(vcol), 1, set});
+    }
+    if (F.monos.size() > FMAXM || F.wcols.size() > FMAXW) return false;
+    if (!fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return false;
+    int nfac = 0;
+    for (auto &m : F.monos) nfac += (int)m.size();
+    if (nfac > FMAXF) return false;
+    const int nw = (int)F.wcols.size();
+    for (auto &pd : pend) {
+      const ItemD &it = pd.it;
+      if (pd.kind == 0) {
+        DCombItem c{};
+        c.psi = it.psi;
+        c.block = -1;
+        c.integral = it.integral;
+        if (it.integral) {
+          int pos = -1;
+          for (size_t i = 0; i < F.int0.size(); ++i)
+            if (F.int0[i].first == pd.j && F.int0[i].second == pd.w) pos = (int)i;
+          if (pos < 0) {
+            if ((int)F.int0.size() >= NI0_MAX) return false;
+            F.int0.push_back({pd.j, pd.w});
+            pos = (int)F.int0.size() - 1;
+          }
+          c.col = pos;
+        } else {
+          c.col = pd.j * nw + pd.w;
+        }
+        c.og0 = add_grefs(it.og);
+        c.nog = (int)it.og.size();
+        c.out = it.out;
+        c.cellmul = it.cellmul;
+        P.comb.push_back(c);
+      } else if (pd.kind == 1) {
+        auto &S = F.b1[pd.set];
+        auto &cols = it.integral ? S.icols : S.fcols;
+        int pos = -1;
+        for (size_t i = 0; i < cols.size(); ++i) if (cols[i].first == pd.j && cols[i].second == pd.w) pos = (int)i;
+        if (pos < 0) {
+          if ((int)cols.size() >= FMAXC) return false;
+          cols.push_back({pd.j, pd.w});
+          pos = (int)cols.size() - 1;
+        }
+        DCombItem c{};
+        c.psi = it.psi;
+        c.block = pd.set;
+        c.integral = it.integral;
+        c.col = pos;
+        c.og0 = add_grefs(it.og);
+        c.nog = (int)it.og.size();
+        c.ig0 = add_grefs(it.ig);
+        c.nig = (int)it.ig.size();
+        c.out = it.out;
+        c.cellmul = it.cellmul;
+        P.comb.push_back(c);
+      } else {
+        int pos = -1;
+        for (size_t i = 0; i < F.p3.size(); ++i) if (F.p3[i].first == pd.j && F.p3[i].second == it.integral) pos = (int)i;
+        if (pos < 0) {
+          if ((int)F.p3.size() >= FMAXC) return false;
+          F.p3.push_back({pd.j, it.integral});
+          pos = (int)F.p3.size() - 1;
+        }
+        DB3Item b{};
+        const View &v = P.views[P.inner[0]];
+        b.w = it.integral ? pd.w : pd.w;  // FP64 view column; integral values are exact there
+        (void)v;
+        b.c = pos;
+        b.integral = it.integral;
+        b.ig0 = add_grefs(it.ig);
+        b.nig = (int)it.ig.size();
+        b.out = it.out;
+        b.cellmul = it.cellmul;
+        F.b3.push_back(b);
+      }
+    }
+    F.on = true;
+    return true;
+  }
+
+  int code_group(int r, int code) const {  // group item behind a view code
+    const CodeSpec &cs = P.views[r].codes[code];
+    if (cs.group >= 0) return cs.group;
+    return code_group(cs.child_rel, cs.child_code);
+  }
+  std::vector<float> thr_of(const DGroupRef &g) const {
+    return std::vector<float>(P.thr.begin() + g.thr0, P.thr.begin() + g.thr0 + g.nthr);
+  }
+  int64_t gdom_of_slot(const DGroupRef &g) const {  // VALUE code on a root column
+    int col = P.rowcols[g.a];
+    return R(t.root).cols[col].domain;
   }
 };
 
@@ -680,6 +877,34 @@ DViewRef view_ref(const View &v) {
 
 DCol dcol(const Column &c) { return DCol{c.dev, c.dtype}; }
 
+// Largest number of tuples per join-key value of every non-root relation, and an upper
+// bound of each view's COUNT column (the product of multiplicities down the subtree).
+void compute_multiplicities(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
+  cudaStream_t s = ctx->stream;
+  for (int r : t.post) {
+    View &v = P.views[r];
+    std::vector<DCol> kc;
+    std::vector<int64_t> st(v.keycols.size());
+    int64_t acc = 1;
+    for (int i = (int)v.keycols.size() - 1; i >= 0; --i) { st[i] = acc; acc *= v.keydom[i]; }
+    for (int c : v.keycols) kc.push_back(dcol(ctx->rels[r].cols[c]));
+    unsigned int *hist = (unsigned int *)P.arena.alloc(v.nkeys * 4 + 16);
+    unsigned int *mx = hist + v.nkeys;
+    int64_t *std_ = P.arena.upload(st, s);
+    LMFAO_CUDA(cudaMemsetAsync(hist, 0, v.nkeys * 4 + 16, s));
+    launch_key_multiplicity(kc.data(), (int)kc.size(), std_, ctx->rels[r].nrows, hist, s);
+    launch_max_u32(hist, v.nkeys, mx, s);
+    unsigned int h = 0;
+    LMFAO_CUDA(cudaMemcpyAsync(&h, mx, 4, cudaMemcpyDeviceToHost, s));
+    LMFAO_CUDA(cudaStreamSynchronize(s));
+    v.maxmult = h;
+    v.unique_keys = h <= 1;
+    double b = std::max(1u, h);
+    for (int c : t.children[r]) b *= P.views[c].count_bound;
+    v.count_bound = b;
+  }
+}
+
 void setup_views(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, bool need32) {
   cudaStream_t s = ctx->stream;
   for (int r : t.post) {
@@ -696,25 +921,6 @@ void setup_views(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, bool need32) {
     v.vint = (uint32_t *)P.arena.alloc(v.nkeys * std::max<size_t>(1, ic.size()) * 4);
     v.vcodes = (int32_t *)P.arena.alloc(v.nkeys * std::max<size_t>(1, v.codes.size()) * 4);
     int *icd = P.arena.upload(ic, s);
-    // unique keys?
-    {
-      std::vector<DCol> kc;
-      std::vector<int64_t> st(v.keycols.size());
-      int64_t acc = 1;
-      for (int i = (int)v.keycols.size() - 1; i >= 0; --i) { st[i] = acc; acc *= v.keydom[i]; }
-      for (int c : v.keycols) kc.push_back(dcol(ctx->rels[r].cols[c]));
-      unsigned int *hist = (unsigned int *)P.arena.alloc(v.nkeys * 4);
-      unsigned int *mx = (unsigned int *)P.arena.alloc(4);
-      int64_t *std_ = P.arena.upload(st, s);
-      LMFAO_CUDA(cudaMemsetAsync(hist, 0, v.nkeys * 4, s));
-      LMFAO_CUDA(cudaMemsetAsync(mx, 0, 4, s));
-      launch_key_multiplicity(kc.data(), (int)kc.size(), std_, ctx->rels[r].nrows, hist, s);
-      launch_max_u32(hist, v.nkeys, mx, s);
-      unsigned int h = 0;
-      LMFAO_CUDA(cudaMemcpyAsync(&h, mx, 4, cudaMemcpyDeviceToHost, s));
-      LMFAO_CUDA(cudaStreamSynchronize(s));
-      v.unique_keys = h <= 1;
-    }
     // kernel descriptor
     DViewKernel d{};
     const Relation &Rr = ctx->rels[r];
@@ -858,6 +1064,310 @@ void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   }
   P.nwork = (int64_t)work.size();
   P.work = P.arena.upload(work, s);
+}
+
+// Device tables of the specialised root pass and of the B3 finalisation.
+void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
+  cudaStream_t s = ctx->stream;
+  auto &F = P.fast;
+  DFast &d = P.fd;
+  d = DFast{};
+  const size_t ts = P.fp64 ? 8 : 4;
+  d.nwork = P.nwork;
+  d.work = P.work;
+  d.wseg = P.wseg;
+  d.ncols = (int)P.rowdev.size();
+  for (size_t i = 0; i < P.rowdev.size(); ++i) d.col[i] = P.rowdev[i];
+  d.ni = (int)P.inner.size();
+  std::vector<int> codecol;  // inner view code indices staged with the table
+  auto code_pos = [&](int b) {
+    for (size_t i = 0; i < codecol.size(); ++i) if (codecol[i] == b) return (int)i;
+    codecol.push_back(b);
+    return (int)codecol.size() - 1;
+  };
+  const View *iv = d.ni ? &P.views[P.inner[0]] : nullptr;
+  if (iv) {
+    DViewRef r = view_ref(*iv);
+    d.nk = (int)iv->keycols.size();
+    for (int i = 0; i < d.nk; ++i) { d.kslot[i] = P.rowslot.at(iv->pkeycols[i]); d.kstride[i] = r.kstride[i]; }
+    d.nkeys = iv->nkeys;
+  }
+  d.nw = (int)F.wcols.size();
+  // monomials
+  std::vector<int> xslot;
+  int nf = 0;
+  d.nm = (int)F.monos.size();
+  for (int j = 0; j < d.nm; ++j) {
+    d.mono_f0[j] = nf;
+    for (int f : F.monos[j]) {
+      const Fac &fc = P.facs[f];
+      int slot = P.rowslot.at(fc.col);
+      d.facs[nf] = DFac{slot, fc.ind, fc.pow, fc.op, fc.t};
+      int xi = 0;
+      if (!fc.ind) {
+        auto it = std::find(xslot.begin(), xslot.end(), slot);
+        if (it == xslot.end()) {
+          if ((int)xslot.size() >= FMAXX) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: too many fact columns");
+          xslot.push_back(slot);
+          xi = (int)xslot.size() - 1;
+        } else xi = (int)(it - xslot.begin());
+      }
+      d.fx[nf] = xi;
+      ++nf;
+    }
+    d.mono_nf[j] = (int)F.monos[j].size();
+  }
+  d.nx = (int)xslot.size();
+  for (size_t i = 0; i < xslot.size(); ++i) d.xslot[i] = xslot[i];
+  // B0
+  d.n0i = (int)F.int0.size();
+  for (int i = 0; i < d.n0i; ++i) { d.i0j[i] = F.int0[i].first; d.i0w[i] = F.int0[i].second; }
+  P.phi0f = P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * d.nm * d.nw) * ts);
+  P.phi0i = (unsigned long long *)P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * d.n0i) * 8);
+  d.phi0f = P.phi0f;
+  d.phi0i = P.phi0i;
+  // B1
+  d.nb1 = (int)F.b1.size();
+  int64_t segf = 0, segi = 0;
+  P.b1sets.clear();
+  for (int si = 0; si < d.nb1; ++si) {
+    auto &S = F.b1[si];
+    DFastB1 &b = d.b1[si];
+    b = DFastB1{};
+    b.G = (int)S.G;
+    b.nref = (int)S.refs.size();
+    int64_t radix = 1;
+    DB1Set cs{};
+    cs.G = b.G;
+    cs.nref = b.nref;
+    for (int i = b.nref - 1; i >= 0; --i) {
+      b.ref[i] = S.refs[i];
+      b.ref[i].stride = radix;
+      if (S.refs[i].src == 3) b.ref[i].b = code_pos(S.refs[i].b);
+      cs.radix[i] = radix;
+      cs.dom[i] = S.dom[i];
+      radix *= S.dom[i];
+    }
+    b.nf = (int)S.fcols.size();
+    b.ni = (int)S.icols.size();
+    for (int c = 0; c < b.nf; ++c) { b.fj[c] = S.fcols[c].first; b.fw[c] = S.fcols[c].second; }
+    for (int c = 0; c < b.ni; ++c) { b.ij[c] = S.icols[c].first; b.iw[c] = S.icols[c].second; }
+    b.smem_f = d.hist_f;
+    b.smem_i = d.hist_i;
+    d.hist_f += b.G * b.nf;
+    d.hist_i += b.G * b.ni;
+    b.gbase_f = segf;
+    b.gbase_i = segi;
+    cs.nf = b.nf;
+    cs.ni = b.ni;
+    cs.gbase_f = segf;
+    cs.gbase_i = segi;
+    segf += (int64_t)b.G * b.nf;
+    segi += (int64_t)b.G * b.ni;
+    P.b1sets.push_back(cs);
+  }
+  d.phi1f_seg = segf;
+  d.phi1i_seg = segi;
+  if ((double)P.nseg * (segf + segi) * 4 > 6e9) throw Error(LMFAO_ERR_UNSUPPORTED, "grouped per-segment sums exceed 6 GB");
+  d.phi1f = (float *)P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * segf) * 4);
+  d.phi1i = (unsigned int *)P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * segi) * 4);
+  // B3
+  d.n3 = (int)F.p3.size();
+  for (int c = 0; c < d.n3; ++c) { d.j3[c] = F.p3[c].first; d.int3[c] = F.p3[c].second ? 1 : 0; }
+  int64_t nk3 = std::max<int64_t>(1, d.nkeys);
+  d.p3f = (double *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3) * 8);
+  d.p3i = (unsigned long long *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3) * 8);
+  d.thr = cb.thr;
+  // inner view table (staged per run by fast_prep) and codes
+  for (auto &b3 : F.b3) (void)b3;
+  d.ncode = (int)codecol.size();
+  void *table = P.arena.alloc((size_t)nk3 * std::max(1, d.nw) * ts);
+  int *codes = (int *)P.arena.alloc((size_t)nk3 * std::max(1, d.ncode) * 4);
+  d.table = table;
+  d.codes = codes;
+  P.fwcol_dev = P.arena.upload(F.wcols, s);
+  P.fcodecol_dev = P.arena.upload(codecol.empty() ? std::vector<int>{0} : codecol, s);
+  // shared memory: the table and the B3 partials when they fit (1 CTA of 512 threads per SM)
+  P.fast_block = 512;
+  size_t pbytes = d.n3 ? (ts + 4) * (size_t)d.nkeys * d.n3 : 0;
+  size_t vbytes = d.ni ? ts * (size_t)d.nkeys * d.nw + 4 * (size_t)d.nkeys * d.ncode : 0;
+  size_t hbytes = (size_t)(P.fast_block / 32) * (d.hist_f + d.hist_i) * 4;
+  if (hbytes > 96 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: group histograms too large");
+  d.smem_p = d.n3 && pbytes + hbytes <= 190 * 1024 ? 1 : 0;
+  d.smem_view = d.ni && vbytes + (d.smem_p ? pbytes : 0) + hbytes <= 190 * 1024 ? 1 : 0;
+  size_t sm = fast_smem(d, P.fp64, P.fast_block);
+  P.fast_grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm > 100 * 1024 ? 148 : 296, (P.nwork + 15) / 16));
+  // B3 finalisation
+  DB3Final &f = P.b3f;
+  f = DB3Final{};
+  if (iv) {
+    f.nkeys = iv->nkeys;
+    f.v64 = iv->v64;
+    f.vcols = (int)iv->cols.size();
+    f.vcodes = iv->vcodes;
+    f.vncodes = (int)iv->codes.size();
+  }
+  f.p3f = d.p3f;
+  f.p3i = d.p3i;
+  f.n3 = d.n3;
+  f.nitems = (int)F.b3.size();
+  f.items = P.arena.upload(F.b3, s);
+  f.grefs = cb.grefs;
+  f.fsum = P.fsum;
+  f.icnt = P.icnt;
+  // combine reads the specialised PHI layout
+  cb.n0f = d.nm * d.nw;
+  cb.n0i = d.n0i;
+  cb.phi0f = P.phi0f;
+  cb.phi0i = P.phi0i;
+  cb.nsets = (int)P.b1sets.size();
+  cb.sets = P.arena.upload(P.b1sets, s);
+  cb.phi1f = d.phi1f;
+  cb.phi1i = d.phi1i;
+  cb.phi1f_seg = segf;
+  cb.phi1i_seg = segi;
+  (void)t;
+}
+
+// Entries, staged columns and outer-cell sets of the combine (combine.cu).
+void setup_combine2(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPart> &pparts) {
+  cudaStream_t s = ctx->stream;
+  const DCombine &cb = P.cb;
+  DComb2 &d = P.c2;
+  d = DComb2{};
+  d.nseg = P.nseg;
+  d.wseg = P.wseg;
+  d.seg = cb.seg;
+  d.nouter = cb.nouter;
+  for (int i = 0; i < cb.nouter; ++i) d.outer[i] = cb.outer[i];
+  // staged outer view columns
+  std::vector<int2> stage;
+  std::vector<int> psi_stage;
+  for (const DPart &pp : pparts) {
+    int at = -1;
+    for (size_t i = 0; i < stage.size(); ++i)
+      if (stage[i].x == pp.branch && stage[i].y == pp.col) at = (int)i;
+    if (at < 0) { stage.push_back(make_int2(pp.branch, pp.col)); at = (int)stage.size() - 1; }
+    psi_stage.push_back(at);
+  }
+  d.nstage = (int)stage.size();
+  d.stage_col = P.arena.upload(stage.empty() ? std::vector<int2>{make_int2(0, 0)} : stage, s);
+  d.npsi = cb.npsi;
+  d.psi = cb.psi;
+  d.segfacs = cb.segfacs;
+  d.psi_stage = P.arena.upload(psi_stage.empty() ? std::vector<int>{0} : psi_stage, s);
+  // outer-cell sets
+  std::vector<std::vector<DGroupRef>> ogs{{}};
+  auto same = [](const DGroupRef &a, const DGroupRef &b) {
+    return a.src == b.src && a.a == b.a && a.b == b.b && a.stride == b.stride;
+  };
+  auto og_of = [&](const DCombItem &it) {
+    std::vector<DGroupRef> g(P.grefs.begin() + it.og0, P.grefs.begin() + it.og0 + it.nog);
+    for (size_t i = 0; i < ogs.size(); ++i) {
+      if (ogs[i].size() != g.size()) continue;
+      bool eq = true;
+      for (size_t j = 0; j < g.size(); ++j) eq = eq && same(ogs[i][j], g[j]);
+      if (eq) return (int)i;
+    }
+    ogs.push_back(g);
+    return (int)ogs.size() - 1;
+  };
+  // Y columns
+  d.n0f = cb.n0f;
+  d.n0i = cb.n0i;
+  int64_t segf = P.fast.on ? P.fd.phi1f_seg : 0, segi = P.fast.on ? P.fd.phi1i_seg : 0;
+  d.nyf = (int)(d.n0f + segf);
+  d.nyi = (int)(d.n0i + segi);
+  d.phi0f = cb.phi0f;
+  d.phi0i = cb.phi0i;
+  d.phi1f = P.fast.on ? P.fd.phi1f : nullptr;
+  d.phi1i = P.fast.on ? P.fd.phi1i : nullptr;
+  d.phi1f_seg = segf;
+  d.phi1i_seg = segi;
+  // mirrors: query output regions of entries whose cell varies, while they fit
+  std::vector<DMirror> mirrors;
+  std::map<int64_t, int> fmir, imir;
+  int fcells = 0, icells = 0;
+  const int budget = 10 * 1024;
+  auto mirror_of = [&](const DCombItem &it) -> int {
+    if (it.nog == 0 && it.block < 0) return -1;
+    for (auto &q : P.qout) {
+      int64_t base = it.integral ? q.io : q.fo;
+      int64_t len = it.integral ? q.cells * (1 + q.naggs) : q.cells * q.naggs;
+      if (it.out < base || it.out >= base + len) continue;
+      auto &mp = it.integral ? imir : fmir;
+      int &cells = it.integral ? icells : fcells;
+      auto f = mp.find(base);
+      if (f == mp.end()) {
+        if (cells + len > budget) return -1;
+        mp[base] = cells;
+        mirrors.push_back(DMirror{base, cells, (int)len, it.integral, 0});
+        f = mp.find(base);
+        cells += (int)len;
+      }
+      return f->second + (int)(it.out - base);
+    }
+    return -1;
+  };
+  std::vector<DEntry> ent;
+  for (const DCombItem &it : P.comb) {
+    int og = og_of(it);
+    int so = mirror_of(it);
+    if (it.block < 0) {
+      DEntry e{};
+      e.psi = it.psi;
+      e.ycol = it.col;
+      e.og = og;
+      e.integral = it.integral;
+      e.so = so;
+      e.out = it.out;
+      e.cellmul = it.cellmul;
+      e.icell = 0;
+      ent.push_back(e);
+    } else {
+      const DB1Set &S = P.b1sets[it.block];
+      for (int g = 0; g < S.G; ++g) {
+        DEntry e{};
+        e.psi = it.psi;
+        e.ycol = it.integral ? (int)(d.n0i + S.gbase_i + (int64_t)g * S.ni + it.col)
+                             : (int)(d.n0f + S.gbase_f + (int64_t)g * S.nf + it.col);
+        e.og = og;
+        e.integral = it.integral;
+        e.so = so;
+        e.out = it.out;
+        e.cellmul = it.cellmul;
+        int64_t ic = 0;
+        for (int i = 0; i < S.nref; ++i) ic += ((g / S.radix[i]) % S.dom[i]) * P.grefs[it.ig0 + i].stride;
+        e.icell = ic;
+        ent.push_back(e);
+      }
+    }
+  }
+  std::vector<int> og_off{0};
+  std::vector<DGroupRef> og_refs;
+  for (auto &g : ogs) {
+    og_refs.insert(og_refs.end(), g.begin(), g.end());
+    og_off.push_back((int)og_refs.size());
+  }
+  d.nog = (int)ogs.size();
+  d.og_off = P.arena.upload(og_off, s);
+  d.grefs = P.arena.upload(og_refs.empty() ? std::vector<DGroupRef>{DGroupRef{}} : og_refs, s);
+  d.nent = (int)ent.size();
+  d.ent = P.arena.upload(ent.empty() ? std::vector<DEntry>{DEntry{}} : ent, s);
+  d.nmirror = (int)mirrors.size();
+  d.mirror = P.arena.upload(mirrors.empty() ? std::vector<DMirror>{DMirror{}} : mirrors, s);
+  d.mirror_f = fcells;
+  d.mirror_i = icells;
+  d.fsum = P.fsum;
+  d.icnt = P.icnt;
+  d.tile = 16;
+  while (d.tile > 1 && combine2_smem(d, P.fp64) > 200 * 1024) d.tile /= 2;
+  if (combine2_smem(d, P.fp64) > 220 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "combine needs too much shared memory");
+  P.c2_block = 512;
+  size_t sm = combine2_smem(d, P.fp64);
+  int per_sm = sm > 110 * 1024 ? 1 : 2;
+  int64_t ranges = std::max<int64_t>(1, std::min<int64_t>(148 * per_sm, (P.nseg + d.tile - 1) / d.tile));
+  P.c2_grid = (int)ranges;
 }
 
 void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
@@ -1018,6 +1528,7 @@ void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   cb.thr = fp.thr;
   cb.fsum = P.fsum;
   cb.icnt = P.icnt;
+  if (P.fast.on) setup_fast(ctx, P, t, cb);
   // mirror outputs of queries with outer-grouped items in shared memory while they fit
   std::vector<int> item_smem(P.comb.size(), -1);
   std::vector<DMirror> mirrors;
@@ -1026,7 +1537,7 @@ void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   const int budget_cells = 12 * 1024;
   for (size_t i = 0; i < P.comb.size(); ++i) {
     const DCombItem &it = P.comb[i];
-    if (it.nog == 0) continue;
+    if (it.nog == 0 && it.block < 0) continue;
     // find the query owning this output
     for (auto &q : P.qout) {
       int64_t base = it.integral ? q.io : q.fo;
@@ -1053,11 +1564,11 @@ void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   cb.mirror = P.arena.upload(mirrors, s);
   cb.tile = 32;
   while (cb.tile > 1 && combine_smem(cb, P.fp64) > 200 * 1024) cb.tile /= 2;
-  if (combine_smem(cb, P.fp64) > 200 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "combine needs too much shared memory");
   P.cb_smem = combine_smem(cb, P.fp64);
   P.cb_block = 256;
   int64_t ntiles = (P.nseg + cb.tile - 1) / cb.tile;
   P.cb_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 2));
+  setup_combine2(ctx, P, pparts);
   (void)t;
 }
 
@@ -1079,8 +1590,8 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   LMFAO_CUDA(cudaMemsetAsync(P.err, 0, 4, s));
   if (P.nfsum) LMFAO_CUDA(cudaMemsetAsync(P.fsum, 0, P.nfsum * 8, s));
   if (P.nicnt) LMFAO_CUDA(cudaMemsetAsync(P.icnt, 0, P.nicnt * 8, s));
-  if (!P.b0f.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * P.b0f.size() * (P.fp64 ? 8 : 4), s));
-  if (!P.b0i.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * P.b0i.size() * 8, s));
+  if (!P.fast.on && !P.b0f.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * P.b0f.size() * (P.fp64 ? 8 : 4), s));
+  if (!P.fast.on && !P.b0i.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * P.b0i.size() * 8, s));
   mark("memset");
   for (size_t i = 0; i < P.vk.size(); ++i) {
     int r = P.vk_rel[i];
@@ -1093,9 +1604,31 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   }
   launch_segment_weights(P.sw, s);
   mark("segment_weights");
-  launch_fact_pass(P.fp, P.fp64, P.nb0, P.fp_grid, P.fp_block, s);
-  mark("fact_pass");
-  if (!P.comb.empty()) launch_combine(P.cb, P.fp64, P.cb_grid, P.cb_block, P.cb_smem, s);
+  if (P.fast.on) {
+    const DFast &d = P.fd;
+    if (d.nm * d.nw) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * d.nm * d.nw * (P.fp64 ? 8 : 4), s));
+    if (d.n0i) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * d.n0i * 8, s));
+    if (d.phi1f_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1f, 0, P.nseg * d.phi1f_seg * 4, s));
+    if (d.phi1i_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1i, 0, P.nseg * d.phi1i_seg * 4, s));
+    if (d.n3) {
+      LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3 * 8, s));
+      LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3 * 8, s));
+    }
+    if (d.ni) {
+      const View &v = P.views[P.inner[0]];
+      launch_fast_prep(d, v.v64, (int)v.cols.size(), P.fwcol_dev, v.vcodes, (int)v.codes.size(), P.fcodecol_dev,
+                       const_cast<void *>(d.table), const_cast<int *>(d.codes), P.fp64, s);
+    }
+    if (!launch_fast_pass(d, P.fp64, P.fast_grid, P.fast_block, s))
+      throw Error(LMFAO_ERR_UNSUPPORTED, "internal: no root-pass variant for this shape");
+    mark("fact_pass");
+    if (P.b3f.nitems) launch_b3_final(P.b3f, s);
+    mark("b3_final");
+  } else {
+    launch_fact_pass(P.fp, P.fp64, P.nb0, P.fp_grid, P.fp_block, s);
+    mark("fact_pass");
+  }
+  if (!P.comb.empty()) launch_combine2(P.c2, P.fp64, P.c2_grid, P.c2_block, s);
   mark("combine");
   LMFAO_CUDA(cudaGetLastError());
   (void)t;
@@ -1382,13 +1915,22 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
     PhysPlan *P = new PhysPlan();
     ctx->plan = P;
     P->fp64 = o.precision == LMFAO_FP64;
-    P->mode = o.mode == LMFAO_MODE_PER_TUPLE ? LMFAO_MODE_PER_TUPLE : LMFAO_MODE_FACTORISED;
+    P->mode = (o.mode == LMFAO_MODE_PER_TUPLE || o.mode == LMFAO_MODE_GENERIC) ? o.mode : LMFAO_MODE_FACTORISED;
     P->root = root;
     P->err = (int *)P->arena.alloc(16);
     Planner pl(ctx, *P, ctx->tree);
     pl.init_views();
+    compute_multiplicities(ctx, *P, ctx->tree);
     pl.choose_segments(o);
-    pl.build_items(P->mode);
+    {
+      auto items = pl.decompose();
+      if (!(P->mode == LMFAO_MODE_FACTORISED && pl.route_fast(items))) {
+        P->fast = PhysPlan::Fast{};
+        P->comb.clear();
+        P->grefs.resize(P->grefs.size());
+        pl.route_generic(items, P->mode);
+      }
+    }
     // inner branch keys are read per tuple
     for (int c : P->inner)
       for (int pc : P->views[c].pkeycols) pl.rowslot(pc);
@@ -1563,7 +2105,8 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
     o << "],\"inner\":[";
     for (size_t i = 0; i < P.inner.size(); ++i) o << (i ? "," : "") << nm(P.inner[i]);
     o << "],\"precision\":\"" << (P.fp64 ? "fp64" : "fp32") << "\",\"mode\":\""
-      << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : "factorised") << "\",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
+      << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : P.fast.on ? "factorised" : "generic")
+      << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false") << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
       << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows

@@ -128,6 +128,8 @@ struct View {
   std::vector<int> intcol;     // view column -> integral column index (-1 if not integral)
   int nint = 0;
   bool unique_keys = false;    // every key value occurs at most once in the relation
+  unsigned int maxmult = 0;    // largest number of tuples sharing one key value
+  double count_bound = 1;      // upper bound of the COUNT column (product over the subtree)
   // device storage
   double *v64 = nullptr;      // nkeys x ncols
   float *v32 = nullptr;       // nkeys x ncols (FP32 copy for FP32 passes)

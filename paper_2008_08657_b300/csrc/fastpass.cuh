@@ -1,0 +1,113 @@
+// Specialised root pass for plans with at most one inner child of the root.
+//
+// Per tuple r of segment s (Fig. 3 with two loop levels, segment key outside, tuple inside):
+//   u_j(r)  monomials over the root's own attributes (j < nm),
+//   v_w(r)  the inner view row V_I[k_I(r)] restricted to the nw columns the batch needs,
+//   B0:     PHI0[s][j][w]  += u_j * v_w                 (registers; warp sum per work item)
+//   B1:     PHI1[s][g][c]  += u_j(c) * v_w(c)          (per-warp shared histogram per segment,
+//                                                       g = inner group code of the tuple)
+//   B3:     P[k_I][c]      += w_s * u_j(c)             (CTA-private shared partials; this is the
+//                                                       view from the root to the inner relation,
+//                                                       V_{S->I} of Fig. 2, w_s the outer weight)
+#pragma once
+
+#include "kernels.cuh"
+
+namespace lmfao {
+
+constexpr int FMAXM = 16;   // monomials
+constexpr int FMAXW = 8;    // inner view columns
+constexpr int FMAXF = 24;   // factors of all monomials
+constexpr int FMAXB1 = 4;   // B1 group sets
+constexpr int FMAXC = 8;    // columns per B1 set / B3 columns
+constexpr int FMAXX = 6;    // root columns read per tuple (fact values and group columns)
+
+struct DFastB1 {
+  int G;                 // cells of the group set
+  int nref;              // group refs (src 2: root column slot; src 3: inner view code)
+  DGroupRef ref[2];      // stride = radix inside the set
+  int nf, ni;            // float / integral columns
+  int fj[FMAXC], fw[FMAXC];
+  int ij[FMAXC], iw[FMAXC];
+  int smem_f, smem_i;    // offsets of this set inside a warp's histogram (floats / u32)
+  int64_t gbase_f, gbase_i;  // offsets in phi1f / phi1i (per segment: G x nf / G x ni)
+};
+
+struct DFast {
+  int64_t nwork;
+  const DWork *work;
+  const unsigned long long *wseg;
+  int ncols;
+  DCol col[MAXRC];
+  // inner branch
+  int ni;                 // 0 or 1
+  int nk;
+  int kslot[2];
+  int64_t kstride[2];
+  int64_t nkeys;
+  int nw;                 // inner view columns used (column 0: COUNT)
+  int ncode;              // inner view codes used (B1 / B3 groups)
+  const void *table;      // [nkeys][nw] in T (prepared by fast_prep_kernel)
+  const int *codes;       // [nkeys][ncode]
+  int smem_view;          // stage table and codes in shared memory
+  // monomials
+  int nm;
+  int mono_f0[FMAXM], mono_nf[FMAXM];
+  DFac facs[FMAXF];
+  int nx;                 // root columns whose values feed the monomials
+  int xslot[FMAXX];
+  int fx[FMAXF];          // factor -> index into the loaded values
+  // B0
+  void *phi0f;            // [nseg][nm*nw]
+  unsigned long long *phi0i;  // [nseg][n0i]
+  int n0i;
+  int i0j[NI0_MAX], i0w[NI0_MAX];
+  // B1
+  int nb1;
+  DFastB1 b1[FMAXB1];
+  int hist_f, hist_i;     // per-warp histogram sizes (floats, u32)
+  float *phi1f;
+  unsigned int *phi1i;
+  int64_t phi1f_seg, phi1i_seg;  // per-segment stride
+  // B3
+  int n3;
+  int j3[FMAXC];
+  int int3[FMAXC];
+  int smem_p;             // P in shared memory (else global atomics)
+  double *p3f;            // [nkeys][n3]
+  unsigned long long *p3i;
+  const float *thr;
+};
+
+void launch_fast_prep(const DFast &d, const double *v64, int vcols, const int *wcol, const int32_t *vcodes,
+                      int vncodes, const int *codecol, void *table, int *codes, bool fp64, cudaStream_t s);
+size_t fast_smem(const DFast &d, bool fp64, int block);
+bool launch_fast_pass(const DFast &d, bool fp64, int grid, int block, cudaStream_t s);
+bool fast_shape_ok(int nm, int nw);  // a kernel variant exists for nm monomials x nw view columns
+
+// B3 finalisation: out[cell(k)] += V[k][w] * P[k][c] over the inner relation's keys.
+struct DB3Item {
+  int w;          // view column (FP64 view)
+  int c;          // P column
+  int integral;
+  int ig0, nig;   // group refs (src 3: view code index)
+  int64_t out, cellmul;
+};
+struct DB3Final {
+  int64_t nkeys;
+  const double *v64;
+  int vcols;
+  const int32_t *vcodes;
+  int vncodes;
+  const double *p3f;
+  const unsigned long long *p3i;
+  int n3;
+  int nitems;
+  const DB3Item *items;
+  const DGroupRef *grefs;
+  double *fsum;
+  unsigned long long *icnt;
+};
+void launch_b3_final(const DB3Final &d, cudaStream_t s);
+
+}  // namespace lmfao

@@ -410,6 +410,37 @@ __global__ void __launch_bounds__(256) combine_kernel(DCombine d) {
     for (int it = tid; it < d.nitems; it += bs) {
       const DCombItem item = d.items[it];
       const int so = d.item_smem[it];
+      if (item.block >= 0) {  // B1: per-segment sums grouped by the inner group codes
+        const DB1Set S = d.sets[item.block];
+        for (int s = 0; s < TS; ++s) {
+          int64_t seg = seg0 + s;
+          if (seg >= d.nseg) break;
+          T pf = psif[s * d.npsi + item.psi];
+          unsigned long long pi = psii[s * d.npsi + item.psi];
+          if (item.integral ? (pi == 0) : (pf == T(0))) continue;
+          bool ok = true;
+          int64_t oc = item.nog ? outer_cell(d.grefs + item.og0, item.nog, d.outer, d.seg, seg, ok) : 0;
+          if (!ok) continue;
+          for (int g = 0; g < S.G; ++g) {
+            int64_t cell = oc;
+            for (int i = 0; i < S.nref; ++i) cell += ((g / S.radix[i]) % S.dom[i]) * d.grefs[item.ig0 + i].stride;
+            if (item.integral) {
+              unsigned int ph = d.phi1i[seg * d.phi1i_seg + S.gbase_i + (int64_t)g * S.ni + item.col];
+              if (!ph) continue;
+              unsigned long long v = pi * ph;
+              if (so >= 0) atomicAdd(outi + so + cell * item.cellmul, v);
+              else atomicAdd(d.icnt + item.out + cell * item.cellmul, v);
+            } else {
+              float ph = d.phi1f[seg * d.phi1f_seg + S.gbase_f + (int64_t)g * S.nf + item.col];
+              if (ph == 0.f) continue;
+              T v = pf * (T)ph;
+              if (so >= 0) atomicAdd(outf + so + cell * item.cellmul, v);
+              else atomic_add_out<T>(d.fsum + item.out + cell * item.cellmul, v);
+            }
+          }
+        }
+        continue;
+      }
       for (int s = 0; s < TS; ++s) {
         int64_t seg = seg0 + s;
         if (seg >= d.nseg) break;
@@ -442,6 +473,7 @@ __global__ void __launch_bounds__(256) combine_kernel(DCombine d) {
   __syncthreads();
   for (int it = tid; it < d.nitems; it += bs) {
     const DCombItem item = d.items[it];
+    if (item.block >= 0) continue;
     if (item.integral) { if (acci[it]) atomicAdd(d.icnt + item.out, acci[it]); }
     else if (accf[it] != T(0)) atomic_add_out<T>(d.fsum + item.out, accf[it]);
   }

@@ -75,6 +75,14 @@ struct DFactPass {
 // A query output region mirrored in shared memory by the combine (CTA-private sums).
 struct DMirror { long long gout; int soff; int len; int integral; int pad; };
 
+// A B1 block of per-segment sums grouped by inner group codes.
+struct DB1Set {
+  int G, nref;
+  int64_t radix[2], dom[2];
+  int nf, ni;
+  int64_t gbase_f, gbase_i;
+};
+
 struct DCombine {
   int64_t nseg;
   const unsigned long long *wseg;
@@ -96,10 +104,55 @@ struct DCombine {
   int smem_fcells, smem_icells;
   int nmirror;
   const DMirror *mirror;
+  int nsets;
+  const DB1Set *sets;
+  const float *phi1f;
+  const unsigned int *phi1i;
+  int64_t phi1f_seg, phi1i_seg;
   double *fsum;
   unsigned long long *icnt;
   int tile;
 };
+
+// One output entry of the combine: psi term x one Y column, written to
+// out + (outer cell + icell) * cellmul.
+struct DEntry {
+  int psi, ycol, og, integral, so, pad;
+  long long out, cellmul, icell;
+};
+
+struct DComb2 {
+  int64_t nseg;
+  const unsigned long long *wseg;
+  DSegment seg;
+  int nouter;
+  DOuter outer[MAXOUT];
+  int nstage;
+  const int2 *stage_col;  // (outer view, column) staged per segment
+  int npsi;
+  const DPsi *psi;
+  const DSegFac *segfacs;
+  const int *psi_stage;   // psi parts -> staged column
+  int nog;
+  const int *og_off;      // outer-cell sets (CSR over grefs)
+  const DGroupRef *grefs;
+  int n0f, n0i, nyf, nyi;
+  const void *phi0f;
+  const unsigned long long *phi0i;
+  const float *phi1f;
+  const unsigned int *phi1i;
+  int64_t phi1f_seg, phi1i_seg;
+  int nent;
+  const DEntry *ent;
+  int nmirror;
+  const DMirror *mirror;
+  int mirror_f, mirror_i;
+  double *fsum;
+  unsigned long long *icnt;
+  int tile;
+};
+size_t combine2_smem(const DComb2 &d, bool fp64);
+void launch_combine2(const DComb2 &d, bool fp64, int grid, int block, cudaStream_t s);
 
 struct DSegWeight {
   int64_t nseg;

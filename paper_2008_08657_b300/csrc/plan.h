@@ -3,7 +3,7 @@
 
 #include <set>
 
-#include "kernels.cuh"
+#include "fastpass.cuh"
 
 namespace lmfao {
 
@@ -89,6 +89,28 @@ struct PhysPlan {
   std::vector<DGroupRef> grefs;
   std::vector<float> thr;
   int nb0 = 4;
+  // specialised root pass (at most one inner child)
+  struct Fast {
+    bool on = false;
+    std::vector<std::vector<int>> monos;       // row factor lists
+    std::vector<int> wcols;                    // inner view columns (0: COUNT)
+    std::vector<std::pair<int, int>> int0;     // integral (monomial, column) pairs of PHI0
+    struct B1 {
+      std::vector<DGroupRef> refs;
+      std::vector<std::vector<float>> thrs;
+      std::vector<int64_t> dom;
+      int64_t G = 1;
+      std::vector<std::pair<int, int>> fcols, icols;
+    };
+    std::vector<B1> b1;
+    std::vector<std::pair<int, bool>> p3;      // B3 columns: (monomial, integral)
+    std::vector<DB3Item> b3;
+  } fast;
+  DFast fd{};
+  DB3Final b3f{};
+  int *fwcol_dev = nullptr, *fcodecol_dev = nullptr;
+  int fast_grid = 0, fast_block = 512;
+  std::vector<DB1Set> b1sets;
   // device
   DeviceArena arena;
   std::vector<DCol> rowdev;        // reorganised root columns (per row slot)
@@ -104,6 +126,8 @@ struct PhysPlan {
   std::vector<int> vk_rel;
   DFactPass fp{};
   DCombine cb{};
+  DComb2 c2{};
+  int c2_grid = 0, c2_block = 512;
   DSegWeight sw{};
   size_t cb_smem = 0;
   int fp_grid = 0, fp_block = 256, cb_grid = 0, cb_block = 256;

@@ -26,7 +26,7 @@ GB_VALUE, GB_BUCKET = 0, 1
 OPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3, "eq": 4, "ne": 5}
 PRECISION = {"fp64": 0, "fp32": 1, "split_tf32": 2}
 PLANNER = {"heuristic": 0, "exhaustive": 1, "learned": 2, "forced": 3}
-MODE = {"auto": 0, "factorised": 1, "per_tuple": 2}
+MODE = {"auto": 0, "factorised": 1, "per_tuple": 2, "generic": 3}
 ROLE = {"key": KEY, "cat": CAT, "cont": CONT}
 
 # The C entry points of include/lmfao.h (checked by the tests against the header).

@@ -29,7 +29,7 @@ def run_engine(rels, qs, **plan):
 
 @pytest.mark.parametrize("seed", range(16))
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("mode", ["factorised", "per_tuple"])
+@pytest.mark.parametrize("mode", ["factorised", "generic", "per_tuple"])
 @pytest.mark.parametrize("segment", [None, "R1", "R2", "R4"])
 def test_tiny_schemas_match_oracle(seed, precision, mode, segment):
     shared3 = seed % 2 == 1
@@ -58,22 +58,24 @@ def test_star_config_full_size(precision):
     assert got[0]["counts"][0] == 200_000
 
 
-def test_retailer_scaled():
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_retailer_scaled(precision):
     rels = W.retailer_schema(n_fact=300_000)
     qs = W.retailer_batch()
     ref = O.evaluate(rels, qs)
-    got, info = run_engine(rels, qs, precision="fp32")
+    got, info = run_engine(rels, qs, precision=precision)
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"query {i}")
 
 
-def test_favorita_scaled_fig2_tree():
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_favorita_scaled_fig2_tree(precision):
     rels = W.favorita_schema(n_fact=300_000)
     qs = W.favorita_batch()
     names = [R["name"] for R in rels]
     parent = [names.index(W.FAVORITA_TREE[n]) if n in W.FAVORITA_TREE else -1 for n in names]
     ref = O.evaluate(rels, qs)
-    got, info = run_engine(rels, qs, precision="fp32", join_parent=parent)
+    got, info = run_engine(rels, qs, precision=precision, join_parent=parent)
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"query {i}")
 
@@ -82,7 +84,8 @@ def test_plan_invariance_retailer():
     rels = W.retailer_schema(n_fact=200_000)
     qs = W.retailer_batch()[:4]
     base, _ = run_engine(rels, qs, precision="fp32")
-    for plan in ({"segment": None}, {"segment": "Location"}, {"mode": "per_tuple"}, {"precision": "fp64"}):
+    for plan in ({"segment": None}, {"segment": "Location"}, {"mode": "per_tuple"}, {"mode": "generic"},
+                 {"precision": "fp64"}):
         kw = {"precision": "fp32", **plan}
         other, _ = run_engine(rels, qs, **kw)
         for q, a, b in zip(qs, base, other):
