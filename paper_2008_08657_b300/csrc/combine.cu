@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(512) combine2_kernel(DComb2 d) {
 
   // entries owned by this thread (chunk blockIdx.y)
   const int ebase = blockIdx.y * bs * EMAX;
-  int epsi[EMAX], ey[EMAX], eog[EMAX], eint[EMAX], cur[EMAX];
+  int epsi[EMAX], ey[EMAX], eog[EMAX], eint[EMAX], eyi[EMAX], cur[EMAX];
   T accf[EMAX];
   unsigned long long acci[EMAX];
 #pragma unroll
@@ -63,9 +63,10 @@ __global__ void __launch_bounds__(512) combine2_kernel(DComb2 d) {
       ey[k] = en.ycol;
       eog[k] = en.og;
       eint[k] = en.integral;
+      eyi[k] = en.yint;
     } else {
       epsi[k] = -1;
-      ey[k] = eog[k] = eint[k] = 0;
+      ey[k] = eog[k] = eint[k] = eyi[k] = 0;
     }
     cur[k] = -1;
     accf[k] = T(0);
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(512) combine2_kernel(DComb2 d) {
           cur[k] = (int)cell;
         }
         if (eint[k]) acci[k] += psii[s * d.npsi + epsi[k]] * yi[s * d.nyi + ey[k]];
+        else if (eyi[k]) accf[k] += psif[s * d.npsi + epsi[k]] * (T)yi[s * d.nyi + ey[k]];
         else accf[k] += psif[s * d.npsi + epsi[k]] * yf[s * d.nyf + ey[k]];
       }
     }

@@ -761,11 +761,67 @@ struct Planner {
       }
       pend.push_back({it, j, wcol_of(vcol), 1, set});
     }
+    // Lean variant: root-level monomials of degree <= 2 over at most 3 value columns and no
+    // indicators. The monomial list becomes the full basis (1, x_i, x_i x_j) in the order
+    // the kernel computes it.
+    F.lean = false;
+    {
+      bool ok = P.inner.size() <= 1 && (P.inner.empty() || P.views[P.inner[0]].keycols.size() == 1);
+      std::vector<int> xcols;
+      std::vector<std::map<int, int>> exps(F.monos.size());
+      for (size_t j = 0; j < F.monos.size() && ok; ++j) {
+        int deg = 0;
+        for (int f : F.monos[j]) {
+          const Fac &fc = P.facs[f];
+          if (fc.ind) { ok = false; break; }
+          if (std::find(xcols.begin(), xcols.end(), fc.col) == xcols.end()) xcols.push_back(fc.col);
+          exps[j][fc.col] += fc.pow;
+          deg += fc.pow;
+        }
+        if (deg > 2) ok = false;
+      }
+      if (ok && xcols.size() <= 3) {
+        std::vector<std::map<int, int>> basis{{}};
+        for (int c : xcols) basis.push_back({{c, 1}});
+        for (size_t a = 0; a < xcols.size(); ++a)
+          for (size_t b = a; b < xcols.size(); ++b) {
+            std::map<int, int> e;
+            e[xcols[a]] += 1;
+            e[xcols[b]] += 1;
+            basis.push_back(e);
+          }
+        std::vector<int> remap(F.monos.size());
+        for (size_t j = 0; j < F.monos.size(); ++j)
+          remap[j] = (int)(std::find(basis.begin(), basis.end(), exps[j]) - basis.begin());
+        std::vector<std::vector<int>> bm;
+        for (auto &e : basis) {
+          std::vector<int> fs;
+          for (int c : xcols)  // first-order factors first so the kernel's column order is xcols
+            for (int q = 0; q < (e.count(c) ? e.at(c) : 0); ++q) {
+              Fac f;
+              f.rel = t.root;
+              f.col = c;
+              fs.push_back(fac_id(f));
+            }
+          bm.push_back(fs);
+        }
+        F.monos = bm;
+        for (auto &pd : pend) pd.j = remap[pd.j];
+        F.lean = true;
+        F.lean_cols = xcols;
+      }
+    }
     if (F.monos.size() > FMAXM || F.wcols.size() > FMAXW) return false;
-    if (!fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return false;
+    if (!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return false;
     int nfac = 0;
-    for (auto &m : F.monos) nfac += (int)m.size();
-    if (nfac > FMAXF) return false;
+    std::set<int> xcols;
+    for (auto &m : F.monos)
+      for (int f : m) {
+        if (P.facs[f].ind) ++nfac;
+        else xcols.insert(P.facs[f].col);
+      }
+    if (nfac > FMAXF || (int)xcols.size() > FMAXX) return false;
+    if (P.inner.size() == 1 && P.views[P.inner[0]].nkeys * (int64_t)F.wcols.size() >= (int64_t(1) << 31)) return false;
     const int nw = (int)F.wcols.size();
     for (auto &pd : pend) {
       const ItemD &it = pd.it;
@@ -794,7 +850,14 @@ struct Planner {
         P.comb.push_back(c);
       } else if (pd.kind == 1) {
         auto &S = F.b1[pd.set];
-        auto &cols = it.integral ? S.icols : S.fcols;
+        // the column kind follows the column (an inner COUNT is integral even when the
+        // outer factor of the item is not)
+        bool mono_int = true;
+        for (int f : F.monos[pd.j]) mono_int = mono_int && P.facs[f].ind;
+        // with no inner child the tuple's view row is the constant COUNT 1 (integral)
+        const bool colint =
+            mono_int && (P.inner.empty() ? F.wcols[pd.w] == 0 : P.views[P.inner[0]].cols[F.wcols[pd.w]].integral);
+        auto &cols = colint ? S.icols : S.fcols;
         int pos = -1;
         for (size_t i = 0; i < cols.size(); ++i) if (cols[i].first == pd.j && cols[i].second == pd.w) pos = (int)i;
         if (pos < 0) {
@@ -806,6 +869,7 @@ struct Planner {
         c.psi = it.psi;
         c.block = pd.set;
         c.integral = it.integral;
+        c.yint = colint ? 1 : 0;
         c.col = pos;
         c.og0 = add_grefs(it.og);
         c.nog = (int)it.og.size();
@@ -834,6 +898,15 @@ struct Planner {
         b.cellmul = it.cellmul;
         F.b3.push_back(b);
       }
+    }
+    if (F.lean) {
+      for (auto &S : F.b1)
+        if (S.refs.size() != 1 || S.refs[0].src != 3 || !S.fcols.empty() || S.icols.size() != 1 ||
+            S.icols[0].first != 0 || S.icols[0].second != 0)
+          F.lean = false;
+      for (auto &c : F.p3)
+        if (c.second && c.first != 0) F.lean = false;
+      if (!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return false;
     }
     F.on = true;
     return true;
@@ -1093,29 +1166,33 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
     d.nkeys = iv->nkeys;
   }
   d.nw = (int)F.wcols.size();
-  // monomials
+  // monomials as exponent tables over the loaded root columns, plus indicator factors
   std::vector<int> xslot;
-  int nf = 0;
   d.nm = (int)F.monos.size();
+  std::memset(d.mexp, 0, sizeof(d.mexp));
+  d.nind = 0;
   for (int j = 0; j < d.nm; ++j) {
-    d.mono_f0[j] = nf;
     for (int f : F.monos[j]) {
       const Fac &fc = P.facs[f];
       int slot = P.rowslot.at(fc.col);
-      d.facs[nf] = DFac{slot, fc.ind, fc.pow, fc.op, fc.t};
-      int xi = 0;
-      if (!fc.ind) {
-        auto it = std::find(xslot.begin(), xslot.end(), slot);
-        if (it == xslot.end()) {
-          if ((int)xslot.size() >= FMAXX) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: too many fact columns");
-          xslot.push_back(slot);
-          xi = (int)xslot.size() - 1;
-        } else xi = (int)(it - xslot.begin());
+      if (fc.ind) {
+        if (d.nind >= FMAXF) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: too many indicator factors");
+        d.ind[d.nind] = DFac{slot, 1, 1, fc.op, fc.t};
+        d.ind_mono[d.nind] = j;
+        ++d.nind;
+        continue;
       }
-      d.fx[nf] = xi;
-      ++nf;
+      auto it = std::find(xslot.begin(), xslot.end(), slot);
+      int xi;
+      if (it == xslot.end()) {
+        if ((int)xslot.size() >= FMAXX) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: too many fact columns");
+        xslot.push_back(slot);
+        xi = (int)xslot.size() - 1;
+      } else xi = (int)(it - xslot.begin());
+      int e2 = d.mexp[j][xi] + fc.pow;
+      if (e2 > 255) throw Error(LMFAO_ERR_UNSUPPORTED, "exponent too large");
+      d.mexp[j][xi] = (unsigned char)e2;
     }
-    d.mono_nf[j] = (int)F.monos[j].size();
   }
   d.nx = (int)xslot.size();
   for (size_t i = 0; i < xslot.size(); ++i) d.xslot[i] = xslot[i];
@@ -1168,15 +1245,24 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   }
   d.phi1f_seg = segf;
   d.phi1i_seg = segi;
+  d.lean = F.lean ? 1 : 0;
+  for (int si = 0; si < d.nb1; ++si) d.b1code[si] = d.b1[si].ref[0].b;
   if ((double)P.nseg * (segf + segi) * 4 > 6e9) throw Error(LMFAO_ERR_UNSUPPORTED, "grouped per-segment sums exceed 6 GB");
   d.phi1f = (float *)P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * segf) * 4);
   d.phi1i = (unsigned int *)P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * segi) * 4);
   // B3
   d.n3 = (int)F.p3.size();
-  for (int c = 0; c < d.n3; ++c) { d.j3[c] = F.p3[c].first; d.int3[c] = F.p3[c].second ? 1 : 0; }
+  d.n3f = d.n3i = 0;
+  for (int c = 0; c < d.n3; ++c) {
+    d.j3[c] = F.p3[c].first;
+    d.int3[c] = F.p3[c].second ? 1 : 0;
+    d.p3col[c] = d.int3[c] ? d.n3i++ : d.n3f++;
+  }
+  for (auto &b3 : F.b3) b3.c = d.p3col[b3.c];
   int64_t nk3 = std::max<int64_t>(1, d.nkeys);
-  d.p3f = (double *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3) * 8);
-  d.p3i = (unsigned long long *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3) * 8);
+  d.p3f = (double *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3f) * 8);
+  d.p3i = (unsigned long long *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3i) * 8);
+  d.ticket = (unsigned int *)P.arena.alloc(16);
   d.thr = cb.thr;
   // inner view table (staged per run by fast_prep) and codes
   for (auto &b3 : F.b3) (void)b3;
@@ -1188,8 +1274,8 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   P.fwcol_dev = P.arena.upload(F.wcols, s);
   P.fcodecol_dev = P.arena.upload(codecol.empty() ? std::vector<int>{0} : codecol, s);
   // shared memory: the table and the B3 partials when they fit (1 CTA of 512 threads per SM)
-  P.fast_block = 512;
-  size_t pbytes = d.n3 ? (ts + 4) * (size_t)d.nkeys * d.n3 : 0;
+  P.fast_block = P.fp64 ? 256 : 512;
+  size_t pbytes = ts * (size_t)d.nkeys * d.n3f + 4 * (size_t)d.nkeys * d.n3i;
   size_t vbytes = d.ni ? ts * (size_t)d.nkeys * d.nw + 4 * (size_t)d.nkeys * d.ncode : 0;
   size_t hbytes = (size_t)(P.fast_block / 32) * (d.hist_f + d.hist_i) * 4;
   if (hbytes > 96 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: group histograms too large");
@@ -1210,6 +1296,8 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   f.p3f = d.p3f;
   f.p3i = d.p3i;
   f.n3 = d.n3;
+  f.n3f = d.n3f;
+  f.n3i = d.n3i;
   f.nitems = (int)F.b3.size();
   f.items = P.arena.upload(F.b3, s);
   f.grefs = cb.grefs;
@@ -1329,8 +1417,9 @@ void setup_combine2(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPart> &ppart
       for (int g = 0; g < S.G; ++g) {
         DEntry e{};
         e.psi = it.psi;
-        e.ycol = it.integral ? (int)(d.n0i + S.gbase_i + (int64_t)g * S.ni + it.col)
-                             : (int)(d.n0f + S.gbase_f + (int64_t)g * S.nf + it.col);
+        e.ycol = it.yint ? (int)(d.n0i + S.gbase_i + (int64_t)g * S.ni + it.col)
+                         : (int)(d.n0f + S.gbase_f + (int64_t)g * S.nf + it.col);
+        e.yint = it.yint;
         e.og = og;
         e.integral = it.integral;
         e.so = so;
@@ -1610,10 +1699,9 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     if (d.n0i) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * d.n0i * 8, s));
     if (d.phi1f_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1f, 0, P.nseg * d.phi1f_seg * 4, s));
     if (d.phi1i_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1i, 0, P.nseg * d.phi1i_seg * 4, s));
-    if (d.n3) {
-      LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3 * 8, s));
-      LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3 * 8, s));
-    }
+    if (d.n3f) LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3f * 8, s));
+    if (d.n3i) LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3i * 8, s));
+    LMFAO_CUDA(cudaMemsetAsync(d.ticket, 0, 4, s));
     if (d.ni) {
       const View &v = P.views[P.inner[0]];
       launch_fast_prep(d, v.v64, (int)v.cols.size(), P.fwcol_dev, v.vcodes, (int)v.codes.size(), P.fcodecol_dev,
@@ -2106,7 +2194,8 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
     for (size_t i = 0; i < P.inner.size(); ++i) o << (i ? "," : "") << nm(P.inner[i]);
     o << "],\"precision\":\"" << (P.fp64 ? "fp64" : "fp32") << "\",\"mode\":\""
       << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : P.fast.on ? "factorised" : "generic")
-      << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false") << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
+      << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false")
+      << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false") << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
       << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows

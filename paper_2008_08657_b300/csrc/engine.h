@@ -221,6 +221,8 @@ struct DCombItem {
   int ig0, nig;     // inner group refs (B1: in the set's digit order, with the query strides)
   int64_t out;      // base cell of the query output (float: fsum index; int: icnt index)
   int64_t cellmul;  // multiplier from cell index to the output array index
+  int yint;         // B1: the column is an integral (count) column
+  int pad_;
 };
 
 // Outer term: segment-key factors x product of outer view columns.

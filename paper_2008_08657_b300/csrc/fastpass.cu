@@ -75,18 +75,36 @@ __global__ void fast_prep_kernel(int64_t nkeys, const double *v64, int vcols, co
   }
 }
 
+template <typename T>
+__device__ __forceinline__ T powu(T x, int e) {  // e is uniform across the warp
+  T y = T(1);
+  for (int k = 0; k < e; ++k) y *= x;
+  return y;
+}
+
+constexpr int RU = 2;  // tuples per lane per step (their loads are issued first)
+
+// Small descriptors of the per-tuple scatter work, copied to shared memory once per CTA.
+struct SDesc {
+  DFastB1 b1[FMAXB1];
+  int j3[FMAXC], int3[FMAXC], p3col[FMAXC];
+  DFac ind[FMAXF];
+  int ind_mono[FMAXF];
+};
+
 template <typename T, int NM, int W>
-__global__ void __launch_bounds__(512) fast_pass_kernel(DFast d) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kernel(DFast d) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SDesc sd;
   const int bs = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = bs >> 5;
   // shared layout: [Pf T nkeys*n3][Pi u32 nkeys*n3][table T nkeys*nw][codes int nkeys*ncode][warp hists]
   size_t off = 0;
   T *Pf = reinterpret_cast<T *>(smem);
   unsigned int *Pi = nullptr;
   if (d.smem_p) {
-    off += sizeof(T) * (size_t)d.nkeys * d.n3;
+    off += sizeof(T) * (size_t)d.nkeys * d.n3f;
     Pi = reinterpret_cast<unsigned int *>(smem + off);
-    off += 4 * (size_t)d.nkeys * d.n3;
+    off += 4 * (size_t)d.nkeys * d.n3i;
   }
   off = (off + 15) & ~(size_t)15;
   const T *table = reinterpret_cast<const T *>(d.table);
@@ -104,18 +122,30 @@ __global__ void __launch_bounds__(512) fast_pass_kernel(DFast d) {
   off = (off + 15) & ~(size_t)15;
   float *hf = reinterpret_cast<float *>(smem + off) + (size_t)warp * (d.hist_f + d.hist_i);
   unsigned int *hi = reinterpret_cast<unsigned int *>(hf + d.hist_f);
-  if (d.smem_p)
-    for (int64_t i = tid; i < d.nkeys * d.n3; i += bs) { Pf[i] = T(0); Pi[i] = 0u; }
+  if (d.smem_p) {
+    for (int64_t i = tid; i < d.nkeys * d.n3f; i += bs) Pf[i] = T(0);
+    for (int64_t i = tid; i < d.nkeys * d.n3i; i += bs) Pi[i] = 0u;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < FMAXB1; ++s) sd.b1[s] = d.b1[s];
+    for (int c = 0; c < FMAXC; ++c) { sd.j3[c] = d.j3[c]; sd.int3[c] = d.int3[c]; sd.p3col[c] = d.p3col[c]; }
+    for (int f = 0; f < FMAXF; ++f) { sd.ind[f] = d.ind[f]; sd.ind_mono[f] = d.ind_mono[f]; }
+  }
   __syncthreads();
+  const int nb1 = d.nb1, n3 = d.n3, nind = d.nind, nx = d.nx, nw = d.nw, ncode = d.ncode;
+  const int n3f = d.n3f, n3i = d.n3i;
 
-  for (int64_t wi = (int64_t)blockIdx.x * nwarps + warp; wi < d.nwork; wi += (int64_t)gridDim.x * nwarps) {
+  for (;;) {
+    int64_t wi = 0;
+    if (lane == 0) wi = atomicAdd(d.ticket, 1u);
+    wi = __shfl_sync(0xffffffffu, wi, 0);
+    if (wi >= d.nwork) break;
     const DWork wk = d.work[wi];
     const unsigned long long ws = d.wseg[wk.seg];
     if (ws == 0) continue;  // the whole segment has no outer partner
     const T wsT = (T)ws;
-    if (d.nb1) {
-      for (int i = lane; i < d.hist_f; i += 32) hf[i] = 0.f;
-      for (int i = lane; i < d.hist_i; i += 32) hi[i] = 0u;
+    if (nb1) {
+      for (int i = lane; i < d.hist_f + d.hist_i; i += 32) hf[i] = 0.f;  // hi follows hf
       __syncwarp();
     }
     T acc[NM][W];
@@ -124,108 +154,136 @@ __global__ void __launch_bounds__(512) fast_pass_kernel(DFast d) {
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[j][w] = T(0);
     const long long rend = wk.r0 + wk.len;
-    for (long long r = wk.r0 + lane; r < rend; r += 32) {
-      int64_t k = 0;
-      T v[W];
-      if (d.ni) {
-        for (int i = 0; i < d.nk; ++i) k += (int64_t)ldi(d.col[d.kslot[i]], r) * d.kstride[i];
+    int kn[RU];
+    T xn[RU][FMAXX];
+    auto load = [&](long long rb, int (&kk)[RU], T (&xv)[RU][FMAXX]) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) v[w] = (w < d.nw) ? table[k * d.nw + w] : T(0);
-      } else {
-        v[0] = T(1);
+      for (int u = 0; u < RU; ++u) {
+        const long long r = rb + 32 * u;
+        const bool ok = r < rend;
+        int k = 0;
+        if (ok && d.ni) {
+          k = ldi(d.col[d.kslot[0]], r) * (int)d.kstride[0];
+          if (d.nk > 1) k += ldi(d.col[d.kslot[1]], r) * (int)d.kstride[1];
+        }
+        kk[u] = ok ? k : -1;
 #pragma unroll
-        for (int w = 1; w < W; ++w) v[w] = T(0);
+        for (int i = 0; i < FMAXX; ++i) xv[u][i] = (ok && i < nx) ? ldn<T>(d.col[d.xslot[i]], r) : T(0);
       }
-      if (v[0] == T(0)) continue;  // no partner in the inner relation: not in the join
-      T x[FMAXX];
+    };
+    load(wk.r0 + lane, kn, xn);
+    for (long long rb = wk.r0 + lane; rb < rend; rb += 32 * RU) {
+      int kk[RU];
+      T xv[RU][FMAXX];
 #pragma unroll
-      for (int i = 0; i < FMAXX; ++i) x[i] = (i < d.nx) ? ldn<T>(d.col[d.xslot[i]], r) : T(0);
-      T m[NM];
+      for (int u = 0; u < RU; ++u) {
+        kk[u] = kn[u];
 #pragma unroll
-      for (int j = 0; j < NM; ++j) {
-        T p = T(1);
-        if (j < d.nm) {
-          for (int f = d.mono_f0[j]; f < d.mono_f0[j] + d.mono_nf[j]; ++f) {
-            const DFac fc = d.facs[f];
-            if (fc.ind) {
-              if (!pred(d.col[fc.col], r, fc.op, fc.t)) p = T(0);
-            } else {
-              T xv = sel<FMAXX, T>(x, d.fx[f]);
-              T y = xv;
-              for (int e = 1; e < fc.pow; ++e) y *= xv;
-              p *= y;
+        for (int i = 0; i < FMAXX; ++i) xv[u][i] = xn[u][i];
+      }
+      if (rb + 32 * RU < rend) load(rb + 32 * RU, kn, xn);  // prefetch the next step
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const int k = kk[u];
+        if (k < 0) continue;
+        const long long r = rb + 32 * u;
+        T v[W];
+        if (d.ni) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) v[w] = (w < nw) ? table[(int64_t)k * nw + w] : T(0);
+        } else {
+          v[0] = T(1);
+#pragma unroll
+          for (int w = 1; w < W; ++w) v[w] = T(0);
+        }
+        if (v[0] == T(0)) continue;  // no partner in the inner relation: not in the join
+        T m[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          T p = T(1);
+#pragma unroll
+          for (int i = 0; i < FMAXX; ++i)
+            if (i < nx) {
+              const int e = d.mexp[j][i];
+              if (e) p *= powu<T>(xv[u][i], e);
             }
+          m[j] = p;
+        }
+        for (int f = 0; f < nind; ++f) {
+          const DFac fc = sd.ind[f];
+          if (!pred(d.col[fc.col], r, fc.op, fc.t)) {
+            const int jm = sd.ind_mono[f];
+#pragma unroll
+            for (int j = 0; j < NM; ++j)
+              if (j == jm) m[j] = T(0);
           }
         }
-        m[j] = p;
-      }
 #pragma unroll
-      for (int j = 0; j < NM; ++j)
+        for (int j = 0; j < NM; ++j)
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[j][w] += m[j] * v[w];
-      for (int s = 0; s < d.nb1; ++s) {
-        const DFastB1 &b = d.b1[s];
-        int g = 0;
-        bool ok = true;
-        for (int i = 0; i < b.nref; ++i) {
-          const DGroupRef &q = b.ref[i];
-          int code = (q.src == 3) ? codes[k * d.ncode + q.b] : row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
-          if (code < 0) ok = false;
-          g += code * (int)q.stride;
+          for (int w = 0; w < W; ++w) acc[j][w] += m[j] * v[w];
+        for (int s = 0; s < nb1; ++s) {
+          const DFastB1 &b = sd.b1[s];
+          int g = 0;
+          bool ok = true;
+          for (int i = 0; i < b.nref; ++i) {
+            const DGroupRef &q = b.ref[i];
+            int code = (q.src == 3) ? codes[(int64_t)k * ncode + q.b]
+                                    : row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
+            if (code < 0) ok = false;
+            g += code * (int)q.stride;
+          }
+          if (!ok) continue;
+          for (int c = 0; c < b.nf; ++c) {
+            T val = sel<NM, T>(m, b.fj[c]) * sel<W, T>(v, b.fw[c]);
+            if (val != T(0)) atomicAdd(hf + b.smem_f + g * b.nf + c, (float)val);
+          }
+          for (int c = 0; c < b.ni; ++c) {
+            T val = sel<NM, T>(m, b.ij[c]) * sel<W, T>(v, b.iw[c]);
+            if (val != T(0)) atomicAdd(hi + b.smem_i + g * b.ni + c, (unsigned int)val);
+          }
         }
-        if (!ok) continue;
-        for (int c = 0; c < b.nf; ++c) {
-          T val = sel<NM, T>(m, b.fj[c]) * sel<W, T>(v, b.fw[c]);
-          if (val != T(0)) atomicAdd(hf + b.smem_f + g * b.nf + c, (float)val);
-        }
-        for (int c = 0; c < b.ni; ++c) {
-          T val = sel<NM, T>(m, b.ij[c]) * sel<W, T>(v, b.iw[c]);
-          if (val != T(0)) atomicAdd(hi + b.smem_i + g * b.ni + c, (unsigned int)val);
-        }
-      }
-      for (int c = 0; c < d.n3; ++c) {
-        T val = sel<NM, T>(m, d.j3[c]);
-        if (val == T(0)) continue;
-        if (d.int3[c]) {
-          unsigned long long iv = (unsigned long long)val * ws;
-          if (d.smem_p) atomicAdd(Pi + k * d.n3 + c, (unsigned int)iv);
-          else atomicAdd(d.p3i + k * d.n3 + c, iv);
-        } else {
-          val *= wsT;
-          if (d.smem_p) atomicAdd(Pf + k * d.n3 + c, val);
-          else atomicAdd(d.p3f + k * d.n3 + c, (double)val);
+        for (int c = 0; c < n3; ++c) {
+          T val = sel<NM, T>(m, sd.j3[c]);
+          if (val == T(0)) continue;
+          const int pc = sd.p3col[c];
+          if (sd.int3[c]) {
+            unsigned long long iv = (unsigned long long)val * ws;
+            if (d.smem_p) atomicAdd(Pi + (int64_t)k * n3i + pc, (unsigned int)iv);
+            else atomicAdd(d.p3i + (int64_t)k * n3i + pc, iv);
+          } else {
+            val *= wsT;
+            if (d.smem_p) atomicAdd(Pf + (int64_t)k * n3f + pc, val);
+            else atomicAdd(d.p3f + (int64_t)k * n3f + pc, (double)val);
+          }
         }
       }
     }
-    // segment sums: warp reduction, then one atomic per entry
-    const int n0 = d.nm * d.nw;
+    // segment sums: warp reduction, one atomic per entry spread over the lanes
+    const int n0 = d.nm * nw;
+    T ival = T(0);
+    const int my_ij = lane < d.n0i ? d.i0j[lane] : -1, my_iw = lane < d.n0i ? d.i0w[lane] : -1;
 #pragma unroll
     for (int j = 0; j < NM; ++j)
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        if (j < d.nm && w < d.nw) {
+        if (j < d.nm && w < nw) {
           T t = acc[j][w];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          acc[j][w] = t;
           if (lane == ((j * W + w) & 31) && t != T(0))
-            atomicAdd(reinterpret_cast<T *>(d.phi0f) + (int64_t)wk.seg * n0 + j * d.nw + w, t);
+            atomicAdd(reinterpret_cast<T *>(d.phi0f) + (int64_t)wk.seg * n0 + j * nw + w, t);
+          if (j == my_ij && w == my_iw) ival = t;
         }
       }
     if (lane < d.n0i) {
-      T t = T(0);
-#pragma unroll
-      for (int j = 0; j < NM; ++j)
-#pragma unroll
-        for (int w = 0; w < W; ++w)
-          if (j == d.i0j[lane] && w == d.i0w[lane]) t = acc[j][w];
-      unsigned long long it = (unsigned long long)(t + T(0.5));
+      unsigned long long it = (unsigned long long)(ival + T(0.5));
       if (it) atomicAdd(d.phi0i + (int64_t)wk.seg * d.n0i + lane, it);
     }
-    if (d.nb1) {
+    if (nb1) {
       __syncwarp();
-      for (int s = 0; s < d.nb1; ++s) {
-        const DFastB1 &b = d.b1[s];
+      for (int s = 0; s < nb1; ++s) {
+        const DFastB1 &b = sd.b1[s];
         for (int i = lane; i < b.G * b.nf; i += 32) {
           float x = hf[b.smem_f + i];
           if (x != 0.f) atomicAdd(d.phi1f + (int64_t)wk.seg * d.phi1f_seg + b.gbase_f + i, x);
@@ -240,10 +298,202 @@ __global__ void __launch_bounds__(512) fast_pass_kernel(DFast d) {
   }
   if (d.smem_p) {
     __syncthreads();
-    for (int64_t i = tid; i < d.nkeys * d.n3; i += bs) {
+    for (int64_t i = tid; i < d.nkeys * n3f; i += bs)
       if (Pf[i] != T(0)) atomicAdd(d.p3f + i, (double)Pf[i]);
+    for (int64_t i = tid; i < d.nkeys * n3i; i += bs)
       if (Pi[i]) atomicAdd(d.p3i + i, (unsigned long long)Pi[i]);
+  }
+}
+
+
+// Lean root pass: the same outputs as fast_pass_kernel for batches whose root-level
+// monomials are the degree <= 2 basis over NX value columns, whose grouped per-segment sums
+// are inner COUNTs and whose root-to-inner partials read basis monomials. Straight-line
+// per-tuple code (no descriptor loops): loads of the next step are in flight while the
+// current one is processed.
+template <int NX>
+struct Basis { static constexpr int N = 1 + NX + NX * (NX + 1) / 2; };
+
+template <typename T, int NX>
+__device__ __forceinline__ void basis(const T (&x)[NX > 0 ? NX : 1], T (&u)[Basis<NX>::N]) {
+  u[0] = T(1);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) u[1 + i] = x[i];
+  int q = 1 + NX;
+#pragma unroll
+  for (int i = 0; i < NX; ++i)
+#pragma unroll
+    for (int j = i; j < NX; ++j) u[q++] = x[i] * x[j];
+}
+
+template <typename T, int NX, int W>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) lean_pass_kernel(DFast d) {
+  constexpr int NM = Basis<NX>::N;
+  constexpr int XA = NX > 0 ? NX : 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int bs = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = bs >> 5;
+  size_t off = 0;
+  T *Pf = reinterpret_cast<T *>(smem);
+  unsigned int *Pi = nullptr;
+  if (d.smem_p) {
+    off += sizeof(T) * (size_t)d.nkeys * d.n3f;
+    Pi = reinterpret_cast<unsigned int *>(smem + off);
+    off += 4 * (size_t)d.nkeys * d.n3i;
+  }
+  off = (off + 15) & ~(size_t)15;
+  const T *table = reinterpret_cast<const T *>(d.table);
+  const int *codes = d.codes;
+  if (d.smem_view && d.ni) {
+    T *st = reinterpret_cast<T *>(smem + off);
+    off += sizeof(T) * (size_t)d.nkeys * d.nw;
+    int *sc = reinterpret_cast<int *>(smem + off);
+    off += 4 * (size_t)d.nkeys * d.ncode;
+    for (int64_t i = tid; i < d.nkeys * d.nw; i += bs) st[i] = reinterpret_cast<const T *>(d.table)[i];
+    for (int64_t i = tid; i < d.nkeys * d.ncode; i += bs) sc[i] = d.codes[i];
+    table = st;
+    codes = sc;
+  }
+  off = (off + 15) & ~(size_t)15;
+  unsigned int *hi = reinterpret_cast<unsigned int *>(smem + off) + (size_t)warp * d.hist_i;
+  if (d.smem_p) {
+    for (int64_t i = tid; i < d.nkeys * d.n3f; i += bs) Pf[i] = T(0);
+    for (int64_t i = tid; i < d.nkeys * d.n3i; i += bs) Pi[i] = 0u;
+  }
+  __syncthreads();
+  const int nb1 = d.nb1, n3 = d.n3, nw = d.nw, ncode = d.ncode, n3f = d.n3f, n3i = d.n3i;
+  const DCol kc = d.col[d.kslot[0]];
+  DCol xc[XA];
+#pragma unroll
+  for (int i = 0; i < XA; ++i) xc[i] = d.col[d.xslot[i]];
+
+  for (;;) {
+    int64_t wi = 0;
+    if (lane == 0) wi = atomicAdd(d.ticket, 1u);
+    wi = __shfl_sync(0xffffffffu, wi, 0);
+    if (wi >= d.nwork) break;
+    const DWork wk = d.work[wi];
+    const unsigned long long ws = d.wseg[wk.seg];
+    if (ws == 0) continue;  // the whole segment has no outer partner
+    const T wsT = (T)ws;
+    if (nb1) {
+      for (int i = lane; i < d.hist_i; i += 32) hi[i] = 0u;
+      __syncwarp();
     }
+    T acc[NM][W];
+#pragma unroll
+    for (int j = 0; j < NM; ++j)
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[j][w] = T(0);
+    const long long rend = wk.r0 + wk.len;
+    int kn[RU];
+    T xn[RU][XA];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const long long r = wk.r0 + lane + 32 * u;
+      const bool ok = r < rend;
+      kn[u] = ok ? (d.ni ? ldi(kc, r) : 0) : -1;
+#pragma unroll
+      for (int i = 0; i < XA; ++i) xn[u][i] = (ok && NX > 0) ? ldn<T>(xc[i], r) : T(0);
+    }
+    for (long long rb = wk.r0 + lane; rb < rend; rb += 32 * RU) {
+      int kk[RU];
+      T xv[RU][XA];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        kk[u] = kn[u];
+#pragma unroll
+        for (int i = 0; i < XA; ++i) xv[u][i] = xn[u][i];
+      }
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {  // prefetch the next step
+        const long long r = rb + 32 * (RU + u);
+        const bool ok = r < rend;
+        kn[u] = ok ? (d.ni ? ldi(kc, r) : 0) : -1;
+#pragma unroll
+        for (int i = 0; i < XA; ++i) xn[u][i] = (ok && NX > 0) ? ldn<T>(xc[i], r) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const int k = kk[u];
+        if (k < 0) continue;
+        T v[W];
+        if (d.ni) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) v[w] = (w < nw) ? table[k * nw + w] : T(0);
+        } else {
+          v[0] = T(1);
+#pragma unroll
+          for (int w = 1; w < W; ++w) v[w] = T(0);
+        }
+        if (v[0] == T(0)) continue;  // no partner in the inner relation: not in the join
+        T um[NM];
+        basis<T, NX>(xv[u], um);
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+#pragma unroll
+          for (int w = 0; w < W; ++w) acc[j][w] += um[j] * v[w];
+        const unsigned int cnt = (unsigned int)v[0];
+#pragma unroll
+        for (int s = 0; s < FMAXB1; ++s)
+          if (s < nb1) {
+            const int code = codes[k * ncode + d.b1code[s]];
+            if (code >= 0) atomicAdd(hi + d.b1[s].smem_i + code, cnt);
+          }
+#pragma unroll
+        for (int c = 0; c < FMAXC; ++c)
+          if (c < n3) {
+            const int pc = d.p3col[c];
+            if (d.int3[c]) {
+              if (d.smem_p) atomicAdd(Pi + k * n3i + pc, (unsigned int)ws);
+              else atomicAdd(d.p3i + (int64_t)k * n3i + pc, ws);
+            } else {
+              const T val = wsT * sel<NM, T>(um, d.j3[c]);
+              if (d.smem_p) atomicAdd(Pf + k * n3f + pc, val);
+              else atomicAdd(d.p3f + (int64_t)k * n3f + pc, (double)val);
+            }
+          }
+      }
+    }
+    // segment sums: warp reduction, one atomic per entry spread over the lanes
+    const int n0 = NM * nw;
+    T ival = T(0);
+    const int my_ij = lane < d.n0i ? d.i0j[lane] : -1, my_iw = lane < d.n0i ? d.i0w[lane] : -1;
+#pragma unroll
+    for (int j = 0; j < NM; ++j)
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        if (w < nw) {
+          T t = acc[j][w];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+          if (lane == ((j * W + w) & 31) && t != T(0))
+            atomicAdd(reinterpret_cast<T *>(d.phi0f) + (int64_t)wk.seg * n0 + j * nw + w, t);
+          if (j == my_ij && w == my_iw) ival = t;
+        }
+      }
+    if (lane < d.n0i) {
+      unsigned long long it = (unsigned long long)(ival + T(0.5));
+      if (it) atomicAdd(d.phi0i + (int64_t)wk.seg * d.n0i + lane, it);
+    }
+    if (nb1) {
+      __syncwarp();
+      for (int s = 0; s < nb1; ++s) {
+        const int G = d.b1[s].G, so = d.b1[s].smem_i;
+        const int64_t gb = (int64_t)wk.seg * d.phi1i_seg + d.b1[s].gbase_i;
+        for (int i = lane; i < G; i += 32) {
+          unsigned int x = hi[so + i];
+          if (x) atomicAdd(d.phi1i + gb + i, x);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (d.smem_p) {
+    __syncthreads();
+    for (int64_t i = tid; i < d.nkeys * n3f; i += bs)
+      if (Pf[i] != T(0)) atomicAdd(d.p3f + i, (double)Pf[i]);
+    for (int64_t i = tid; i < d.nkeys * n3i; i += bs)
+      if (Pi[i]) atomicAdd(d.p3i + i, (unsigned long long)Pi[i]);
   }
 }
 
@@ -266,10 +516,10 @@ __global__ void b3_final_kernel(DB3Final d) {
     double vv = d.v64[k * d.vcols + item.w];
     if (vv == 0.0) continue;
     if (item.integral) {
-      unsigned long long p = d.p3i[k * d.n3 + item.c];
+      unsigned long long p = d.p3i[k * d.n3i + item.c];
       if (p) atomicAdd(d.icnt + item.out + cell * item.cellmul, p * (unsigned long long)vv);
     } else {
-      double p = d.p3f[k * d.n3 + item.c];
+      double p = d.p3f[k * d.n3f + item.c];
       if (p != 0.0) atomicAdd(d.fsum + item.out + cell * item.cellmul, p * vv);
     }
   }
@@ -292,7 +542,7 @@ void launch_fast_prep(const DFast &d, const double *v64, int vcols, const int *w
 size_t fast_smem(const DFast &d, bool fp64, int block) {
   size_t ts = fp64 ? 8 : 4;
   size_t off = 0;
-  if (d.smem_p) off += (ts + 4) * (size_t)d.nkeys * d.n3;
+  if (d.smem_p) off += ts * (size_t)d.nkeys * d.n3f + 4 * (size_t)d.nkeys * d.n3i;
   off = (off + 15) & ~(size_t)15;
   if (d.smem_view && d.ni) off += ts * (size_t)d.nkeys * d.nw + 4 * (size_t)d.nkeys * d.ncode;
   off = (off + 15) & ~(size_t)15;
@@ -331,8 +581,39 @@ bool fast_shape_ok(int nm, int nw) {
   return false;
 }
 
+bool lean_shape_ok(int nx, int nw) { return nx >= 0 && nx <= 3 && nw >= 1 && nw <= 8; }
+
+template <typename T, int NX, int W>
+static void go_lean(const DFast &d, int grid, int block, size_t smem, cudaStream_t s) {
+  cudaFuncSetAttribute(lean_pass_kernel<T, NX, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  lean_pass_kernel<T, NX, W><<<grid, block, smem, s>>>(d);
+}
+
+template <typename T, int NX>
+static void lean_w(const DFast &d, int grid, int block, size_t smem, cudaStream_t s) {
+  if (d.nw <= 1) go_lean<T, NX, 1>(d, grid, block, smem, s);
+  else if (d.nw <= 2) go_lean<T, NX, 2>(d, grid, block, smem, s);
+  else if (d.nw <= 4) go_lean<T, NX, 4>(d, grid, block, smem, s);
+  else go_lean<T, NX, 8>(d, grid, block, smem, s);
+}
+
+template <typename T>
+static void lean_x(const DFast &d, int grid, int block, size_t smem, cudaStream_t s) {
+  switch (d.nx) {
+    case 0: lean_w<T, 0>(d, grid, block, smem, s); break;
+    case 1: lean_w<T, 1>(d, grid, block, smem, s); break;
+    case 2: lean_w<T, 2>(d, grid, block, smem, s); break;
+    default: lean_w<T, 3>(d, grid, block, smem, s); break;
+  }
+}
+
 bool launch_fast_pass(const DFast &d, bool fp64, int grid, int block, cudaStream_t s) {
   size_t smem = fast_smem(d, fp64, block);
+  if (d.lean) {
+    if (fp64) lean_x<double>(d, grid, block, smem, s);
+    else lean_x<float>(d, grid, block, smem, s);
+    return true;
+  }
   if (fp64) return dispatch<double>(d, grid, block, smem, s);
   return dispatch<float>(d, grid, block, smem, s);
 }

@@ -50,13 +50,14 @@ struct DFast {
   const void *table;      // [nkeys][nw] in T (prepared by fast_prep_kernel)
   const int *codes;       // [nkeys][ncode]
   int smem_view;          // stage table and codes in shared memory
-  // monomials
+  // monomials: u_j = prod_i x_i^mexp[j][i] * prod of the indicators of monomial j
   int nm;
-  int mono_f0[FMAXM], mono_nf[FMAXM];
-  DFac facs[FMAXF];
   int nx;                 // root columns whose values feed the monomials
   int xslot[FMAXX];
-  int fx[FMAXF];          // factor -> index into the loaded values
+  unsigned char mexp[FMAXM][FMAXX];
+  int nind;               // indicator factors on root columns
+  DFac ind[FMAXF];
+  int ind_mono[FMAXF];
   // B0
   void *phi0f;            // [nseg][nm*nw]
   unsigned long long *phi0i;  // [nseg][n0i]
@@ -74,6 +75,13 @@ struct DFast {
   int j3[FMAXC];
   int int3[FMAXC];
   int smem_p;             // P in shared memory (else global atomics)
+  int n3f, n3i;           // float / integral B3 columns (P columns are split by kind)
+  int p3col[FMAXC];       // B3 column -> index within its kind
+  unsigned int *ticket;   // work-item ticket (zeroed before every launch)
+  // lean variant: monomials are the full basis of degree <= 2 over the nx value columns
+  // (1, x_i, x_i x_j), no indicators, B1 columns are inner COUNTs only
+  int lean;
+  int b1code[FMAXB1];     // inner view code (position in codes) of each B1 set
   double *p3f;            // [nkeys][n3]
   unsigned long long *p3i;
   const float *thr;
@@ -84,11 +92,12 @@ void launch_fast_prep(const DFast &d, const double *v64, int vcols, const int *w
 size_t fast_smem(const DFast &d, bool fp64, int block);
 bool launch_fast_pass(const DFast &d, bool fp64, int grid, int block, cudaStream_t s);
 bool fast_shape_ok(int nm, int nw);  // a kernel variant exists for nm monomials x nw view columns
+bool lean_shape_ok(int nx, int nw);
 
 // B3 finalisation: out[cell(k)] += V[k][w] * P[k][c] over the inner relation's keys.
 struct DB3Item {
   int w;          // view column (FP64 view)
-  int c;          // P column
+  int c;          // P column (within the float or integral part)
   int integral;
   int ig0, nig;   // group refs (src 3: view code index)
   int64_t out, cellmul;
@@ -102,6 +111,7 @@ struct DB3Final {
   const double *p3f;
   const unsigned long long *p3i;
   int n3;
+  int n3f, n3i;
   int nitems;
   const DB3Item *items;
   const DGroupRef *grefs;

@@ -424,7 +424,13 @@ __global__ void __launch_bounds__(256) combine_kernel(DCombine d) {
           for (int g = 0; g < S.G; ++g) {
             int64_t cell = oc;
             for (int i = 0; i < S.nref; ++i) cell += ((g / S.radix[i]) % S.dom[i]) * d.grefs[item.ig0 + i].stride;
-            if (item.integral) {
+            if (item.yint && !item.integral) {
+              unsigned int ph = d.phi1i[seg * d.phi1i_seg + S.gbase_i + (int64_t)g * S.ni + item.col];
+              if (!ph) continue;
+              T v = pf * (T)ph;
+              if (so >= 0) atomicAdd(outf + so + cell * item.cellmul, v);
+              else atomic_add_out<T>(d.fsum + item.out + cell * item.cellmul, v);
+            } else if (item.integral) {
               unsigned int ph = d.phi1i[seg * d.phi1i_seg + S.gbase_i + (int64_t)g * S.ni + item.col];
               if (!ph) continue;
               unsigned long long v = pi * ph;

@@ -117,7 +117,7 @@ struct DCombine {
 // One output entry of the combine: psi term x one Y column, written to
 // out + (outer cell + icell) * cellmul.
 struct DEntry {
-  int psi, ycol, og, integral, so, pad;
+  int psi, ycol, og, integral, so, yint;
   long long out, cellmul, icell;
 };
 

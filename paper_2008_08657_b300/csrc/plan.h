@@ -92,6 +92,8 @@ struct PhysPlan {
   // specialised root pass (at most one inner child)
   struct Fast {
     bool on = false;
+    bool lean = false;                         // lean kernel variant (degree <= 2 basis)
+    std::vector<int> lean_cols;                // value columns of the basis
     std::vector<std::vector<int>> monos;       // row factor lists
     std::vector<int> wcols;                    // inner view columns (0: COUNT)
     std::vector<std::pair<int, int>> int0;     // integral (monomial, column) pairs of PHI0

@@ -80,6 +80,21 @@ def test_favorita_scaled_fig2_tree(precision):
         compare(q, g, r, where=f"query {i}")
 
 
+@pytest.mark.parametrize("which", ["star", "retailer", "favorita"])
+def test_benchmark_shapes_use_the_lean_root_pass(which):
+    rels = {"star": lambda: W.star_schema(n_fact=50_000), "retailer": lambda: W.retailer_schema(n_fact=1_000_000),
+            "favorita": lambda: W.favorita_schema(n_fact=200_000)}[which]()
+    qs = {"star": W.star_batch, "retailer": W.retailer_batch, "favorita": W.favorita_batch}[which]()
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_queries(qs)
+    e.plan()
+    phys = e.describe()["physical"]
+    e.close()
+    assert phys["specialised_pass"] and phys["lean_pass"] and phys["per_tuple_items"] == 0
+
+
 def test_plan_invariance_retailer():
     rels = W.retailer_schema(n_fact=200_000)
     qs = W.retailer_batch()[:4]
