@@ -132,6 +132,8 @@ typedef struct lmfao_plan_opts {
   const int32_t *query_root;  /* host, nullable: logical root relation per query (-1:
                                heuristic); used by the view-generation layer             */
   const char *cost_model;   /* path of a learned cost model file (LEARNED), or NULL      */
+  int32_t combine;          /* 0: automatic; 1: entry-wise combine; 2: prefix-block combine
+                               when the plan allows it (results are the same)             */
 } lmfao_plan_opts;
 
 typedef struct lmfao_plan_info {

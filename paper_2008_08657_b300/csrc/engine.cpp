@@ -474,12 +474,49 @@ struct Planner {
     }
     P.segrel = seg;
     P.nseg = 1;
+    P.prefix_len = 0;
     if (seg >= 0) {
       const View &v = P.views[seg];
       P.segcols = v.pkeycols;
       P.segdom = v.keydom;
       for (int64_t d : P.segdom) P.nseg *= d;
       if (P.segcols.size() > 8) throw Error(LMFAO_ERR_UNSUPPORTED, "segment key with more than 8 attributes");
+      // Trie order of the segment key: the key of the outer child with the largest subtree
+      // whose key is a proper part of the segment key goes first, so that its view is
+      // constant over contiguous blocks of segments (the prefix).
+      int best = -1, bestw = -1;
+      for (int c : t.children[root]) {
+        if (c == seg) continue;
+        const View &cv = P.views[c];
+        bool inside = !cv.pkeycols.empty() && cv.pkeycols.size() < P.segcols.size();
+        for (int pc : cv.pkeycols)
+          inside = inside && std::find(P.segcols.begin(), P.segcols.end(), pc) != P.segcols.end();
+        if (!inside) continue;
+        int width = 0;
+        std::vector<int> st{c};
+        while (!st.empty()) {
+          int x = st.back();
+          st.pop_back();
+          width += (int)R(x).cols.size();
+          for (int y : t.children[x]) st.push_back(y);
+        }
+        if (width > bestw) { bestw = width; best = c; }
+      }
+      if (best >= 0) {
+        std::vector<int> cols, rest;
+        std::vector<int64_t> dom, rdom;
+        const View &bv = P.views[best];
+        for (size_t i = 0; i < P.segcols.size(); ++i) {
+          bool in = std::find(bv.pkeycols.begin(), bv.pkeycols.end(), P.segcols[i]) != bv.pkeycols.end();
+          (in ? cols : rest).push_back(P.segcols[i]);
+          (in ? dom : rdom).push_back(P.segdom[i]);
+        }
+        P.prefix_len = (int)cols.size();
+        cols.insert(cols.end(), rest.begin(), rest.end());
+        dom.insert(dom.end(), rdom.begin(), rdom.end());
+        P.segcols = cols;
+        P.segdom = dom;
+      }
     }
     P.kind.assign(ctx->rels.size(), 0);
     P.branch.assign(ctx->rels.size(), -1);
@@ -1459,6 +1496,237 @@ void setup_combine2(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPart> &ppart
   P.c2_grid = (int)ranges;
 }
 
+// Prefix-block combine (combine3.cu): eligible when the segment key has a proper prefix,
+// every outer cell is constant inside a block (A-level group references only) and the
+// block tables fit in shared memory. Returns false otherwise (the entry combine runs).
+bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, const std::vector<DSegFac> &segfacs,
+                    const std::vector<DPart> &pparts) {
+  cudaStream_t s = ctx->stream;
+  const DCombine &cb = P.cb;
+  const int L = P.prefix_len, nd = (int)P.segcols.size();
+  if (L <= 0 || L >= nd || P.comb.empty()) return false;
+  DComb3 d{};
+  d.m = 1;
+  for (int i = L; i < nd; ++i) d.m *= P.segdom[i];
+  d.nblocks = P.nseg / d.m;
+  if (d.m < 2) return false;
+  d.wseg = P.wseg;
+  d.seg = cb.seg;
+  d.nouter = cb.nouter;
+  std::vector<bool> aview(cb.nouter, true);
+  for (int o = 0; o < cb.nouter; ++o) {
+    d.outer[o] = cb.outer[o];
+    for (int i = L; i < nd; ++i)
+      if (cb.outer[o].dstride[i]) aview[o] = false;
+  }
+  // split every psi term into its prefix (A) part and its block-varying (B) part
+  struct TermKey {
+    std::vector<int> segf;
+    std::vector<std::pair<int, int>> parts;
+    bool operator<(const TermKey &o) const { return std::tie(segf, parts) < std::tie(o.segf, o.parts); }
+  };
+  auto integral_part = [&](int o, int col) { return P.views[P.outer[o]].cols[col].integral; };
+  std::map<TermKey, int> amap, bmap;
+  std::vector<TermKey> aterms, bterms;
+  std::vector<bool> aint, bint;
+  std::vector<int> psi_a(psi.size()), psi_b(psi.size());
+  for (size_t t = 0; t < psi.size(); ++t) {
+    TermKey ka, kb;
+    bool ia = true, ib = true;
+    for (int f = psi[t].f0; f < psi[t].f0 + psi[t].nf; ++f) {
+      bool inA = segfacs[f].digit < L;
+      (inA ? ka : kb).segf.push_back(f);
+      if (!segfacs[f].ind) (inA ? ia : ib) = false;
+    }
+    for (int i = psi[t].p0; i < psi[t].p0 + psi[t].np; ++i) {
+      const DPart &q = pparts[i];
+      if (aview[q.branch]) { ka.parts.push_back({q.branch, q.col}); ia = ia && integral_part(q.branch, q.col); }
+      else { kb.parts.push_back({q.branch, q.col}); ib = ib && integral_part(q.branch, q.col); }
+    }
+    auto put = [](std::map<TermKey, int> &mp, std::vector<TermKey> &v, std::vector<bool> &iv, const TermKey &k, bool in) {
+      auto it = mp.find(k);
+      if (it != mp.end()) return it->second;
+      int id = (int)v.size();
+      mp[k] = id;
+      v.push_back(k);
+      iv.push_back(in);
+      return id;
+    };
+    psi_a[t] = put(amap, aterms, aint, ka, ia);
+    psi_b[t] = put(bmap, bterms, bint, kb, ib);
+  }
+  // integral B terms first
+  std::vector<int> border(bterms.size()), bpos(bterms.size());
+  int nbi = 0;
+  {
+    int q = 0;
+    for (size_t b = 0; b < bterms.size(); ++b) if (bint[b]) border[q++] = (int)b;
+    nbi = q;
+    for (size_t b = 0; b < bterms.size(); ++b) if (!bint[b]) border[q++] = (int)b;
+    for (size_t i = 0; i < border.size(); ++i) bpos[border[i]] = (int)i;
+  }
+  auto stage_terms = [&](const std::vector<TermKey> &terms, const std::vector<int> &order, std::vector<int2> &stage,
+                         std::vector<DPsi> &out, std::vector<int> &part, const std::vector<bool> &isint) {
+    for (int ti : order) {
+      const TermKey &k = terms[ti];
+      DPsi dp{};
+      dp.f0 = 0;
+      dp.nf = 0;
+      dp.p0 = (int)part.size();
+      for (auto &pr : k.parts) {
+        int at = -1;
+        for (size_t i = 0; i < stage.size(); ++i) if (stage[i].x == pr.first && stage[i].y == pr.second) at = (int)i;
+        if (at < 0) { stage.push_back(make_int2(pr.first, pr.second)); at = (int)stage.size() - 1; }
+        part.push_back(at);
+      }
+      dp.np = (int)k.parts.size();
+      dp.integral = isint[ti] ? 1 : 0;
+      out.push_back(dp);
+    }
+  };
+  // segment factors stay in the shared segfacs table: a term lists them as a contiguous run
+  std::vector<DSegFac> sf2;
+  auto with_segf = [&](std::vector<DPsi> &terms, const std::vector<TermKey> &keys, const std::vector<int> &order) {
+    for (size_t i = 0; i < order.size(); ++i) {
+      terms[i].f0 = (int)sf2.size();
+      for (int f : keys[order[i]].segf) sf2.push_back(segfacs[f]);
+      terms[i].nf = (int)keys[order[i]].segf.size();
+    }
+  };
+  std::vector<int2> astage, bstage;
+  std::vector<DPsi> adesc, bdesc;
+  std::vector<int> apart, bpart;
+  std::vector<int> aorder(aterms.size());
+  std::iota(aorder.begin(), aorder.end(), 0);
+  stage_terms(aterms, aorder, astage, adesc, apart, aint);
+  stage_terms(bterms, border, bstage, bdesc, bpart, bint);
+  with_segf(adesc, aterms, aorder);
+  with_segf(bdesc, bterms, border);
+  // Y columns
+  d.n0f = cb.n0f;
+  d.n0i = cb.n0i;
+  int64_t segf = P.fast.on ? P.fd.phi1f_seg : 0, segi = P.fast.on ? P.fd.phi1i_seg : 0;
+  d.nyf = (int)(d.n0f + segf);
+  d.nyi = (int)(d.n0i + segi);
+  d.phi0f = cb.phi0f;
+  d.phi0i = cb.phi0i;
+  d.phi1f = P.fast.on ? P.fd.phi1f : nullptr;
+  d.phi1i = P.fast.on ? P.fd.phi1i : nullptr;
+  d.phi1f_seg = segf;
+  d.phi1i_seg = segi;
+  // outer-cell sets (A-level only) and entries
+  std::vector<std::vector<DGroupRef>> ogs{{}};
+  auto og_of = [&](const DCombItem &it) -> int {
+    std::vector<DGroupRef> g(P.grefs.begin() + it.og0, P.grefs.begin() + it.og0 + it.nog);
+    for (auto &r : g) {
+      if (r.src == 0 && r.a >= L) return -1;
+      if (r.src == 1 && !aview[r.a]) return -1;
+    }
+    for (size_t i = 0; i < ogs.size(); ++i) {
+      if (ogs[i].size() != g.size()) continue;
+      bool eq = true;
+      for (size_t j = 0; j < g.size(); ++j)
+        eq = eq && ogs[i][j].src == g[j].src && ogs[i][j].a == g[j].a && ogs[i][j].b == g[j].b &&
+             ogs[i][j].stride == g[j].stride;
+      if (eq) return (int)i;
+    }
+    ogs.push_back(g);
+    return (int)ogs.size() - 1;
+  };
+  std::vector<DMirror> mirrors;
+  std::map<int64_t, int> fmir, imir;
+  int fcells = 0, icells = 0;
+  auto mirror_of = [&](const DCombItem &it) -> int {
+    if (it.nog == 0 && it.block < 0) return -1;
+    for (auto &q : P.qout) {
+      int64_t base = it.integral ? q.io : q.fo;
+      int64_t len = it.integral ? q.cells * (1 + q.naggs) : q.cells * q.naggs;
+      if (it.out < base || it.out >= base + len) continue;
+      auto &mp = it.integral ? imir : fmir;
+      int &cells = it.integral ? icells : fcells;
+      auto f = mp.find(base);
+      if (f == mp.end()) {
+        if (cells + len > 8 * 1024) return -1;
+        mp[base] = cells;
+        mirrors.push_back(DMirror{base, cells, (int)len, it.integral, 0});
+        f = mp.find(base);
+        cells += (int)len;
+      }
+      return f->second + (int)(it.out - base);
+    }
+    return -1;
+  };
+  std::vector<DEntry3> ent;
+  for (const DCombItem &it : P.comb) {
+    int og = og_of(it);
+    if (og < 0) return false;  // an outer cell varies inside a block
+    int so = mirror_of(it);
+    int a = psi_a[it.psi], b = bpos[psi_b[it.psi]];
+    if (it.integral && b >= nbi) return false;
+    auto add = [&](int c, int yint, int64_t icell) {
+      DEntry3 e{};
+      e.a = a;
+      e.b = b;
+      e.c = c;
+      e.yint = yint;
+      e.integral = it.integral;
+      e.og = og;
+      e.so = so;
+      e.out = it.out;
+      e.cellmul = it.cellmul;
+      e.icell = icell;
+      ent.push_back(e);
+    };
+    if (it.block < 0) {
+      add(it.col, it.integral ? 1 : 0, 0);  // B0: integral items read PHI0 integral columns
+    } else {
+      const DB1Set &S = P.b1sets[it.block];
+      for (int g = 0; g < S.G; ++g) {
+        int64_t ic = 0;
+        for (int i = 0; i < S.nref; ++i) ic += ((g / S.radix[i]) % S.dom[i]) * P.grefs[it.ig0 + i].stride;
+        int c = it.yint ? (int)(d.n0i + S.gbase_i + (int64_t)g * S.ni + it.col)
+                        : (int)(d.n0f + S.gbase_f + (int64_t)g * S.nf + it.col);
+        add(c, it.yint, ic);
+      }
+    }
+  }
+  std::vector<int> og_off{0};
+  std::vector<DGroupRef> og_refs;
+  for (auto &g : ogs) {
+    og_refs.insert(og_refs.end(), g.begin(), g.end());
+    og_off.push_back((int)og_refs.size());
+  }
+  d.nbst = (int)bstage.size();
+  d.nb = (int)bdesc.size();
+  d.nbi = nbi;
+  d.nast = (int)astage.size();
+  d.na = (int)adesc.size();
+  d.nog = (int)ogs.size();
+  d.nent = (int)ent.size();
+  d.mirror_f = fcells;
+  d.mirror_i = icells;
+  d.nmirror = (int)mirrors.size();
+  if (combine3_smem(d, P.fp64) > 200 * 1024) return false;
+  d.bstage = P.arena.upload(bstage.empty() ? std::vector<int2>{make_int2(0, 0)} : bstage, s);
+  d.bterm = P.arena.upload(bdesc.empty() ? std::vector<DPsi>{DPsi{}} : bdesc, s);
+  d.bpart = P.arena.upload(bpart.empty() ? std::vector<int>{0} : bpart, s);
+  d.astage = P.arena.upload(astage.empty() ? std::vector<int2>{make_int2(0, 0)} : astage, s);
+  d.aterm = P.arena.upload(adesc.empty() ? std::vector<DPsi>{DPsi{}} : adesc, s);
+  d.apart = P.arena.upload(apart.empty() ? std::vector<int>{0} : apart, s);
+  d.segfacs = P.arena.upload(sf2.empty() ? std::vector<DSegFac>{DSegFac{}} : sf2, s);
+  d.og_off = P.arena.upload(og_off, s);
+  d.grefs = P.arena.upload(og_refs.empty() ? std::vector<DGroupRef>{DGroupRef{}} : og_refs, s);
+  d.ent = P.arena.upload(ent.empty() ? std::vector<DEntry3>{DEntry3{}} : ent, s);
+  d.mirror = P.arena.upload(mirrors.empty() ? std::vector<DMirror>{DMirror{}} : mirrors, s);
+  d.fsum = P.fsum;
+  d.icnt = P.icnt;
+  P.c3 = d;
+  P.use_c3 = true;
+  P.c3_block = 512;
+  P.c3_grid = (int)std::max<int64_t>(1, std::min<int64_t>(148, d.nblocks));
+  return true;
+}
+
 void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   cudaStream_t s = ctx->stream;
   // outputs and per-segment sums
@@ -1658,6 +1926,8 @@ void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   int64_t ntiles = (P.nseg + cb.tile - 1) / cb.tile;
   P.cb_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 2));
   setup_combine2(ctx, P, pparts);
+  P.use_c3 = false;
+  if (!P.no_c3) setup_combine3(ctx, P, psi, segfacs, pparts);
   (void)t;
 }
 
@@ -1716,7 +1986,10 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     launch_fact_pass(P.fp, P.fp64, P.nb0, P.fp_grid, P.fp_block, s);
     mark("fact_pass");
   }
-  if (!P.comb.empty()) launch_combine2(P.c2, P.fp64, P.c2_grid, P.c2_block, s);
+  if (!P.comb.empty()) {
+    if (P.use_c3) launch_combine3(P.c3, P.fp64, P.c3_grid, P.c3_block, s);
+    else launch_combine2(P.c2, P.fp64, P.c2_grid, P.c2_block, s);
+  }
   mark("combine");
   LMFAO_CUDA(cudaGetLastError());
   (void)t;
@@ -2003,6 +2276,7 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
     PhysPlan *P = new PhysPlan();
     ctx->plan = P;
     P->fp64 = o.precision == LMFAO_FP64;
+    P->no_c3 = o.combine == 1;
     P->mode = (o.mode == LMFAO_MODE_PER_TUPLE || o.mode == LMFAO_MODE_GENERIC) ? o.mode : LMFAO_MODE_FACTORISED;
     P->root = root;
     P->err = (int *)P->arena.alloc(16);
@@ -2195,7 +2469,9 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
     o << "],\"precision\":\"" << (P.fp64 ? "fp64" : "fp32") << "\",\"mode\":\""
       << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : P.fast.on ? "factorised" : "generic")
       << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false")
-      << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false") << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
+      << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false")
+      << ",\"block_combine\":" << (P.use_c3 ? "true" : "false") << ",\"prefix_digits\":" << P.prefix_len
+      << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
       << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows

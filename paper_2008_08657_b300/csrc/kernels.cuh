@@ -184,3 +184,54 @@ void launch_results(const unsigned long long *icnt, const double *fsum, int64_t 
                     const int *integral, int64_t *counts, double *sums, cudaStream_t s);
 
 }  // namespace lmfao
+
+namespace lmfao {
+
+// Prefix-block combine. The segment key is ordered so that its first L digits (the
+// prefix) are the key of the "A" outer views; the other outer views ("B") vary inside a
+// block of m consecutive segments sharing a prefix. Every outer term factors as
+// psi_t(s) = a_alpha(p) * b_beta(s) (Fig. 3 with the prefix as one more loop level), so
+//     SUM_s psi_t(s) Y_c(s) = SUM_p a_alpha(p) * Z_p[beta][c],   Z_p = B_p^T Y_p,
+// a contraction over the m segments of block p, computed once per block for all
+// (beta, c), followed by one multiply-add per output entry and block.
+struct DEntry3 {
+  int a, b, c, yint, integral, og, so, pad;
+  long long out, cellmul, icell;
+};
+
+struct DComb3 {
+  int64_t nblocks, m;
+  const unsigned long long *wseg;
+  DSegment seg;
+  int nouter;
+  DOuter outer[MAXOUT];
+  int nbst, nb, nbi;        // staged B columns, B terms, integral B terms (first nbi terms)
+  const int2 *bstage;       // (outer view, column)
+  const DPsi *bterm;        // parts index bpart[]
+  const int *bpart;         // -> staged B column
+  int nast, na;
+  const int2 *astage;
+  const DPsi *aterm;
+  const int *apart;
+  const DSegFac *segfacs;   // digits < L belong to A terms, others to B terms
+  int n0f, n0i, nyf, nyi;   // Y columns: float [0, nyf), integral [0, nyi)
+  const void *phi0f;
+  const unsigned long long *phi0i;
+  const float *phi1f;
+  const unsigned int *phi1i;
+  int64_t phi1f_seg, phi1i_seg;
+  int nog;
+  const int *og_off;
+  const DGroupRef *grefs;   // A-level refs (src 0 digit < L, or src 1 A view)
+  int nent;
+  const DEntry3 *ent;
+  int nmirror;
+  const DMirror *mirror;
+  int mirror_f, mirror_i;
+  double *fsum;
+  unsigned long long *icnt;
+};
+size_t combine3_smem(const DComb3 &d, bool fp64);
+void launch_combine3(const DComb3 &d, bool fp64, int grid, int block, cudaStream_t s);
+
+}  // namespace lmfao

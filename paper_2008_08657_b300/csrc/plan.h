@@ -62,6 +62,7 @@ struct PhysPlan {
   std::vector<int> segcols;        // root columns forming the segment key
   std::vector<int64_t> segdom;
   int64_t nseg = 1;
+  int prefix_len = 0;              // leading segment digits forming the block key of the combine
   std::vector<int> outer, inner;   // root children
   std::vector<int> kind;           // per relation: 0 root, 1 outer subtree, 2 inner subtree
   std::vector<int> branch;         // per relation: root child whose subtree holds it (-1 root)
@@ -130,6 +131,9 @@ struct PhysPlan {
   DCombine cb{};
   DComb2 c2{};
   int c2_grid = 0, c2_block = 512;
+  DComb3 c3{};
+  bool use_c3 = false, no_c3 = false;
+  int c3_grid = 0, c3_block = 512;
   DSegWeight sw{};
   size_t cb_smem = 0;
   int fp_grid = 0, fp_block = 256, cb_grid = 0, cb_block = 256;

@@ -64,7 +64,7 @@ class PlanOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("planner", C.c_int32), ("root_rel", C.c_int32),
                 ("segment_rel", C.c_int32), ("mode", C.c_int32), ("autotune", C.c_int32),
                 ("join_parent", C.POINTER(C.c_int32)), ("query_root", C.POINTER(C.c_int32)),
-                ("cost_model", C.c_char_p)]
+                ("cost_model", C.c_char_p), ("combine", C.c_int32)]
 
 
 class PlanInfo(C.Structure):
@@ -243,7 +243,7 @@ class Engine:
 
     # ------------------------------------------------------------------ plan / run / fetch
     def plan(self, precision="fp32", planner="heuristic", root=None, segment="default", mode="auto",
-             join_parent=None, query_roots=None, autotune=False, cost_model=None):
+             join_parent=None, query_roots=None, autotune=False, cost_model=None, combine="auto"):
         o = PlanOpts()
         o.precision = PRECISION[precision]
         forced = root is not None or segment != "default" or planner == "forced"
@@ -257,6 +257,7 @@ class Engine:
             o.segment_rel = self.rel_ids[segment] if isinstance(segment, str) else int(segment)
         o.mode = MODE[mode]
         o.autotune = 1 if autotune else 0
+        o.combine = {"auto": 0, "entry": 1, "block": 2}[combine]
         keep = []
         if join_parent is not None:
             arr = (C.c_int32 * len(join_parent))(*[int(x) for x in join_parent])

@@ -59,11 +59,12 @@ def test_star_config_full_size(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_retailer_scaled(precision):
-    rels = W.retailer_schema(n_fact=300_000)
+@pytest.mark.parametrize("combine", ["block", "entry"])
+def test_retailer_scaled(precision, combine):
+    rels = W.retailer_schema(n_fact=1_000_000)
     qs = W.retailer_batch()
     ref = O.evaluate(rels, qs)
-    got, info = run_engine(rels, qs, precision=precision)
+    got, info = run_engine(rels, qs, precision=precision, combine=combine)
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"query {i}")
 
@@ -83,7 +84,7 @@ def test_favorita_scaled_fig2_tree(precision):
 @pytest.mark.parametrize("which", ["star", "retailer", "favorita"])
 def test_benchmark_shapes_use_the_lean_root_pass(which):
     rels = {"star": lambda: W.star_schema(n_fact=50_000), "retailer": lambda: W.retailer_schema(n_fact=1_000_000),
-            "favorita": lambda: W.favorita_schema(n_fact=200_000)}[which]()
+            "favorita": lambda: W.favorita_schema(n_fact=2_000_000)}[which]()
     qs = {"star": W.star_batch, "retailer": W.retailer_batch, "favorita": W.favorita_batch}[which]()
     e = Engine(0)
     for R in rels:
@@ -93,6 +94,8 @@ def test_benchmark_shapes_use_the_lean_root_pass(which):
     phys = e.describe()["physical"]
     e.close()
     assert phys["specialised_pass"] and phys["lean_pass"] and phys["per_tuple_items"] == 0
+    if which == "retailer":
+        assert phys["block_combine"] and phys["prefix_digits"] == 1
 
 
 def test_plan_invariance_retailer():
@@ -100,7 +103,7 @@ def test_plan_invariance_retailer():
     qs = W.retailer_batch()[:4]
     base, _ = run_engine(rels, qs, precision="fp32")
     for plan in ({"segment": None}, {"segment": "Location"}, {"mode": "per_tuple"}, {"mode": "generic"},
-                 {"precision": "fp64"}):
+                 {"precision": "fp64"}, {"combine": "entry"}):
         kw = {"precision": "fp32", **plan}
         other, _ = run_engine(rels, qs, **kw)
         for q, a, b in zip(qs, base, other):
