@@ -95,9 +95,17 @@ __device__ __forceinline__ int64_t outer_key(const DOuter &o, const DSegment &s,
 }
 
 // ------------------------------------------------------------------ view kernel
+constexpr int VIEW_CHUNK = 16;  // view columns per thread
+
 __global__ void view_kernel(DViewKernel d) {
+  // one thread per (tuple, chunk of VIEW_CHUNK columns): wide views (hundreds of product
+  // columns) spread over many threads instead of looping per tuple
+  const int nchunk = (d.ncols + VIEW_CHUNK - 1) / VIEW_CHUNK;
+  const int64_t total = d.nrows * nchunk;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < d.nrows; r += stride) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const int64_t r = idx / nchunk;
+    const int chunk = (int)(idx - r * nchunk);
     int64_t k = 0;
     for (int i = 0; i < d.nk; ++i) k += (int64_t)ld_i32(d.in[d.kcol[i]], r) * d.kstride[i];
     int64_t ck[MAXCH];
@@ -111,7 +119,8 @@ __global__ void view_kernel(DViewKernel d) {
     }
     if (w == 0.0) continue;  // the tuple has no partner in some child: it does not join
     double *row = d.v64 + k * d.ncols;
-    for (int j = 0; j < d.ncols; ++j) {
+    const int j1 = min(d.ncols, (chunk + 1) * VIEW_CHUNK);
+    for (int j = chunk * VIEW_CHUNK; j < j1; ++j) {
       double val = 1.0;
       for (int f = d.col_fac_off[j]; f < d.col_fac_off[j + 1]; ++f) val *= fac_at<double>(d.in, d.facs[f], r);
       for (int p = d.col_part_off[j]; p < d.col_part_off[j + 1]; ++p) {
@@ -121,6 +130,7 @@ __global__ void view_kernel(DViewKernel d) {
       if (d.unique) row[j] = val;
       else if (val != 0.0) atomicAdd(row + j, val);
     }
+    if (chunk != 0) continue;
     for (int c = 0; c < d.ncodes; ++c) {
       int4 cd = d.code_desc[c];
       int code;
@@ -603,7 +613,8 @@ static int grid_for(int64_t n, int block) {
 
 void launch_view_kernel(const DViewKernel &d, cudaStream_t s) {
   if (d.nrows == 0) return;
-  view_kernel<<<grid_for(d.nrows, 256), 256, 0, s>>>(d);
+  int64_t n = d.nrows * ((d.ncols + VIEW_CHUNK - 1) / VIEW_CHUNK);
+  view_kernel<<<grid_for(n, 128), 128, 0, s>>>(d);
 }
 
 void launch_view_finish(const double *v64, float *v32, uint32_t *vint, const int *intcols, int ncols, int nint,
