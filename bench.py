@@ -38,9 +38,24 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def workload(n_fact, seed=0):
+WORKLOADS = {
+    "retailer": ("retailer-snowflake ridge batch", 84_000_000),
+    "favorita": ("favorita-schema ridge + categorical-pair batch", 120_000_000),
+    "star": ("star-join ridge batch", 200_000),
+    "dt": ("decision-tree level (8 leaves x 37 features x 20 buckets) on the retailer snowflake", 84_000_000),
+}
+
+
+def workload(n_fact, seed=0, which="retailer"):
     from paper_2008_08657_b300 import workloads as W
-    return W.retailer_schema(n_fact=n_fact, seed=seed), W.retailer_batch()
+    if which == "favorita":
+        return W.favorita_schema(n_fact=n_fact, seed=seed), W.favorita_batch()
+    if which == "star":
+        return W.star_schema(n_fact=n_fact, seed=seed), W.star_batch()
+    rels = W.retailer_schema(n_fact=n_fact, seed=seed)
+    if which == "dt":
+        return rels, W.dt_level_batch(rels, seed=seed)[0]
+    return rels, W.retailer_batch()
 
 
 class Clocks:
@@ -113,7 +128,7 @@ def bench_lmfao(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    rels, qs = workload(args.fact_rows, seed=args.seed)
+    rels, qs = workload(args.fact_rows, seed=args.seed, which=args.workload)
     n_fact = rels[0]["nrows"]
     eng = Engine(local)
     for R in rels:
@@ -172,8 +187,8 @@ def bench_lmfao(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-        "data": "synthetic (seeded, Retailer-shaped)",
-        "config": {"workload": f"retailer-snowflake ridge batch, {n_fact} fact tuples, {len(qs)} queries, "
+        "data": f"synthetic (seeded, {args.workload}-shaped)",
+        "config": {"workload": f"{WORKLOADS[args.workload][0]}, {n_fact} fact tuples, {len(qs)} queries, "
                                f"{sum(len(q['aggs']) for q in qs)} aggregates", "fact_tuples": n_fact,
                    "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
                    "segments": info["n_segments"], "segment_relation": desc["physical"]["segment_relation"]},
@@ -236,7 +251,7 @@ def cpu_baseline(args, sample_rows=300_000):
     """The oracle as it stands, on a bounded sample of the same workload (first
     ``sample_rows`` fact tuples with all dimension relations), timed on the host."""
     from oracle import lmfao_oracle as O
-    rels, qs = workload(sample_rows, seed=args.seed)
+    rels, qs = workload(sample_rows, seed=args.seed, which=args.workload)
     t0 = time.perf_counter()
     O.evaluate(rels, qs)
     dt = time.perf_counter() - t0
@@ -253,7 +268,7 @@ def bench_reference(args):
         return
     from oracle import lmfao_oracle as O
     sample = args.ref_rows
-    rels, qs = workload(sample, seed=args.seed)
+    rels, qs = workload(sample, seed=args.seed, which=args.workload)
     for _ in range(args.warmup):
         O.evaluate(rels, qs)
     t = []
@@ -266,8 +281,8 @@ def bench_reference(args):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, Retailer-shaped)",
-        "config": {"workload": f"retailer-snowflake ridge batch, sample of {sample} fact tuples per step",
+        "vs_baseline": None, "dtype": "f64", "data": f"synthetic (seeded, {args.workload}-shaped)",
+        "config": {"workload": f"{WORKLOADS[args.workload][0]}, sample of {sample} fact tuples per step",
                    "fact_tuples": sample},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{sample} fact tuples per step"},
@@ -282,13 +297,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lmfao", choices=["lmfao", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fact-rows", type=int, default=84_000_000)
+    ap.add_argument("--workload", default="retailer", choices=sorted(WORKLOADS))
+    ap.add_argument("--fact-rows", type=int, default=None)
     ap.add_argument("--ref-rows", type=int, default=200_000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
+    if args.fact_rows is None:
+        args.fact_rows = WORKLOADS[args.workload][1]
     if args.warmup < 3 and args.impl == "lmfao":
         args.warmup = 3
     if args.impl == "reference":

@@ -199,6 +199,14 @@ LMFAO_API int lmfao_clear_batch(struct lmfao_ctx *ctx);
  * work (reorganisation, autotuning) on the context's internal stream and waits for it. */
 LMFAO_API int lmfao_plan(struct lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *info);
 
+/* Candidate physical plans of the current batch (root relation, segment relation, root
+ * pass, combine) for training a cost model: cand (host, cap x 4 int32: root_rel,
+ * segment_rel, mode, combine -- usable as FORCED plan options) and feats (host, cap x nfeat
+ * floats: the features the LEARNED planner feeds to its model). Either may be NULL.
+ * *n receives the number of candidates, *nfeat the feature count. */
+LMFAO_API int lmfao_plan_candidates(struct lmfao_ctx *ctx, const lmfao_plan_opts *opts, int32_t *cand, float *feats,
+                                    int cap, int *n, int *nfeat);
+
 /* Evaluate the planned batch asynchronously on `stream` (a cudaStream_t; NULL = the
  * legacy default stream). All work (view kernels, root pass, contraction,
  * finalisation) is enqueued on that stream; device-side failures are latched and
@@ -247,6 +255,26 @@ LMFAO_API int lmfao_cart_variances(struct lmfao_ctx *ctx, const int *qids, int n
 #define LMFAO_NOALLOC_MAX_QUERIES 4096
 LMFAO_API int lmfao_cart_variances_noalloc(struct lmfao_ctx *ctx, const int *qids, int n, double *out,
                                            void *stream);
+
+/* ---- learned cost model (planner) -----------------------------------------------------
+ * A 3-layer perceptron of width 64 over plan features predicts log run time of a plan
+ * (the planner's "find roots" and grouping choices of Fig. 1 are ranked by it). Parameters
+ * are one FP32 device buffer of lmfao_mlp_param_count(d) floats: W1 (d x 64, row-major),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1). All pointers are device memory; work is
+ * enqueued on `stream`. d must be in [1, 256]. */
+LMFAO_API int64_t lmfao_mlp_param_count(int d);
+/* y[i] = MLP(x[i, :]) for n samples (x: n x d). h1, h2 (n x 64 each) receive the hidden
+ * activations when non-NULL (needed by lmfao_mlp_backward). */
+LMFAO_API int lmfao_mlp_forward(const float *x, int n, int d, const float *params, float *h1, float *h2, float *y,
+                                void *stream);
+/* loss = mean((y - t)^2) into *loss (device float) and gy[i] = 2 (y[i] - t[i]) / n. */
+LMFAO_API int lmfao_mlp_loss(const float *y, const float *t, int n, float *gy, float *loss, void *stream);
+/* grad = d(sum_i gy[i] * y[i]) / d(params) from the activations of lmfao_mlp_forward. */
+LMFAO_API int lmfao_mlp_backward(const float *x, int n, int d, const float *params, const float *h1,
+                                 const float *h2, const float *gy, float *grad, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected for step >= 1). */
+LMFAO_API int lmfao_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t np, int step, float lr,
+                             void *stream);
 
 /* Timings of the last lmfao_run measured with CUDA events around each kernel (host
  * array of at most cap doubles, milliseconds, in launch order; names via

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblmfao.so")
-SOURCES = ["kernels.cu", "fastpass.cu", "combine.cu", "combine3.cu", "engine.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "fastpass.cu", "combine.cu", "combine3.cu", "mlp.cu", "engine.cpp", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-diag-suppress", "177",

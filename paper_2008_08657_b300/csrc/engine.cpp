@@ -11,6 +11,12 @@
 #include "ctx.h"
 #include "fastpass.cuh"
 
+namespace lmfao {
+int64_t mlp_param_count(int d);
+}
+extern "C" int lmfao_mlp_forward(const float *x, int n, int d, const float *params, float *h1, float *h2, float *y,
+                                 void *stream);
+
 using namespace lmfao;
 
 
@@ -2023,6 +2029,258 @@ std::string json_escape(const std::string &x) {
 
 }  // namespace
 
+
+// ======================================================================================
+// plan building, candidates, features, cost model
+// ======================================================================================
+namespace {
+
+constexpr int NFEAT = 24;
+
+lmfao_plan_opts default_opts() {
+  lmfao_plan_opts o{};
+  o.precision = LMFAO_FP32;
+  o.planner = LMFAO_PLAN_HEURISTIC;
+  o.root_rel = -1;
+  o.segment_rel = -2;
+  o.mode = LMFAO_MODE_AUTO;
+  return o;
+}
+
+std::vector<int> parent_links(lmfao_ctx *ctx, const lmfao_plan_opts &o) {
+  int n = (int)ctx->rels.size();
+  std::vector<int> par;
+  if (o.join_parent) {
+    par.assign(o.join_parent, o.join_parent + n);
+    for (int p : par)
+      if (p < -1 || p >= n) throw Error(LMFAO_ERR_ARG, "join_parent out of range");
+  } else if (n == 1) {
+    par.assign(1, -1);
+  } else {
+    par = gyo(ctx);
+  }
+  return par;
+}
+
+int largest_relation(const lmfao_ctx *ctx) {
+  int root = 0;
+  for (int r = 1; r < (int)ctx->rels.size(); ++r)
+    if (ctx->rels[r].nrows > ctx->rels[root].nrows) root = r;
+  return root;
+}
+
+// Plan features of the learned cost model (sizes on a log10 scale).
+std::vector<float> plan_features(const lmfao_ctx *ctx, const PhysPlan &P, const JoinTree &t) {
+  auto lg = [](double x) { return (float)std::log10(1.0 + std::max(0.0, x)); };
+  const double rows = (double)ctx->rels[P.root].nrows;
+  double in_keys = 0, out_keys = 0, cols = 0, maxcols = 0, other_rows = 0;
+  for (int c : P.inner) in_keys += (double)P.views[c].nkeys;
+  for (int c : P.outer) out_keys += (double)P.views[c].nkeys;
+  for (int r : t.post) {
+    cols += (double)P.views[r].cols.size();
+    maxcols = std::max(maxcols, (double)P.views[r].cols.size());
+    other_rows += (double)ctx->rels[r].nrows;
+  }
+  double b0 = P.fast.on ? (double)(P.fast.monos.size() * P.fast.wcols.size()) : (double)(P.b0f.size() + P.b0i.size());
+  double b1g = 0;
+  for (auto &S : P.fast.b1) b1g += (double)S.G * (double)(S.fcols.size() + S.icols.size());
+  double naggs = 0;
+  for (auto &q : ctx->queries) naggs += (double)q.aggs.size();
+  std::vector<float> f(NFEAT, 0.f);
+  f[0] = lg(rows);
+  f[1] = lg((double)P.nseg);
+  f[2] = lg(rows / std::max<double>(1, (double)P.nseg));
+  f[3] = (float)P.outer.size();
+  f[4] = (float)P.inner.size();
+  f[5] = lg(in_keys);
+  f[6] = lg(out_keys);
+  f[7] = lg(cols);
+  f[8] = lg(maxcols);
+  f[9] = lg(b0);
+  f[10] = (float)P.fast.b1.size();
+  f[11] = lg(b1g);
+  f[12] = (float)P.fast.p3.size();
+  f[13] = lg((double)P.b2.size());
+  f[14] = lg((double)P.comb.size());
+  f[15] = (P.prefix_len > 0 && !P.no_c3) ? 1.f : 0.f;
+  f[16] = P.fast.on ? 1.f : 0.f;
+  f[17] = (P.fast.on && P.fast.lean) ? 1.f : 0.f;
+  f[18] = P.mode == LMFAO_MODE_GENERIC ? 1.f : 0.f;
+  f[19] = lg((double)ctx->queries.size());
+  f[20] = lg(naggs);
+  f[21] = P.root == largest_relation(ctx) ? 1.f : 0.f;
+  f[22] = lg(other_rows);
+  f[23] = lg(rows * (1.0 + (double)P.inner.size()));
+  return f;
+}
+
+// Build the plan of options o into ctx (tree, logical plan, physical plan). With dry, stop
+// after routing and return the plan features instead of setting up the device passes.
+void build_plan(lmfao_ctx *ctx, const lmfao_plan_opts &o, bool dry, std::vector<float> *feats) {
+  int n = (int)ctx->rels.size();
+  std::vector<int> par = parent_links(ctx, o);
+  int root = o.root_rel;
+  if (root < 0 || root >= n || o.planner != LMFAO_PLAN_FORCED) {
+    if (!(o.planner == LMFAO_PLAN_FORCED && root >= 0 && root < n)) root = largest_relation(ctx);
+  }
+  ctx->tree = build_tree(ctx, par, root);
+  ctx->logical = build_logical(ctx, ctx->tree, o.query_root);
+  if (ctx->device < 0) {  // host-only: the logical plan of Section 2 only
+    ctx->planned = true;
+    return;
+  }
+  PhysPlan *P = new PhysPlan();
+  ctx->plan = P;
+  P->fp64 = o.precision == LMFAO_FP64;
+  P->no_c3 = o.combine == 1;
+  P->mode = (o.mode == LMFAO_MODE_PER_TUPLE || o.mode == LMFAO_MODE_GENERIC) ? o.mode : LMFAO_MODE_FACTORISED;
+  P->root = root;
+  P->err = (int *)P->arena.alloc(16);
+  Planner pl(ctx, *P, ctx->tree);
+  pl.init_views();
+  compute_multiplicities(ctx, *P, ctx->tree);
+  pl.choose_segments(o);
+  {
+    auto items = pl.decompose();
+    if (!(P->mode == LMFAO_MODE_FACTORISED && pl.route_fast(items))) {
+      P->fast = PhysPlan::Fast{};
+      P->comb.clear();
+      pl.route_generic(items, P->mode);
+    }
+  }
+  for (int c : P->inner)
+    for (int pc : P->views[c].pkeycols) pl.rowslot(pc);
+  if (dry) {
+    if (feats) *feats = plan_features(ctx, *P, ctx->tree);
+    return;
+  }
+  setup_views(ctx, *P, ctx->tree, !P->fp64);
+  setup_root(ctx, *P, ctx->tree);
+  setup_passes(ctx, *P, ctx->tree);
+  LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->planned = true;
+}
+
+struct Cand {
+  int root, seg, mode, combine;
+};
+
+// Candidate physical plans: root relation (the largest and the next two largest), segment
+// relation (none or any child of the root), root pass (specialised when possible, or the
+// generic pass) and combine (prefix-block or entry-wise).
+std::vector<Cand> candidates(lmfao_ctx *ctx, const lmfao_plan_opts &o) {
+  int n = (int)ctx->rels.size();
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctx->rels[a].nrows > ctx->rels[b].nrows; });
+  std::vector<int> par = parent_links(ctx, o);
+  std::vector<Cand> out;
+  for (int ri = 0; ri < std::min(n, 3); ++ri) {
+    int root = order[ri];
+    JoinTree t = build_tree(ctx, par, root);
+    std::vector<int> segs{-1};
+    for (int c : t.children[root]) {
+      int64_t nk = 1;
+      for (auto &a : shared_attrs(ctx, c, root)) {
+        nk *= ctx->rels[c].cols[ctx->rels[c].col(a)].domain;
+        if (nk > (int64_t(1) << 26)) break;
+      }
+      if (nk <= (int64_t(1) << 26)) segs.push_back(c);
+    }
+    for (int sgi : segs)
+      for (int mode : {LMFAO_MODE_AUTO, LMFAO_MODE_GENERIC})
+        for (int comb : {0, 1}) {
+          if (mode == LMFAO_MODE_GENERIC && comb == 1) continue;
+          out.push_back(Cand{root, sgi, mode, comb});
+        }
+  }
+  return out;
+}
+
+lmfao_plan_opts cand_opts(const lmfao_plan_opts &base, const Cand &c) {
+  lmfao_plan_opts o = base;
+  o.planner = LMFAO_PLAN_FORCED;
+  o.root_rel = c.root;
+  o.segment_rel = c.seg;
+  o.mode = c.mode;
+  o.combine = c.combine;
+  return o;
+}
+
+// Median device time of `reps` evaluations of the current plan after `warm` warm-up runs.
+double time_plan(lmfao_ctx *ctx, int warm, int reps) {
+  PhysPlan &P = *ctx->plan;
+  cudaStream_t s = ctx->stream;
+  for (int i = 0; i < warm; ++i) enqueue_run(ctx, P, ctx->tree, s);
+  cudaEvent_t a, b;
+  LMFAO_CUDA(cudaEventCreate(&a));
+  LMFAO_CUDA(cudaEventCreate(&b));
+  std::vector<double> ms;
+  for (int i = 0; i < reps; ++i) {
+    LMFAO_CUDA(cudaEventRecord(a, s));
+    enqueue_run(ctx, P, ctx->tree, s);
+    LMFAO_CUDA(cudaEventRecord(b, s));
+    LMFAO_CUDA(cudaEventSynchronize(b));
+    float f = 0;
+    LMFAO_CUDA(cudaEventElapsedTime(&f, a, b));
+    ms.push_back(f);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::sort(ms.begin(), ms.end());
+  return ms[ms.size() / 2];
+}
+
+struct CostModelFile {
+  int d = 0;
+  std::vector<float> mean, std, params;
+};
+
+// Text file: "lmfao-cost-model 1 <d>", then d means, d standard deviations, then the
+// lmfao_mlp_param_count(d) parameters (whitespace separated).
+CostModelFile load_cost_model(const char *path) {
+  if (!path) throw Error(LMFAO_ERR_ARG, "the learned planner needs a cost model file");
+  FILE *f = std::fopen(path, "r");
+  if (!f) throw Error(LMFAO_ERR_ARG, std::string("cannot open cost model ") + path);
+  CostModelFile cm;
+  char tag[64] = {0};
+  int ver = 0;
+  bool ok = std::fscanf(f, "%63s %d %d", tag, &ver, &cm.d) == 3 && std::string(tag) == "lmfao-cost-model" &&
+            ver == 1 && cm.d == NFEAT;
+  int64_t np = ok ? mlp_param_count(cm.d) : 0;
+  auto rd = [&](std::vector<float> &v, int64_t k) {
+    v.resize(k);
+    for (int64_t i = 0; i < k && ok; ++i) ok = std::fscanf(f, "%f", &v[i]) == 1;
+  };
+  if (ok) rd(cm.mean, cm.d);
+  if (ok) rd(cm.std, cm.d);
+  if (ok) rd(cm.params, np);
+  std::fclose(f);
+  if (!ok) throw Error(LMFAO_ERR_ARG, std::string("malformed cost model ") + path);
+  for (float &x : cm.std)
+    if (!(x > 0)) x = 1.f;
+  return cm;
+}
+
+std::vector<float> predict(const CostModelFile &cm, const std::vector<float> &X, int n) {
+  float *dx = nullptr, *dp = nullptr, *dy = nullptr;
+  LMFAO_CUDA(cudaMalloc(&dx, X.size() * 4 + 16));
+  LMFAO_CUDA(cudaMalloc(&dp, cm.params.size() * 4 + 16));
+  LMFAO_CUDA(cudaMalloc(&dy, (size_t)n * 4 + 16));
+  LMFAO_CUDA(cudaMemcpy(dx, X.data(), X.size() * 4, cudaMemcpyHostToDevice));
+  LMFAO_CUDA(cudaMemcpy(dp, cm.params.data(), cm.params.size() * 4, cudaMemcpyHostToDevice));
+  int rc = lmfao_mlp_forward(dx, n, cm.d, dp, nullptr, nullptr, dy, nullptr);
+  std::vector<float> y(n);
+  cudaError_t e = cudaMemcpy(y.data(), dy, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dp);
+  cudaFree(dy);
+  if (rc != LMFAO_OK || e != cudaSuccess) throw Error(LMFAO_ERR_CUDA, "cost model evaluation failed");
+  return y;
+}
+
+}  // namespace
+
 // ======================================================================================
 // C ABI
 // ======================================================================================
@@ -2234,84 +2492,82 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
     auto t0 = std::chrono::steady_clock::now();
     drop_plan(ctx);
     if (ctx->rels.empty()) return fail(ctx, LMFAO_ERR_ARG, "no relations loaded");
-    lmfao_plan_opts o{};
-    o.precision = LMFAO_FP32;
-    o.planner = LMFAO_PLAN_HEURISTIC;
-    o.root_rel = -1;
-    o.segment_rel = -2;
-    o.mode = LMFAO_MODE_AUTO;
+    lmfao_plan_opts o = default_opts();
     if (opts) o = *opts;
-    int n = (int)ctx->rels.size();
-    std::vector<int> par;
-    if (o.join_parent) {
-      par.assign(o.join_parent, o.join_parent + n);
-      for (int p : par) if (p < -1 || p >= n) return fail(ctx, LMFAO_ERR_ARG, "join_parent out of range");
-    } else if (n == 1) {
-      par.assign(1, -1);
+    double predicted = -1;
+    if (ctx->device >= 0 && (o.planner == LMFAO_PLAN_EXHAUSTIVE || o.planner == LMFAO_PLAN_LEARNED)) {
+      std::vector<Cand> cands = candidates(ctx, o);
+      if (cands.empty()) return fail(ctx, LMFAO_ERR_ARG, "no candidate plan");
+      int best = 0;
+      if (o.planner == LMFAO_PLAN_EXHAUSTIVE) {
+        double bt = 1e300;
+        for (size_t c = 0; c < cands.size(); ++c) {
+          build_plan(ctx, cand_opts(o, cands[c]), false, nullptr);
+          double ms = time_plan(ctx, 1, 3);
+          drop_plan(ctx);
+          if (ms < bt) { bt = ms; best = (int)c; }
+        }
+        predicted = bt;
+      } else {
+        CostModelFile cm = load_cost_model(o.cost_model);
+        std::vector<float> X;
+        for (auto &c : cands) {
+          std::vector<float> f;
+          build_plan(ctx, cand_opts(o, c), true, &f);
+          drop_plan(ctx);
+          for (size_t k = 0; k < f.size(); ++k) X.push_back((f[k] - cm.mean[k]) / cm.std[k]);
+        }
+        std::vector<float> y = predict(cm, X, (int)cands.size());
+        for (size_t c = 1; c < cands.size(); ++c)
+          if (y[c] < y[best]) best = (int)c;
+        predicted = std::exp((double)y[best]);
+      }
+      build_plan(ctx, cand_opts(o, cands[best]), false, nullptr);
     } else {
-      par = gyo(ctx);
+      build_plan(ctx, o, false, nullptr);
     }
-    int root = o.root_rel;
-    if (root < 0 || o.planner != LMFAO_PLAN_FORCED) {
-      if (root < 0 || root >= n) {
-        root = 0;
-        for (int r = 1; r < n; ++r) if (ctx->rels[r].nrows > ctx->rels[root].nrows) root = r;
-      }
-    }
-    if (root >= n) return fail(ctx, LMFAO_ERR_ARG, "root_rel out of range");
-    ctx->tree = build_tree(ctx, par, root);
-    ctx->logical = build_logical(ctx, ctx->tree, o.query_root);
-    if (ctx->device < 0) {  // host-only: the logical plan of Section 2 only
-      ctx->planned = true;
-      if (info) {
-        std::memset(info, 0, sizeof(*info));
-        info->root_rel = root;
-        info->segment_rel = -1;
-        info->n_views = (int)ctx->logical.views.size();
-        info->n_groups = (int)ctx->logical.groups.size();
-        info->predicted_ms = -1;
-      }
-      return LMFAO_OK;
-    }
-    PhysPlan *P = new PhysPlan();
-    ctx->plan = P;
-    P->fp64 = o.precision == LMFAO_FP64;
-    P->no_c3 = o.combine == 1;
-    P->mode = (o.mode == LMFAO_MODE_PER_TUPLE || o.mode == LMFAO_MODE_GENERIC) ? o.mode : LMFAO_MODE_FACTORISED;
-    P->root = root;
-    P->err = (int *)P->arena.alloc(16);
-    Planner pl(ctx, *P, ctx->tree);
-    pl.init_views();
-    compute_multiplicities(ctx, *P, ctx->tree);
-    pl.choose_segments(o);
-    {
-      auto items = pl.decompose();
-      if (!(P->mode == LMFAO_MODE_FACTORISED && pl.route_fast(items))) {
-        P->fast = PhysPlan::Fast{};
-        P->comb.clear();
-        P->grefs.resize(P->grefs.size());
-        pl.route_generic(items, P->mode);
-      }
-    }
-    // inner branch keys are read per tuple
-    for (int c : P->inner)
-      for (int pc : P->views[c].pkeycols) pl.rowslot(pc);
-    setup_views(ctx, *P, ctx->tree, !P->fp64);
-    setup_root(ctx, *P, ctx->tree);
-    setup_passes(ctx, *P, ctx->tree);
-    LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
-    ctx->planned = true;
-    P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    PhysPlan *P = ctx->plan;
+    if (P) P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
-      info->root_rel = root;
-      info->segment_rel = P->segrel;
-      info->n_segments = P->nseg;
+      std::memset(info, 0, sizeof(*info));
+      info->root_rel = ctx->tree.root;
+      info->segment_rel = P ? P->segrel : -1;
+      info->n_segments = P ? P->nseg : 0;
       info->n_views = (int)ctx->logical.views.size();
       info->n_groups = (int)ctx->logical.groups.size();
-      info->n_kernels = (int)P->vk.size() * 2 + 2 + (P->comb.empty() ? 0 : 1);
-      info->mode = P->mode;
-      info->predicted_ms = -1;
-      info->plan_ms = P->plan_ms;
+      info->n_kernels = P ? (int)P->vk.size() * 2 + 2 + (P->comb.empty() ? 0 : 1) + (P->fast.on ? 2 : 0) : 0;
+      info->mode = P ? P->mode : 0;
+      info->predicted_ms = predicted;
+      info->plan_ms = P ? P->plan_ms : 0;
+    }
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_plan_candidates(lmfao_ctx *ctx, const lmfao_plan_opts *opts, int32_t *cand, float *feats, int cap, int *n,
+                          int *nfeat) {
+  return guarded(ctx, [&]() -> int {
+    if (ctx->device < 0) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "host-only context");
+    if (ctx->rels.empty()) return fail(ctx, LMFAO_ERR_ARG, "no relations loaded");
+    drop_plan(ctx);
+    lmfao_plan_opts o = default_opts();
+    if (opts) o = *opts;
+    std::vector<Cand> cands = candidates(ctx, o);
+    if (n) *n = (int)cands.size();
+    if (nfeat) *nfeat = NFEAT;
+    for (int c = 0; c < (int)cands.size() && c < cap; ++c) {
+      if (cand) {
+        cand[c * 4 + 0] = cands[c].root;
+        cand[c * 4 + 1] = cands[c].seg;
+        cand[c * 4 + 2] = cands[c].mode;
+        cand[c * 4 + 3] = cands[c].combine;
+      }
+      if (feats) {
+        std::vector<float> f;
+        build_plan(ctx, cand_opts(o, cands[c]), true, &f);
+        drop_plan(ctx);
+        for (int k = 0; k < NFEAT; ++k) feats[(size_t)c * NFEAT + k] = f[k];
+      }
     }
     return LMFAO_OK;
   });

@@ -34,8 +34,10 @@ ENTRY_POINTS = [
     "lmfao_create", "lmfao_destroy", "lmfao_last_error", "lmfao_load_relation", "lmfao_add_batch",
     "lmfao_clear_batch", "lmfao_plan", "lmfao_run", "lmfao_fetch", "lmfao_result_device",
     "lmfao_describe_plan", "lmfao_cart_variances", "lmfao_kernel_times", "lmfao_kernel_name",
-    "lmfao_set_profiling", "lmfao_cart_variances_noalloc",
+    "lmfao_set_profiling", "lmfao_cart_variances_noalloc", "lmfao_mlp_param_count", "lmfao_mlp_forward",
+    "lmfao_mlp_loss", "lmfao_mlp_backward", "lmfao_mlp_adam", "lmfao_plan_candidates",
 ]
+COST_MODEL_PATH = os.path.join(_HERE, "cost_model.txt")
 
 
 class Column(C.Structure):
@@ -115,6 +117,13 @@ def library():
             "lmfao_kernel_name": (C.c_char_p, [P, C.c_int]),
             "lmfao_set_profiling": (C.c_int, [P, C.c_int]),
             "lmfao_cart_variances_noalloc": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, P, P]),
+            "lmfao_mlp_param_count": (C.c_int64, [C.c_int]),
+            "lmfao_plan_candidates": (C.c_int, [P, C.POINTER(PlanOpts), C.POINTER(C.c_int32), C.POINTER(C.c_float),
+                                                C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "lmfao_mlp_forward": (C.c_int, [P, C.c_int, C.c_int, P, P, P, P, P]),
+            "lmfao_mlp_loss": (C.c_int, [P, P, C.c_int, P, P, P]),
+            "lmfao_mlp_backward": (C.c_int, [P, C.c_int, C.c_int, P, P, P, P, P, P]),
+            "lmfao_mlp_adam": (C.c_int, [P, P, P, P, C.c_int64, C.c_int, C.c_float, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -267,6 +276,8 @@ class Engine:
             arr = (C.c_int32 * len(query_roots))(*[int(x) for x in query_roots])
             keep.append(arr)
             o.query_root = arr
+        if cost_model is None and planner == "learned":
+            cost_model = COST_MODEL_PATH
         if cost_model is not None:
             b = cost_model.encode()
             keep.append(b)
@@ -274,6 +285,34 @@ class Engine:
         info = PlanInfo()
         self._check(self.lib.lmfao_plan(self.ctx, C.byref(o), C.byref(info)))
         return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+    def plan_candidates(self, precision="fp32", join_parent=None):
+        """Candidate physical plans (n x 4: root, segment, mode, combine) and their features."""
+        o = PlanOpts()
+        o.precision = PRECISION[precision]
+        o.planner = PLANNER["heuristic"]
+        o.root_rel = -1
+        o.segment_rel = -2
+        keep = None
+        if join_parent is not None:
+            keep = (C.c_int32 * len(join_parent))(*[int(x) for x in join_parent])
+            o.join_parent = keep
+        n = C.c_int()
+        nf = C.c_int()
+        self._check(self.lib.lmfao_plan_candidates(self.ctx, C.byref(o), None, None, 0, C.byref(n), C.byref(nf)))
+        cand = (C.c_int32 * (4 * max(1, n.value)))()
+        feats = (C.c_float * (nf.value * max(1, n.value)))()
+        self._check(self.lib.lmfao_plan_candidates(self.ctx, C.byref(o), cand, feats, n.value, C.byref(n),
+                                                   C.byref(nf)))
+        c = np.ctypeslib.as_array(cand)[:4 * n.value].reshape(n.value, 4).copy()
+        f = np.ctypeslib.as_array(feats)[:nf.value * n.value].reshape(n.value, nf.value).copy()
+        return c, f
+
+    def plan_candidate(self, cand, precision="fp32", join_parent=None):
+        root, seg, mode, comb = [int(v) for v in cand]
+        return self.plan(precision=precision, planner="forced", root=root, segment=None if seg == -1 else seg,
+                         mode={0: "auto", 1: "factorised", 2: "per_tuple", 3: "generic"}[mode],
+                         combine={0: "auto", 1: "entry", 2: "block"}[comb], join_parent=join_parent)
 
     def run(self, stream=None):
         self._check(self.lib.lmfao_run(self.ctx, _stream_handle(stream)))
@@ -334,6 +373,75 @@ class Engine:
         n = C.c_int()
         self._check(self.lib.lmfao_kernel_times(self.ctx, ms, 256, C.byref(n)))
         return [(self.lib.lmfao_kernel_name(self.ctx, i).decode(), ms[i]) for i in range(n.value)]
+
+
+class CostModel:
+    """The planner's cost model: a 3-layer, 64-wide perceptron whose forward, backward and
+    Adam kernels are in liblmfao.so. Tensors are torch CUDA float32 tensors."""
+
+    def __init__(self, d, seed=0, device="cuda"):
+        import torch
+        self.lib = library()
+        self.d = d
+        n = self.lib.lmfao_mlp_param_count(d)
+        if n < 0:
+            raise LmfaoError(ERR_ARG, "feature count must be in [1, 256]")
+        g = torch.Generator().manual_seed(seed)
+        p = torch.zeros(n)
+        h = 64
+        w1 = torch.randn(d, h, generator=g) * (2.0 / d) ** 0.5
+        w2 = torch.randn(h, h, generator=g) * (2.0 / h) ** 0.5
+        w3 = torch.randn(h, generator=g) * (1.0 / h) ** 0.5
+        o = 0
+        p[o:o + d * h] = w1.reshape(-1); o += d * h
+        o += h
+        p[o:o + h * h] = w2.reshape(-1); o += h * h
+        o += h
+        p[o:o + h] = w3; o += h
+        self.params = p.to(device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.step = 0
+
+    def _ptr(self, t):
+        return C.c_void_p(t.data_ptr()) if t is not None else None
+
+    def forward(self, x, keep=False, stream=None):
+        import torch
+        n = x.shape[0]
+        y = torch.empty(n, device=x.device)
+        h1 = torch.empty(n, 64, device=x.device) if keep else None
+        h2 = torch.empty(n, 64, device=x.device) if keep else None
+        rc = self.lib.lmfao_mlp_forward(self._ptr(x), n, self.d, self._ptr(self.params), self._ptr(h1), self._ptr(h2),
+                                        self._ptr(y), _stream_handle(stream))
+        if rc != OK:
+            raise LmfaoError(rc, "lmfao_mlp_forward")
+        return (y, h1, h2) if keep else y
+
+    def backward(self, x, h1, h2, gy, stream=None):
+        rc = self.lib.lmfao_mlp_backward(self._ptr(x), x.shape[0], self.d, self._ptr(self.params), self._ptr(h1),
+                                         self._ptr(h2), self._ptr(gy), self._ptr(self.grad), _stream_handle(stream))
+        if rc != OK:
+            raise LmfaoError(rc, "lmfao_mlp_backward")
+        return self.grad
+
+    def train_step(self, x, t, lr=1e-3, stream=None):
+        import torch
+        y, h1, h2 = self.forward(x, keep=True, stream=stream)
+        gy = torch.empty_like(y)
+        loss = torch.zeros(1, device=x.device)
+        rc = self.lib.lmfao_mlp_loss(self._ptr(y), self._ptr(t), x.shape[0], self._ptr(gy), self._ptr(loss),
+                                     _stream_handle(stream))
+        if rc != OK:
+            raise LmfaoError(rc, "lmfao_mlp_loss")
+        self.backward(x, h1, h2, gy, stream)
+        self.step += 1
+        rc = self.lib.lmfao_mlp_adam(self._ptr(self.params), self._ptr(self.grad), self._ptr(self.m), self._ptr(self.v),
+                                     self.params.numel(), self.step, float(lr), _stream_handle(stream))
+        if rc != OK:
+            raise LmfaoError(rc, "lmfao_mlp_adam")
+        return loss
 
 
 def load_workload(engine, rels, queries, where="host"):

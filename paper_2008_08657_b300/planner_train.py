@@ -1,0 +1,201 @@
+"""Learned planner: measured plan times -> MLP cost model -> regret.
+
+For each seeded random snowflake schema (3-8 relations, uniform or Zipf(1.1) keys, 2-12
+float features per relation) with a ridge + group-by batch of the star-join kind (8
+continuous attributes spread over the relations and up to 2 categoricals):
+
+1. ``lmfao_plan_candidates`` lists the candidate physical plans (root relation, segment
+   relation, root pass, combine) with their features;
+2. every candidate is planned (FORCED) and timed with CUDA events (median of a few runs);
+   the best measured time is the exhaustive planner's choice;
+3. the cost model (3 x 64 MLP, ``CostModel``: forward, backward and Adam run in the
+   engine's CUDA kernels) is trained on log-times of the training schemas;
+4. on held-out schemas the learned choice (argmin of the predicted time) and the
+   heuristic choice (default plan) are compared with the exhaustive one:
+   regret = t(choice) / t(best) - 1.
+
+Usage: ``python -m paper_2008_08657_b300.planner_train --schemas 300 --train 200 --out DIR``
+writes DIR/planner_data.npz, DIR/cost_model.txt and DIR/planner_results.json.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import workloads as W
+from .lmfao import COST_MODEL_PATH, CostModel, Engine, LmfaoError
+
+
+def schema_batch(seed, fact_range=(1e5, 5e6), n_conts=8, n_cats=2):
+    """A random snowflake and its ridge + group-by batch (seeded)."""
+    rels, parents, conts, cats = W.random_snowflake(seed, fact_range=fact_range)
+    r = np.random.default_rng(np.random.SeedSequence([seed, 77]))
+    pick = sorted(r.choice(len(conts), min(n_conts, len(conts)), replace=False))
+    cpick = sorted(r.choice(len(cats), min(n_cats, len(cats)), replace=False)) if cats else []
+    qs = W.ridge_batch([conts[i] for i in pick], [cats[i] for i in cpick])
+    return rels, qs
+
+
+def time_current_plan(eng, torch, stream, reps=5, warm=2):
+    for _ in range(warm):
+        eng.run(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    for i in range(reps):
+        ev[2 * i].record(stream)
+        eng.run(stream)
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    return float(np.median([ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)]))
+
+
+def measure_schema(seed, torch, stream, fact_range=(1e5, 5e6), reps=5):
+    """Features and measured times of every candidate plan, and the heuristic plan's time."""
+    rels, qs = schema_batch(seed, fact_range)
+    eng = Engine(0)
+    try:
+        for R in rels:
+            eng.load_relation(R)
+        eng.add_queries(qs)
+        cands, feats = eng.plan_candidates()
+        times = np.full(len(cands), np.inf)
+        for i, c in enumerate(cands):
+            try:
+                eng.plan_candidate(c)
+                times[i] = time_current_plan(eng, torch, stream, reps)
+            except LmfaoError:
+                pass
+        eng.plan()
+        t_heur = time_current_plan(eng, torch, stream, reps)
+    finally:
+        eng.close()
+    return {"seed": seed, "cands": cands, "feats": feats, "times": times, "t_heur": t_heur,
+            "fact_rows": rels[0]["nrows"], "relations": len(rels)}
+
+
+def collect(seeds, fact_range=(1e5, 5e6), log=None):
+    import torch
+    stream = torch.cuda.Stream()
+    out = []
+    for k, s in enumerate(seeds):
+        out.append(measure_schema(s, torch, stream, fact_range))
+        if log and (k + 1) % 20 == 0:
+            log(f"measured {k + 1}/{len(seeds)} schemas")
+    return out
+
+
+def stack(data):
+    X, y, g = [], [], []
+    for i, d in enumerate(data):
+        ok = np.isfinite(d["times"])
+        X.append(d["feats"][ok])
+        y.append(np.log(d["times"][ok]))
+        g.append(np.full(ok.sum(), i))
+    return np.concatenate(X), np.concatenate(y), np.concatenate(g)
+
+
+def train(data, steps=4000, lr=2e-3, seed=0):
+    import torch
+    X, y, _ = stack(data)
+    mean = X.mean(axis=0)
+    std = X.std(axis=0)
+    std[std < 1e-6] = 1.0
+    model = CostModel(X.shape[1], seed=seed)
+    xt = torch.tensor((X - mean) / std, dtype=torch.float32, device="cuda")
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    losses = []
+    for k in range(steps):
+        loss = model.train_step(xt, yt, lr=lr)
+        if k % 500 == 0 or k == steps - 1:
+            losses.append(float(loss.item()))
+    return model, mean, std, losses
+
+
+def save_model(path, model, mean, std):
+    p = model.params.cpu().numpy()
+    with open(path, "w") as f:
+        f.write(f"lmfao-cost-model 1 {model.d}\n")
+        f.write(" ".join(f"{v:.9g}" for v in mean) + "\n")
+        f.write(" ".join(f"{v:.9g}" for v in std) + "\n")
+        f.write(" ".join(f"{v:.9g}" for v in p) + "\n")
+
+
+def load_model(path):
+    import torch
+    with open(path) as f:
+        head = f.readline().split()
+        d = int(head[2])
+        mean = np.array(f.readline().split(), dtype=np.float64)
+        std = np.array(f.readline().split(), dtype=np.float64)
+        p = np.array(f.readline().split(), dtype=np.float32)
+    m = CostModel(d)
+    m.params.copy_(torch.tensor(p))
+    return m, mean, std
+
+
+def regrets(data, model, mean, std):
+    """Per schema: regret of the learned choice and of the heuristic plan."""
+    import torch
+    rl, rh = [], []
+    for d in data:
+        t = d["times"]
+        ok = np.isfinite(t)
+        if not ok.any():
+            continue
+        best = t[ok].min()
+        x = torch.tensor((d["feats"] - mean) / std, dtype=torch.float32, device="cuda")
+        pred = model.forward(x).cpu().numpy()
+        pred[~ok] = np.inf
+        choice = int(np.argmin(pred))
+        rl.append(t[choice] / best - 1.0)
+        rh.append(d["t_heur"] / best - 1.0)
+    return np.array(rl), np.array(rh)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--schemas", type=int, default=300)
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--fact-min", type=float, default=1e5)
+    ap.add_argument("--fact-max", type=float, default=5e6)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--out", default="gpurun_out/planner")
+    args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    t0 = time.time()
+    data = collect(range(args.schemas), (args.fact_min, args.fact_max), log=print)
+    t1 = time.time()
+    np.savez_compressed(os.path.join(args.out, "planner_data.npz"),
+                        **{f"{k}_{i}": v for i, d in enumerate(data) for k, v in d.items()
+                           if isinstance(v, np.ndarray)},
+                        t_heur=np.array([d["t_heur"] for d in data]),
+                        seeds=np.array([d["seed"] for d in data]))
+    tr, te = data[:args.train], data[args.train:]
+    model, mean, std, losses = train(tr, steps=args.steps)
+    save_model(os.path.join(args.out, "cost_model.txt"), model, mean, std)
+    rl, rh = regrets(te, model, mean, std)
+    rl_tr, rh_tr = regrets(tr, model, mean, std)
+    res = {
+        "schemas": args.schemas, "train": len(tr), "test": len(te),
+        "fact_rows_range": [args.fact_min, args.fact_max],
+        "candidates_per_schema": float(np.mean([len(d["cands"]) for d in data])),
+        "collect_seconds": t1 - t0, "train_losses": losses,
+        "test_regret_learned_mean": float(rl.mean()), "test_regret_learned_median": float(np.median(rl)),
+        "test_regret_learned_p90": float(np.quantile(rl, 0.9)),
+        "test_regret_heuristic_mean": float(rh.mean()), "test_regret_heuristic_median": float(np.median(rh)),
+        "test_regret_heuristic_p90": float(np.quantile(rh, 0.9)),
+        "test_within_10pct_learned": float(np.mean(rl <= 0.10)),
+        "test_within_10pct_heuristic": float(np.mean(rh <= 0.10)),
+        "train_regret_learned_mean": float(rl_tr.mean()), "train_regret_heuristic_mean": float(rh_tr.mean()),
+    }
+    with open(os.path.join(args.out, "planner_results.json"), "w") as f:
+        json.dump(res, f, indent=1)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

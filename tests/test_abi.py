@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_entry_points():
     txt = open(os.path.join(ROOT, "include", "lmfao.h")).read()
-    return sorted(set(re.findall(r"LMFAO_API\s+(?:const\s+char\s*\*|int)\s*(lmfao_\w+)\s*\(", txt)))
+    return sorted(set(re.findall(r"LMFAO_API\s+(?:const\s+char\s*\*|int64_t|int)\s*(lmfao_\w+)\s*\(", txt)))
 
 
 def test_library_exports_every_declared_entry_point():
