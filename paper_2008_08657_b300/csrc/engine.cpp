@@ -590,7 +590,64 @@ struct Planner {
     std::vector<DGroupRef> og, ig;
     int64_t out = 0, cellmul = 1;
     bool outer_dep = false;
+    int leaf = -1;  // filter index within the filter family (-1: filter kept as indicators)
   };
+
+  // Filter family: the distinct filters of the batch when they are pairwise disjoint
+  // conjunctions (the leaves of a decision-tree level). Each tuple satisfies at most one;
+  // its index is computed once per tuple instead of evaluating every filtered item.
+  struct Family {
+    std::vector<std::vector<int>> filters;  // predicate factor ids per filter
+    std::vector<int> preds;                 // distinct predicate factor ids
+    std::vector<int> qfilter;               // per query: filter index or -1
+  } fam;
+  bool use_family = false;
+
+  static bool complementary(const Fac &a, const Fac &b) {
+    if (a.rel != b.rel || a.col != b.col || a.t != b.t) return false;
+    auto pairs = [&](int x, int y) { return (a.op == x && b.op == y) || (a.op == y && b.op == x); };
+    return pairs(LMFAO_LE, LMFAO_GT) || pairs(LMFAO_LT, LMFAO_GE) || pairs(LMFAO_EQ, LMFAO_NE);
+  }
+
+  bool detect_family() {
+    fam = Family{};
+    fam.qfilter.assign(ctx->queries.size(), -1);
+    for (int q = 0; q < (int)ctx->queries.size(); ++q) {
+      const QueryIn &Q = ctx->queries[q];
+      if (Q.filters.empty()) continue;
+      std::vector<int> f;
+      for (auto &pd : Q.filters) f.push_back(fac_id(make_fac(pd.attr, true, 1, pd.op, pd.t)));
+      std::sort(f.begin(), f.end());
+      f.erase(std::unique(f.begin(), f.end()), f.end());
+      int at = -1;
+      for (size_t i = 0; i < fam.filters.size(); ++i) if (fam.filters[i] == f) at = (int)i;
+      if (at < 0) { fam.filters.push_back(f); at = (int)fam.filters.size() - 1; }
+      fam.qfilter[q] = at;
+    }
+    const int K = (int)fam.filters.size();
+    if (K < 2 || K > FMAXFAM) return false;
+    for (int a = 0; a < K; ++a)
+      for (int b = a + 1; b < K; ++b) {
+        bool disjoint = false;
+        for (int x : fam.filters[a])
+          for (int y : fam.filters[b]) disjoint = disjoint || complementary(P.facs[x], P.facs[y]);
+        if (!disjoint) return false;
+      }
+    std::set<int> ps;
+    for (auto &f : fam.filters) ps.insert(f.begin(), f.end());
+    fam.preds.assign(ps.begin(), ps.end());
+    if ((int)fam.preds.size() > FMAXBIT) return false;
+    for (int pfac : fam.preds) {
+      const Fac &fc = P.facs[pfac];
+      if (fc.rel == t.root) {
+        if (seg_digit_of(fc.col) >= 0) return false;  // predicates on segment-key digits stay indicators
+        continue;
+      }
+      // a predicate on a non-root relation is one bit of its (unique) joined tuple
+      if (P.views[P.branch[fc.rel]].count_bound > 1.0) return false;
+    }
+    return true;
+  }
 
   std::vector<ItemD> decompose() {
     int root = t.root;
@@ -627,11 +684,14 @@ struct Planner {
       std::vector<int64_t> stride(qo.dom.size(), 1);
       for (int i = (int)qo.dom.size() - 2; i >= 0; --i) stride[i] = stride[i + 1] * qo.dom[i + 1];
       std::vector<int> inds;
-      for (auto &p : Q.filters) inds.push_back(fac_id(make_fac(p.attr, true, 1, p.op, p.t)));
+      const int leaf = use_family ? fam.qfilter[q] : -1;
+      if (leaf < 0)
+        for (auto &p : Q.filters) inds.push_back(fac_id(make_fac(p.attr, true, 1, p.op, p.t)));
       for (int a = -1; a < qo.naggs; ++a) {
         ItemD it;
         it.q = q;
         it.a = a;
+        it.leaf = leaf;
         Term term = inds;
         if (a >= 0)
           for (auto &f : Q.aggs[a]) {
@@ -701,6 +761,7 @@ struct Planner {
         }
         if (b0) {
           DCombItem c{};
+          c.sel = -1;
           c.psi = it.psi;
           c.block = -1;
           c.col = pos;
@@ -754,15 +815,54 @@ struct Planner {
     };
     struct Pending { ItemD it; int j, w; int kind; int set; };
     std::vector<Pending> pend;
+    F.b3leaf = 1;
+    bool b3_plain = false, b3_leafed = false;
+    const int K = use_family ? (int)fam.filters.size() : 0;
     for (const ItemD &it : items) {
       int j = mono_of(it.rowf);
       int vcol = it.ipart.empty() ? 0 : it.ipart[0].second;
-      bool all_view = true;
-      for (auto &g : it.ig) all_view = all_view && g.src == 3;
+      bool all_view = true, all_row = true;
+      for (auto &g : it.ig) {
+        all_view = all_view && g.src == 3;
+        all_row = all_row && g.src == 2;
+      }
+      if (it.leaf >= 0) {
+        if (!it.ig.empty() && all_view && !it.outer_dep && !it.ipart.empty()) {
+          b3_leafed = true;
+          pend.push_back({it, j, vcol, 3, -1});
+        } else if (!it.ig.empty() && all_row && !it.outer_dep) {
+          pend.push_back({it, j, wcol_of(vcol), 4, -1});
+        } else {
+          if (it.ig.size() > 1) return false;
+          // per-segment sums grouped by the tuple's filter index (and at most one inner code)
+          DGroupRef lr{};
+          lr.src = 4;
+          std::vector<DGroupRef> key{lr};
+          key.insert(key.end(), it.ig.begin(), it.ig.end());
+          std::vector<int64_t> dom{K};
+          int64_t G = K;
+          for (size_t i = 1; i < key.size(); ++i) {
+            const DGroupRef &g = key[i];
+            int64_t dd = g.src == 3 ? P.gitems[code_group(P.inner[0], g.b)].dom
+                                    : (g.kind == LMFAO_GB_BUCKET ? g.nthr + 1 : gdom_of_slot(g));
+            dom.push_back(dd);
+            G *= dd;
+          }
+          if (G > 4096) return false;
+          int set = find_or_add_b1(key, dom, G);
+          if (set < 0) return false;
+          ItemD it2 = it;
+          it2.ig = key;
+          it2.ig[0].stride = 0;  // the filter index selects; it is not an output group
+          pend.push_back({it2, j, wcol_of(vcol), 1, set});
+        }
+        continue;
+      }
       // Items that do not depend on the outer side and read inner view columns (or group by
       // inner codes) go to the view from the root to the inner relation (B3); the rest of the
       // ungrouped items are per-segment sums (B0).
       if (!it.outer_dep && all_view && !it.ipart.empty() && (vcol != 0 || !it.ig.empty())) {
+        b3_plain = true;
         pend.push_back({it, j, vcol, 3, -1});
         continue;
       }
@@ -782,34 +882,18 @@ struct Planner {
         G *= d;
       }
       if (G > 4096) return false;
-      int set = -1;
-      for (size_t s2 = 0; s2 < F.b1.size(); ++s2) {
-        auto &S = F.b1[s2];
-        if (S.refs.size() != key.size()) continue;
-        bool same = true;
-        for (size_t i = 0; i < key.size(); ++i)
-          same = same && S.refs[i].src == key[i].src && S.refs[i].a == key[i].a && S.refs[i].b == key[i].b &&
-                 S.refs[i].kind == key[i].kind && S.thrs[i] == thr_of(key[i]);
-        if (same) { set = (int)s2; break; }
-      }
-      if (set < 0) {
-        if (F.b1.size() >= FMAXB1) return false;
-        PhysPlan::Fast::B1 S;
-        S.refs = key;
-        for (auto &g : key) S.thrs.push_back(thr_of(g));
-        S.dom = dom;
-        S.G = G;
-        F.b1.push_back(S);
-        set = (int)F.b1.size() - 1;
-      }
+      int set = find_or_add_b1(key, dom, G);
+      if (set < 0) return false;
       pend.push_back({it, j, wcol_of(vcol), 1, set});
     }
+    if (b3_plain && b3_leafed) return false;
+    if (b3_leafed) F.b3leaf = K;
     // Lean variant: root-level monomials of degree <= 2 over at most 3 value columns and no
     // indicators. The monomial list becomes the full basis (1, x_i, x_i x_j) in the order
     // the kernel computes it.
     F.lean = false;
     {
-      bool ok = P.inner.size() <= 1 && (P.inner.empty() || P.views[P.inner[0]].keycols.size() == 1);
+      bool ok = P.inner.size() <= 1 && (P.inner.empty() || P.views[P.inner[0]].keycols.size() == 1) && !use_family;
       std::vector<int> xcols;
       std::vector<std::map<int, int>> exps(F.monos.size());
       for (size_t j = 0; j < F.monos.size() && ok; ++j) {
@@ -870,6 +954,7 @@ struct Planner {
       const ItemD &it = pd.it;
       if (pd.kind == 0) {
         DCombItem c{};
+          c.sel = -1;
         c.psi = it.psi;
         c.block = -1;
         c.integral = it.integral;
@@ -909,10 +994,12 @@ struct Planner {
           pos = (int)cols.size() - 1;
         }
         DCombItem c{};
+          c.sel = -1;
         c.psi = it.psi;
         c.block = pd.set;
         c.integral = it.integral;
         c.yint = colint ? 1 : 0;
+        c.sel = it.leaf;
         c.col = pos;
         c.og0 = add_grefs(it.og);
         c.nog = (int)it.og.size();
@@ -921,6 +1008,18 @@ struct Planner {
         c.out = it.out;
         c.cellmul = it.cellmul;
         P.comb.push_back(c);
+      } else if (pd.kind == 4) {
+        PhysPlan::Fast::B4 b;
+        b.j = pd.j;
+        b.w = pd.w;
+        b.integral = it.integral;
+        b.sel = it.leaf;
+        b.refs = it.ig;
+        b.q = it.q;
+        b.out = it.out;
+        b.cellmul = it.cellmul;
+        F.b4.push_back(b);
+        if ((int)F.b4.size() > FMAXB4) return false;
       } else {
         int pos = -1;
         for (size_t i = 0; i < F.p3.size(); ++i) if (F.p3[i].first == pd.j && F.p3[i].second == it.integral) pos = (int)i;
@@ -934,12 +1033,35 @@ struct Planner {
         b.w = it.integral ? pd.w : pd.w;  // FP64 view column; integral values are exact there
         (void)v;
         b.c = pos;
+        b.leaf = it.leaf;
         b.integral = it.integral;
         b.ig0 = add_grefs(it.ig);
         b.nig = (int)it.ig.size();
         b.out = it.out;
         b.cellmul = it.cellmul;
         F.b3.push_back(b);
+      }
+    }
+    if (use_family) {
+      F.fam_k = K;
+      F.fmask.assign(K, 0u);
+      F.obits.clear();
+      F.ibits.clear();
+      F.rbits.clear();
+      for (size_t pi = 0; pi < fam.preds.size(); ++pi) {
+        const int pf = fam.preds[pi];
+        const Fac &fc = P.facs[pf];
+        for (int f = 0; f < K; ++f)
+          if (std::find(fam.filters[f].begin(), fam.filters[f].end(), pf) != fam.filters[f].end())
+            F.fmask[f] |= 1u << pi;
+        if (fc.rel == t.root) {
+          F.rbits.push_back({rowslot(fc.col), (int)pi, pf});
+        } else {
+          const int b = P.branch[fc.rel];
+          const int col = view_col(b, Term{pf});  // filtered COUNT: 1 when the tuple satisfies it
+          if (P.kind[fc.rel] == 1) F.obits.push_back({outer_idx(b), col, (int)pi});
+          else F.ibits.push_back({col, (int)pi, 0});
+        }
       }
     }
     if (F.lean) {
@@ -953,6 +1075,27 @@ struct Planner {
     }
     F.on = true;
     return true;
+  }
+
+  int find_or_add_b1(const std::vector<DGroupRef> &key, const std::vector<int64_t> &dom, int64_t G) {
+    auto &F = P.fast;
+    for (size_t s2 = 0; s2 < F.b1.size(); ++s2) {
+      auto &S = F.b1[s2];
+      if (S.refs.size() != key.size()) continue;
+      bool same = true;
+      for (size_t i = 0; i < key.size(); ++i)
+        same = same && S.refs[i].src == key[i].src && S.refs[i].a == key[i].a && S.refs[i].b == key[i].b &&
+               S.refs[i].kind == key[i].kind && S.thrs[i] == thr_of(key[i]);
+      if (same) return (int)s2;
+    }
+    if (F.b1.size() >= FMAXB1) return -1;
+    PhysPlan::Fast::B1 S;
+    S.refs = key;
+    for (auto &g : key) S.thrs.push_back(thr_of(g));
+    S.dom = dom;
+    S.G = G;
+    F.b1.push_back(S);
+    return (int)F.b1.size() - 1;
   }
 
   int code_group(int r, int code) const {  // group item behind a view code
@@ -1303,12 +1446,86 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   }
   for (auto &b3 : F.b3) b3.c = d.p3col[b3.c];
   int64_t nk3 = std::max<int64_t>(1, d.nkeys);
-  d.p3f = (double *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3f) * 8);
-  d.p3i = (unsigned long long *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3i) * 8);
+  const int lsplit = std::max(1, F.b3leaf);
+  d.p3f = (double *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3f) * lsplit * 8);
+  d.p3i = (unsigned long long *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3i) * lsplit * 8);
   d.ticket = (unsigned int *)P.arena.alloc(16);
   d.thr = cb.thr;
   // inner view table (staged per run by fast_prep) and codes
   for (auto &b3 : F.b3) (void)b3;
+  // filter family: predicate bits per segment (outer), per inner key (inner), per tuple (root)
+  d.nfam = F.fam_k;
+  d.b3leaf = std::max(1, F.b3leaf);
+  d.ibit_code = -1;
+  d.nob = d.nrb = 0;
+  std::vector<int2> ibits;
+  if (d.nfam) {
+    for (int f = 0; f < d.nfam; ++f) d.fmask[f] = F.fmask[f];
+    for (auto &b : F.obits) {
+      d.obit_outer[d.nob] = b[0];
+      d.obit_col[d.nob] = b[1];
+      d.obit_pos[d.nob] = b[2];
+      ++d.nob;
+    }
+    for (auto &b : F.rbits) {
+      const Fac &fc = P.facs[b[2]];
+      d.rb[d.nrb] = DFac{b[0], 1, 1, fc.op, fc.t};
+      d.rb_pos[d.nrb] = b[1];
+      ++d.nrb;
+    }
+    for (auto &b : F.ibits) ibits.push_back(make_int2(b[0], b[1]));
+    if (!ibits.empty()) {
+      d.ibit_code = (int)codecol.size();
+      codecol.push_back(-1);
+    }
+    d.nouter = cb.nouter;
+    for (int o = 0; o < cb.nouter; ++o) d.outer[o] = cb.outer[o];
+    d.seg = cb.seg;
+  }
+  P.fibits_dev = P.arena.upload(ibits.empty() ? std::vector<int2>{make_int2(0, 0)} : ibits, s);
+  P.fnibits = (int)ibits.size();
+  if (d.b3leaf > 1) {
+    for (auto &b3 : F.b3) b3.c = b3.c * d.b3leaf + b3.leaf;  // already within-kind index
+  }
+  // B4: CTA-private outputs mirrored in shared memory per query region
+  d.nb4 = (int)F.b4.size();
+  {
+    std::vector<DGroupRef> g4;
+    std::vector<DMirror> mir;
+    std::map<std::pair<int, int>, int> base;  // (query, integral) -> shared offset
+    int fcells = 0, icells = 0;
+    for (int i = 0; i < d.nb4; ++i) {
+      const auto &b = F.b4[i];
+      const QueryOut &q = P.qout[b.q];
+      const int64_t gbase = b.integral ? q.io : q.fo;
+      const int64_t len = b.integral ? q.cells * (1 + q.naggs) : q.cells * q.naggs;
+      auto key = std::make_pair(b.q, b.integral);
+      auto it = base.find(key);
+      if (it == base.end()) {
+        int &cells = b.integral ? icells : fcells;
+        mir.push_back(DMirror{gbase, cells, (int)len, b.integral, 0});
+        it = base.emplace(key, cells).first;
+        cells += (int)len;
+      }
+      d.b4_j[i] = b.j;
+      d.b4_w[i] = b.w;
+      d.b4_int[i] = b.integral;
+      d.b4_sel[i] = b.sel;
+      d.b4_g0[i] = (int)g4.size();
+      d.b4_ng[i] = (int)b.refs.size();
+      g4.insert(g4.end(), b.refs.begin(), b.refs.end());
+      d.b4_so[i] = it->second + (int)(b.out - gbase);
+      d.b4_cellmul[i] = b.cellmul;
+    }
+    if (fcells + icells > 24 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: per-CTA outputs too large");
+    d.b4_fcells = fcells;
+    d.b4_icells = icells;
+    d.nb4mirror = (int)mir.size();
+    d.b4mirror = P.arena.upload(mir.empty() ? std::vector<DMirror>{DMirror{}} : mir, s);
+    d.grefs4 = P.arena.upload(g4.empty() ? std::vector<DGroupRef>{DGroupRef{}} : g4, s);
+    d.fsum = P.fsum;
+    d.icnt = P.icnt;
+  }
   d.ncode = (int)codecol.size();
   void *table = P.arena.alloc((size_t)nk3 * std::max(1, d.nw) * ts);
   int *codes = (int *)P.arena.alloc((size_t)nk3 * std::max(1, d.ncode) * 4);
@@ -1318,9 +1535,9 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   P.fcodecol_dev = P.arena.upload(codecol.empty() ? std::vector<int>{0} : codecol, s);
   // shared memory: the table and the B3 partials when they fit (1 CTA of 512 threads per SM)
   P.fast_block = P.fp64 ? 256 : 512;
-  size_t pbytes = ts * (size_t)d.nkeys * d.n3f + 4 * (size_t)d.nkeys * d.n3i;
+  size_t pbytes = (ts * (size_t)d.nkeys * d.n3f + 4 * (size_t)d.nkeys * d.n3i) * lsplit;
   size_t vbytes = d.ni ? ts * (size_t)d.nkeys * d.nw + 4 * (size_t)d.nkeys * d.ncode : 0;
-  size_t hbytes = (size_t)(P.fast_block / 32) * (d.hist_f + d.hist_i) * 4;
+  size_t hbytes = (size_t)(P.fast_block / 32) * (d.hist_f + d.hist_i) * 4 + (ts * d.b4_fcells + 4 * d.b4_icells) + 64;
   if (hbytes > 96 * 1024) throw Error(LMFAO_ERR_UNSUPPORTED, "internal: group histograms too large");
   d.smem_p = d.n3 && pbytes + hbytes <= 190 * 1024 ? 1 : 0;
   d.smem_view = d.ni && vbytes + (d.smem_p ? pbytes : 0) + hbytes <= 190 * 1024 ? 1 : 0;
@@ -1339,8 +1556,8 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   f.p3f = d.p3f;
   f.p3i = d.p3i;
   f.n3 = d.n3;
-  f.n3f = d.n3f;
-  f.n3i = d.n3i;
+  f.n3f = d.n3f * lsplit;
+  f.n3i = d.n3i * lsplit;
   f.nitems = (int)F.b3.size();
   f.items = P.arena.upload(F.b3, s);
   f.grefs = cb.grefs;
@@ -1457,7 +1674,12 @@ void setup_combine2(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPart> &ppart
       ent.push_back(e);
     } else {
       const DB1Set &S = P.b1sets[it.block];
+      const auto &srefs = P.fast.b1[it.block].refs;
       for (int g = 0; g < S.G; ++g) {
+        bool pick = true;
+        for (int i = 0; i < S.nref; ++i)
+          if (srefs[i].src == 4 && (g / S.radix[i]) % S.dom[i] != it.sel) pick = false;
+        if (!pick) continue;
         DEntry e{};
         e.psi = it.psi;
         e.ycol = it.yint ? (int)(d.n0i + S.gbase_i + (int64_t)g * S.ni + it.col)
@@ -1687,7 +1909,12 @@ bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
       add(it.col, it.integral ? 1 : 0, 0);  // B0: integral items read PHI0 integral columns
     } else {
       const DB1Set &S = P.b1sets[it.block];
+      const auto &srefs = P.fast.b1[it.block].refs;
       for (int g = 0; g < S.G; ++g) {
+        bool pick = true;
+        for (int i = 0; i < S.nref; ++i)
+          if (srefs[i].src == 4 && (g / S.radix[i]) % S.dom[i] != it.sel) pick = false;
+        if (!pick) continue;
         int64_t ic = 0;
         for (int i = 0; i < S.nref; ++i) ic += ((g / S.radix[i]) % S.dom[i]) * P.grefs[it.ig0 + i].stride;
         int c = it.yint ? (int)(d.n0i + S.gbase_i + (int64_t)g * S.ni + it.col)
@@ -1975,13 +2202,13 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     if (d.n0i) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * d.n0i * 8, s));
     if (d.phi1f_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1f, 0, P.nseg * d.phi1f_seg * 4, s));
     if (d.phi1i_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1i, 0, P.nseg * d.phi1i_seg * 4, s));
-    if (d.n3f) LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3f * 8, s));
-    if (d.n3i) LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3i * 8, s));
+    if (d.n3f) LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3f * d.b3leaf * 8, s));
+    if (d.n3i) LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3i * d.b3leaf * 8, s));
     LMFAO_CUDA(cudaMemsetAsync(d.ticket, 0, 4, s));
     if (d.ni) {
       const View &v = P.views[P.inner[0]];
       launch_fast_prep(d, v.v64, (int)v.cols.size(), P.fwcol_dev, v.vcodes, (int)v.codes.size(), P.fcodecol_dev,
-                       const_cast<void *>(d.table), const_cast<int *>(d.codes), P.fp64, s);
+                       const_cast<void *>(d.table), const_cast<int *>(d.codes), P.fp64, s, P.fibits_dev, P.fnibits);
     }
     if (!launch_fast_pass(d, P.fp64, P.fast_grid, P.fast_block, s))
       throw Error(LMFAO_ERR_UNSUPPORTED, "internal: no root-pass variant for this shape");
@@ -2035,7 +2262,7 @@ std::string json_escape(const std::string &x) {
 // ======================================================================================
 namespace {
 
-constexpr int NFEAT = 24;
+constexpr int NFEAT = 32;
 
 lmfao_plan_opts default_opts() {
   lmfao_plan_opts o{};
@@ -2111,6 +2338,27 @@ std::vector<float> plan_features(const lmfao_ctx *ctx, const PhysPlan &P, const 
   f[21] = P.root == largest_relation(ctx) ? 1.f : 0.f;
   f[22] = lg(other_rows);
   f[23] = lg(rows * (1.0 + (double)P.inner.size()));
+  // work estimates of the plan's kernels
+  double rowbytes = 0;
+  for (int c : P.rowcols) rowbytes += ctx->rels[P.root].cols[c].dtype == LMFAO_U8 ? 1 : 4;
+  double b1cols = 0;
+  for (auto &S : P.fast.b1) b1cols += (double)(S.fcols.size() + S.icols.size());
+  double entries = 0;
+  for (auto &c : P.comb) entries += c.block >= 0 && c.block < (int)P.fast.b1.size() ? (double)P.fast.b1[c.block].G : 1.0;
+  double view_work = 0, inner_table = 0;
+  for (int r : t.post) view_work += (double)ctx->rels[r].nrows * (double)P.views[r].cols.size();
+  for (int c : P.inner) inner_table += (double)P.views[c].nkeys * (double)(P.fast.on ? P.fast.wcols.size() : P.views[c].cols.size());
+  const double block = P.prefix_len > 0 ? std::max<double>(1, (double)P.nseg / (double)std::accumulate(
+                                                P.segdom.begin(), P.segdom.begin() + P.prefix_len, int64_t(1),
+                                                std::multiplies<int64_t>())) : 1.0;
+  f[24] = lg(rows * rowbytes);
+  f[25] = lg(rows * (b1cols + (double)P.fast.p3.size() + (double)P.fast.b4.size() + (double)P.b2.size()));
+  f[26] = lg(entries * (double)P.nseg);
+  f[27] = lg(entries * (double)P.nseg / block);
+  f[28] = lg(view_work);
+  f[29] = lg((double)P.nseg * (b0 + b1g));
+  f[30] = lg(inner_table);
+  f[31] = (float)(t.post.size() * 2 + 3);
   return f;
 }
 
@@ -2141,11 +2389,25 @@ void build_plan(lmfao_ctx *ctx, const lmfao_plan_opts &o, bool dry, std::vector<
   compute_multiplicities(ctx, *P, ctx->tree);
   pl.choose_segments(o);
   {
-    auto items = pl.decompose();
-    if (!(P->mode == LMFAO_MODE_FACTORISED && pl.route_fast(items))) {
+    bool done = false;
+    if (P->mode == LMFAO_MODE_FACTORISED && pl.detect_family()) {
+      pl.use_family = true;
+      auto items = pl.decompose();
+      done = pl.route_fast(items);
+      if (!done) {  // filters go back to indicator factors
+        pl.use_family = false;
+        P->qout.clear();
+      }
+    }
+    if (!done) {
       P->fast = PhysPlan::Fast{};
       P->comb.clear();
-      pl.route_generic(items, P->mode);
+      auto items = pl.decompose();
+      if (!(P->mode == LMFAO_MODE_FACTORISED && pl.route_fast(items))) {
+        P->fast = PhysPlan::Fast{};
+        P->comb.clear();
+        pl.route_generic(items, P->mode);
+      }
     }
   }
   for (int c : P->inner)
@@ -2232,12 +2494,14 @@ double time_plan(lmfao_ctx *ctx, int warm, int reps) {
 }
 
 struct CostModelFile {
-  int d = 0;
-  std::vector<float> mean, std, params;
+  int d = 0, nmodels = 1;
+  std::vector<float> mean, std;
+  std::vector<std::vector<float>> params;  // one parameter vector per ensemble member
 };
 
-// Text file: "lmfao-cost-model 1 <d>", then d means, d standard deviations, then the
-// lmfao_mlp_param_count(d) parameters (whitespace separated).
+// Text file: "lmfao-cost-model 2 <d> <nmodels>", then d feature means, d standard
+// deviations, then nmodels x lmfao_mlp_param_count(d) parameters (whitespace separated).
+// The prediction is the mean over the ensemble.
 CostModelFile load_cost_model(const char *path) {
   if (!path) throw Error(LMFAO_ERR_ARG, "the learned planner needs a cost model file");
   FILE *f = std::fopen(path, "r");
@@ -2245,8 +2509,9 @@ CostModelFile load_cost_model(const char *path) {
   CostModelFile cm;
   char tag[64] = {0};
   int ver = 0;
-  bool ok = std::fscanf(f, "%63s %d %d", tag, &ver, &cm.d) == 3 && std::string(tag) == "lmfao-cost-model" &&
-            ver == 1 && cm.d == NFEAT;
+  bool ok = std::fscanf(f, "%63s %d %d %d", tag, &ver, &cm.d, &cm.nmodels) == 4 &&
+            std::string(tag) == "lmfao-cost-model" && ver == 2 && cm.d == NFEAT && cm.nmodels >= 1 &&
+            cm.nmodels <= 64;
   int64_t np = ok ? mlp_param_count(cm.d) : 0;
   auto rd = [&](std::vector<float> &v, int64_t k) {
     v.resize(k);
@@ -2254,7 +2519,8 @@ CostModelFile load_cost_model(const char *path) {
   };
   if (ok) rd(cm.mean, cm.d);
   if (ok) rd(cm.std, cm.d);
-  if (ok) rd(cm.params, np);
+  cm.params.resize(ok ? cm.nmodels : 0);
+  for (int m = 0; m < cm.nmodels && ok; ++m) rd(cm.params[m], np);
   std::fclose(f);
   if (!ok) throw Error(LMFAO_ERR_ARG, std::string("malformed cost model ") + path);
   for (float &x : cm.std)
@@ -2265,13 +2531,18 @@ CostModelFile load_cost_model(const char *path) {
 std::vector<float> predict(const CostModelFile &cm, const std::vector<float> &X, int n) {
   float *dx = nullptr, *dp = nullptr, *dy = nullptr;
   LMFAO_CUDA(cudaMalloc(&dx, X.size() * 4 + 16));
-  LMFAO_CUDA(cudaMalloc(&dp, cm.params.size() * 4 + 16));
+  LMFAO_CUDA(cudaMalloc(&dp, cm.params[0].size() * 4 + 16));
   LMFAO_CUDA(cudaMalloc(&dy, (size_t)n * 4 + 16));
   LMFAO_CUDA(cudaMemcpy(dx, X.data(), X.size() * 4, cudaMemcpyHostToDevice));
-  LMFAO_CUDA(cudaMemcpy(dp, cm.params.data(), cm.params.size() * 4, cudaMemcpyHostToDevice));
-  int rc = lmfao_mlp_forward(dx, n, cm.d, dp, nullptr, nullptr, dy, nullptr);
-  std::vector<float> y(n);
-  cudaError_t e = cudaMemcpy(y.data(), dy, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  std::vector<float> y(n, 0.f), ym(n);
+  int rc = LMFAO_OK;
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < cm.nmodels && rc == LMFAO_OK && e == cudaSuccess; ++m) {
+    e = cudaMemcpy(dp, cm.params[m].data(), cm.params[m].size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) rc = lmfao_mlp_forward(dx, n, cm.d, dp, nullptr, nullptr, dy, nullptr);
+    if (rc == LMFAO_OK && e == cudaSuccess) e = cudaMemcpy(ym.data(), dy, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    for (int i = 0; i < n; ++i) y[i] += ym[i] / cm.nmodels;
+  }
   cudaFree(dx);
   cudaFree(dp);
   cudaFree(dy);
@@ -2727,6 +2998,7 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false")
       << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false")
       << ",\"block_combine\":" << (P.use_c3 ? "true" : "false") << ",\"prefix_digits\":" << P.prefix_len
+      << ",\"filter_family\":" << P.fast.fam_k << ",\"cta_items\":" << P.fast.b4.size()
       << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork

@@ -222,7 +222,7 @@ struct DCombItem {
   int64_t out;      // base cell of the query output (float: fsum index; int: icnt index)
   int64_t cellmul;  // multiplier from cell index to the output array index
   int yint;         // B1: the column is an integral (count) column
-  int pad_;
+  int sel;          // B1: filter index the entry reads (-1: every group code)
 };
 
 // Outer term: segment-key factors x product of outer view columns.

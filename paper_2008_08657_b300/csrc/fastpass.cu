@@ -67,11 +67,19 @@ __device__ __forceinline__ T sel(const T (&a)[N], int i) {
 
 template <typename T>
 __global__ void fast_prep_kernel(int64_t nkeys, const double *v64, int vcols, const int *wcol, int nw, T *table,
-                                 const int32_t *vcodes, int vncodes, const int *codecol, int ncode, int *codes) {
+                                 const int32_t *vcodes, int vncodes, const int *codecol, int ncode, int *codes,
+                                 const int2 *ib, int nib, int ibcode) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nkeys; k += stride) {
     for (int w = 0; w < nw; ++w) table[k * nw + w] = (T)v64[k * vcols + wcol[w]];
-    for (int c = 0; c < ncode; ++c) codes[k * ncode + c] = vcodes[k * vncodes + codecol[c]];
+    for (int c = 0; c < ncode; ++c)
+      if (c != ibcode) codes[k * ncode + c] = vcodes[k * vncodes + codecol[c]];
+    if (ibcode >= 0) {  // inner predicate bits: the (unique) tuple of key k satisfies predicate j
+      unsigned int bits = 0;
+      for (int j = 0; j < nib; ++j)
+        if (v64[k * vcols + ib[j].x] > 0.0) bits |= 1u << ib[j].y;
+      codes[k * ncode + ibcode] = (int)bits;
+    }
   }
 }
 
@@ -102,9 +110,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
   T *Pf = reinterpret_cast<T *>(smem);
   unsigned int *Pi = nullptr;
   if (d.smem_p) {
-    off += sizeof(T) * (size_t)d.nkeys * d.n3f;
+    off += sizeof(T) * (size_t)d.nkeys * d.n3f * d.b3leaf;
     Pi = reinterpret_cast<unsigned int *>(smem + off);
-    off += 4 * (size_t)d.nkeys * d.n3i;
+    off += 4 * (size_t)d.nkeys * d.n3i * d.b3leaf;
   }
   off = (off + 15) & ~(size_t)15;
   const T *table = reinterpret_cast<const T *>(d.table);
@@ -122,9 +130,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
   off = (off + 15) & ~(size_t)15;
   float *hf = reinterpret_cast<float *>(smem + off) + (size_t)warp * (d.hist_f + d.hist_i);
   unsigned int *hi = reinterpret_cast<unsigned int *>(hf + d.hist_f);
+  off += (size_t)nwarps * (d.hist_f + d.hist_i) * 4;
+  off = (off + 15) & ~(size_t)15;
+  T *b4f = reinterpret_cast<T *>(smem + off);  // CTA-private outputs of B4 items
+  off += sizeof(T) * (size_t)d.b4_fcells;
+  off = (off + 15) & ~(size_t)15;
+  unsigned int *b4i = reinterpret_cast<unsigned int *>(smem + off);
+  for (int i = tid; i < d.b4_fcells; i += bs) b4f[i] = T(0);
+  for (int i = tid; i < d.b4_icells; i += bs) b4i[i] = 0u;
   if (d.smem_p) {
-    for (int64_t i = tid; i < d.nkeys * d.n3f; i += bs) Pf[i] = T(0);
-    for (int64_t i = tid; i < d.nkeys * d.n3i; i += bs) Pi[i] = 0u;
+    for (int64_t i = tid; i < d.nkeys * d.n3f * d.b3leaf; i += bs) Pf[i] = T(0);
+    for (int64_t i = tid; i < d.nkeys * d.n3i * d.b3leaf; i += bs) Pi[i] = 0u;
   }
   if (tid == 0) {
     for (int s = 0; s < FMAXB1; ++s) sd.b1[s] = d.b1[s];
@@ -147,6 +163,18 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
     if (nb1) {
       for (int i = lane; i < d.hist_f + d.hist_i; i += 32) hf[i] = 0.f;  // hi follows hf
       __syncwarp();
+    }
+    unsigned int obits = 0;
+    if (d.nfam && d.nob) {  // predicates on outer relations, once per segment
+      unsigned int mine = 0;
+      if (lane < d.nob) {
+        const DOuter &o = d.outer[d.obit_outer[lane]];
+        int64_t ok = 0;
+        for (int i = 0; i < d.seg.ndig; ++i)
+          if (o.dstride[i]) ok += ((int64_t)wk.seg / d.seg.radix[i]) % d.seg.dom[i] * o.dstride[i];
+        if (__ldg(o.v.v64 + ok * o.v.ncols + d.obit_col[lane]) > 0.0) mine = 1u << d.obit_pos[lane];
+      }
+      obits = __reduce_or_sync(0xffffffffu, mine);
     }
     T acc[NM][W];
 #pragma unroll
@@ -222,6 +250,15 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
         for (int j = 0; j < NM; ++j)
 #pragma unroll
           for (int w = 0; w < W; ++w) acc[j][w] += m[j] * v[w];
+        int leaf = -1;
+        if (d.nfam) {  // the filter of the family this tuple satisfies (filters are disjoint)
+          unsigned int bits = obits;
+          if (d.ibit_code >= 0) bits |= (unsigned int)codes[(int64_t)k * ncode + d.ibit_code];
+          for (int q = 0; q < d.nrb; ++q)
+            if (pred(d.col[d.rb[q].col], r, d.rb[q].op, d.rb[q].t)) bits |= 1u << d.rb_pos[q];
+          for (int f = 0; f < d.nfam; ++f)
+            if ((bits & d.fmask[f]) == d.fmask[f]) { leaf = f; break; }
+        }
         for (int s = 0; s < nb1; ++s) {
           const DFastB1 &b = sd.b1[s];
           int g = 0;
@@ -229,7 +266,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
           for (int i = 0; i < b.nref; ++i) {
             const DGroupRef &q = b.ref[i];
             int code = (q.src == 3) ? codes[(int64_t)k * ncode + q.b]
-                                    : row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
+                       : (q.src == 4) ? leaf
+                                      : row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
             if (code < 0) ok = false;
             g += code * (int)q.stride;
           }
@@ -243,19 +281,36 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
             if (val != T(0)) atomicAdd(hi + b.smem_i + g * b.ni + c, (unsigned int)val);
           }
         }
-        for (int c = 0; c < n3; ++c) {
+        const int lsplit = d.b3leaf;
+        for (int c = 0; c < n3 && (lsplit == 1 || leaf >= 0); ++c) {
           T val = sel<NM, T>(m, sd.j3[c]);
           if (val == T(0)) continue;
-          const int pc = sd.p3col[c];
+          const int pc = sd.p3col[c] * lsplit + (lsplit > 1 ? leaf : 0);
           if (sd.int3[c]) {
             unsigned long long iv = (unsigned long long)val * ws;
-            if (d.smem_p) atomicAdd(Pi + (int64_t)k * n3i + pc, (unsigned int)iv);
-            else atomicAdd(d.p3i + (int64_t)k * n3i + pc, iv);
+            if (d.smem_p) atomicAdd(Pi + (int64_t)k * n3i * lsplit + pc, (unsigned int)iv);
+            else atomicAdd(d.p3i + (int64_t)k * n3i * lsplit + pc, iv);
           } else {
             val *= wsT;
-            if (d.smem_p) atomicAdd(Pf + (int64_t)k * n3f + pc, val);
-            else atomicAdd(d.p3f + (int64_t)k * n3f + pc, (double)val);
+            if (d.smem_p) atomicAdd(Pf + (int64_t)k * n3f * lsplit + pc, val);
+            else atomicAdd(d.p3f + (int64_t)k * n3f * lsplit + pc, (double)val);
           }
+        }
+        for (int i = 0; i < d.nb4; ++i) {  // CTA-private accumulation (no outer dependency)
+          if (d.b4_sel[i] >= 0 && d.b4_sel[i] != leaf) continue;
+          T val = sel<NM, T>(m, d.b4_j[i]) * sel<W, T>(v, d.b4_w[i]);
+          if (val == T(0)) continue;
+          int64_t cell = 0;
+          bool okc = true;
+          for (int g = d.b4_g0[i]; g < d.b4_g0[i] + d.b4_ng[i]; ++g) {
+            const DGroupRef q = d.grefs4[g];
+            int code = row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
+            if (code < 0) okc = false;
+            cell += (int64_t)code * q.stride;
+          }
+          if (!okc) continue;
+          if (d.b4_int[i]) atomicAdd(b4i + d.b4_so[i] + cell * d.b4_cellmul[i], (unsigned int)val * (unsigned int)ws);
+          else atomicAdd(b4f + d.b4_so[i] + cell * d.b4_cellmul[i], val * wsT);
         }
       }
     }
@@ -298,10 +353,20 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
   }
   if (d.smem_p) {
     __syncthreads();
-    for (int64_t i = tid; i < d.nkeys * n3f; i += bs)
+    for (int64_t i = tid; i < d.nkeys * n3f * d.b3leaf; i += bs)
       if (Pf[i] != T(0)) atomicAdd(d.p3f + i, (double)Pf[i]);
-    for (int64_t i = tid; i < d.nkeys * n3i; i += bs)
+    for (int64_t i = tid; i < d.nkeys * n3i * d.b3leaf; i += bs)
       if (Pi[i]) atomicAdd(d.p3i + i, (unsigned long long)Pi[i]);
+  }
+  if (d.nb4mirror) {
+    __syncthreads();
+    for (int mm = 0; mm < d.nb4mirror; ++mm) {
+      const DMirror mr = d.b4mirror[mm];
+      for (int i = tid; i < mr.len; i += bs) {
+        if (mr.integral) { if (b4i[mr.soff + i]) atomicAdd(d.icnt + mr.gout + i, (unsigned long long)b4i[mr.soff + i]); }
+        else if (b4f[mr.soff + i] != T(0)) atomicAdd(d.fsum + mr.gout + i, (double)b4f[mr.soff + i]);
+      }
+    }
   }
 }
 
@@ -528,25 +593,31 @@ __global__ void b3_final_kernel(DB3Final d) {
 }  // namespace
 
 void launch_fast_prep(const DFast &d, const double *v64, int vcols, const int *wcol, const int32_t *vcodes,
-                      int vncodes, const int *codecol, void *table, int *codes, bool fp64, cudaStream_t s) {
+                      int vncodes, const int *codecol, void *table, int *codes, bool fp64, cudaStream_t s,
+                      const int2 *ib, int nib) {
   if (!d.ni || d.nkeys == 0) return;
   int grid = (int)std::min<int64_t>((d.nkeys + 255) / 256, 148 * 8);
   if (fp64)
     fast_prep_kernel<double><<<grid, 256, 0, s>>>(d.nkeys, v64, vcols, wcol, d.nw, (double *)table, vcodes, vncodes,
-                                                   codecol, d.ncode, codes);
+                                                   codecol, d.ncode, codes, ib, nib, d.ibit_code);
   else
     fast_prep_kernel<float><<<grid, 256, 0, s>>>(d.nkeys, v64, vcols, wcol, d.nw, (float *)table, vcodes, vncodes,
-                                                  codecol, d.ncode, codes);
+                                                  codecol, d.ncode, codes, ib, nib, d.ibit_code);
 }
 
 size_t fast_smem(const DFast &d, bool fp64, int block) {
   size_t ts = fp64 ? 8 : 4;
   size_t off = 0;
-  if (d.smem_p) off += ts * (size_t)d.nkeys * d.n3f + 4 * (size_t)d.nkeys * d.n3i;
+  const size_t ls = d.b3leaf > 0 ? (size_t)d.b3leaf : 1;
+  if (d.smem_p) off += ts * (size_t)d.nkeys * d.n3f * ls + 4 * (size_t)d.nkeys * d.n3i * ls;
   off = (off + 15) & ~(size_t)15;
   if (d.smem_view && d.ni) off += ts * (size_t)d.nkeys * d.nw + 4 * (size_t)d.nkeys * d.ncode;
   off = (off + 15) & ~(size_t)15;
   off += (size_t)(block / 32) * (d.hist_f + d.hist_i) * 4;
+  off = (off + 15) & ~(size_t)15;
+  off += ts * (size_t)d.b4_fcells;
+  off = (off + 15) & ~(size_t)15;
+  off += 4 * (size_t)d.b4_icells;
   return off;
 }
 

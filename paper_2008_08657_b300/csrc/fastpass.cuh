@@ -21,6 +21,9 @@ constexpr int FMAXF = 24;   // factors of all monomials
 constexpr int FMAXB1 = 4;   // B1 group sets
 constexpr int FMAXC = 8;    // columns per B1 set / B3 columns
 constexpr int FMAXX = 6;    // root columns read per tuple (fact values and group columns)
+constexpr int FMAXFAM = 16; // filters of a filter family (disjoint conjunctions, e.g. tree leaves)
+constexpr int FMAXBIT = 32; // distinct predicates of a filter family
+constexpr int FMAXB4 = 64;  // items accumulated per CTA without segments
 
 struct DFastB1 {
   int G;                 // cells of the group set
@@ -30,6 +33,7 @@ struct DFastB1 {
   int fj[FMAXC], fw[FMAXC];
   int ij[FMAXC], iw[FMAXC];
   int smem_f, smem_i;    // offsets of this set inside a warp's histogram (floats / u32)
+  // refs of src 4 read the tuple's filter index
   int64_t gbase_f, gbase_i;  // offsets in phi1f / phi1i (per segment: G x nf / G x ni)
 };
 
@@ -85,10 +89,36 @@ struct DFast {
   double *p3f;            // [nkeys][n3]
   unsigned long long *p3i;
   const float *thr;
+  // filter family: the tuple's filter index ("leaf") from predicate bits
+  int nfam;                       // 0: no family
+  unsigned int fmask[FMAXFAM];    // predicate bits of each filter
+  int nob;                        // predicates on outer relations (one bit each)
+  int obit_outer[FMAXBIT], obit_col[FMAXBIT], obit_pos[FMAXBIT];
+  int ibit_code;                  // inner predicate bits: codes column index (-1: none)
+  int nrb;                        // predicates on root columns
+  DFac rb[FMAXBIT];
+  int rb_pos[FMAXBIT];
+  int nouter;
+  DOuter outer[MAXOUT];
+  DSegment seg;
+  int b3leaf;                     // B3 partials split by filter index (1: not split)
+  // B4: items accumulated per CTA (no outer dependency, row-level groups)
+  int nb4;
+  int b4_j[FMAXB4], b4_w[FMAXB4], b4_int[FMAXB4], b4_sel[FMAXB4];
+  int b4_g0[FMAXB4], b4_ng[FMAXB4];   // group refs (src 2) in grefs4
+  int b4_so[FMAXB4];                  // shared-memory output base
+  int64_t b4_cellmul[FMAXB4];
+  const DGroupRef *grefs4;
+  int b4_fcells, b4_icells;
+  int nb4mirror;
+  const DMirror *b4mirror;
+  double *fsum;
+  unsigned long long *icnt;
 };
 
 void launch_fast_prep(const DFast &d, const double *v64, int vcols, const int *wcol, const int32_t *vcodes,
-                      int vncodes, const int *codecol, void *table, int *codes, bool fp64, cudaStream_t s);
+                      int vncodes, const int *codecol, void *table, int *codes, bool fp64, cudaStream_t s,
+                      const int2 *ib, int nib);
 size_t fast_smem(const DFast &d, bool fp64, int block);
 bool launch_fast_pass(const DFast &d, bool fp64, int grid, int block, cudaStream_t s);
 bool fast_shape_ok(int nm, int nw);  // a kernel variant exists for nm monomials x nw view columns
@@ -98,6 +128,7 @@ bool lean_shape_ok(int nx, int nw);
 struct DB3Item {
   int w;          // view column (FP64 view)
   int c;          // P column (within the float or integral part)
+  int leaf;       // filter index of a filter family (-1: none)
   int integral;
   int ig0, nig;   // group refs (src 3: view code index)
   int64_t out, cellmul;

@@ -1,6 +1,7 @@
 // Planner state of a context (join tree, logical views and groups, physical plan).
 #pragma once
 
+#include <array>
 #include <set>
 
 #include "fastpass.cuh"
@@ -108,10 +109,24 @@ struct PhysPlan {
     std::vector<B1> b1;
     std::vector<std::pair<int, bool>> p3;      // B3 columns: (monomial, integral)
     std::vector<DB3Item> b3;
+    int b3leaf = 1;                            // B3 partials split by filter index
+    struct B4 {                                // CTA-private items (no outer dependency)
+      int j, w, integral, sel, q;
+      std::vector<DGroupRef> refs;
+      int64_t out, cellmul;
+    };
+    std::vector<B4> b4;
+    int fam_k = 0;                             // filter family
+    std::vector<unsigned int> fmask;
+    struct Bit { int a, pos, fac; };           // outer: (outer idx, view col, bit); inner: (view col, bit)
+    std::vector<Bit> obits_;
+    std::vector<std::array<int, 3>> obits, ibits, rbits;
   } fast;
   DFast fd{};
   DB3Final b3f{};
   int *fwcol_dev = nullptr, *fcodecol_dev = nullptr;
+  int2 *fibits_dev = nullptr;
+  int fnibits = 0;
   int fast_grid = 0, fast_block = 512;
   std::vector<DB1Set> b1sets;
   // device

@@ -98,48 +98,76 @@ def stack(data):
     return np.concatenate(X), np.concatenate(y), np.concatenate(g)
 
 
-def train(data, steps=4000, lr=2e-3, seed=0):
-    import torch
-    X, y, _ = stack(data)
+def _normaliser(data):
+    X, _, _ = stack(data)
     mean = X.mean(axis=0)
     std = X.std(axis=0)
     std[std < 1e-6] = 1.0
+    return mean, std
+
+
+def _fit(data, mean, std, steps, lr, seed, check=None, every=250):
+    """Train one model; with ``check`` (a callable on the model), record it every ``every`` steps."""
+    import torch
+    X, y, _ = stack(data)
     model = CostModel(X.shape[1], seed=seed)
     xt = torch.tensor((X - mean) / std, dtype=torch.float32, device="cuda")
     yt = torch.tensor(y, dtype=torch.float32, device="cuda")
-    losses = []
-    for k in range(steps):
-        loss = model.train_step(xt, yt, lr=lr)
-        if k % 500 == 0 or k == steps - 1:
-            losses.append(float(loss.item()))
-    return model, mean, std, losses
+    trace = []
+    for k in range(1, steps + 1):
+        model.train_step(xt, yt, lr=lr)
+        if check is not None and k % every == 0:
+            trace.append((k, check(model)))
+    return model, trace
 
 
-def save_model(path, model, mean, std):
-    p = model.params.cpu().numpy()
+def train(data, max_steps=3000, lr=2e-3, members=5, val_frac=0.2, seed=0):
+    """Choose the number of training steps on a validation split of the training schemas
+    (mean regret of the learned choice), then train an ensemble of ``members`` models on all
+    training schemas; the prediction is the ensemble mean."""
+    nval = max(1, int(len(data) * val_frac))
+    fit_part, val_part = data[:-nval], data[-nval:]
+    mean, std = _normaliser(fit_part)
+    _, trace = _fit(fit_part, mean, std, max_steps, lr, seed, check=lambda m: regrets(val_part, [m], mean, std)[0].mean())
+    best_steps = min(trace, key=lambda kv: kv[1])[0]
+    mean, std = _normaliser(data)
+    models = [_fit(data, mean, std, best_steps, lr, seed + 1 + i)[0] for i in range(members)]
+    return models, mean, std, {"validation_trace": trace, "steps": best_steps}
+
+
+def save_model(path, models, mean, std):
     with open(path, "w") as f:
-        f.write(f"lmfao-cost-model 1 {model.d}\n")
+        f.write(f"lmfao-cost-model 2 {models[0].d} {len(models)}\n")
         f.write(" ".join(f"{v:.9g}" for v in mean) + "\n")
         f.write(" ".join(f"{v:.9g}" for v in std) + "\n")
-        f.write(" ".join(f"{v:.9g}" for v in p) + "\n")
+        for m in models:
+            f.write(" ".join(f"{v:.9g}" for v in m.params.cpu().numpy()) + "\n")
 
 
 def load_model(path):
     import torch
     with open(path) as f:
         head = f.readline().split()
-        d = int(head[2])
+        d, k = int(head[2]), int(head[3])
         mean = np.array(f.readline().split(), dtype=np.float64)
         std = np.array(f.readline().split(), dtype=np.float64)
-        p = np.array(f.readline().split(), dtype=np.float32)
-    m = CostModel(d)
-    m.params.copy_(torch.tensor(p))
-    return m, mean, std
+        models = []
+        for _ in range(k):
+            p = np.array(f.readline().split(), dtype=np.float32)
+            m = CostModel(d)
+            m.params.copy_(torch.tensor(p))
+            models.append(m)
+    return models, mean, std
 
 
-def regrets(data, model, mean, std):
-    """Per schema: regret of the learned choice and of the heuristic plan."""
+def predict(models, feats, mean, std):
     import torch
+    x = torch.tensor((feats - mean) / std, dtype=torch.float32, device="cuda")
+    return np.mean([m.forward(x).cpu().numpy() for m in models], axis=0)
+
+
+def regrets(data, models, mean, std):
+    """Per schema: regret of the learned choice and of the heuristic plan."""
     rl, rh = [], []
     for d in data:
         t = d["times"]
@@ -147,8 +175,7 @@ def regrets(data, model, mean, std):
         if not ok.any():
             continue
         best = t[ok].min()
-        x = torch.tensor((d["feats"] - mean) / std, dtype=torch.float32, device="cuda")
-        pred = model.forward(x).cpu().numpy()
+        pred = predict(models, d["feats"], mean, std)
         pred[~ok] = np.inf
         choice = int(np.argmin(pred))
         rl.append(t[choice] / best - 1.0)
@@ -162,7 +189,7 @@ def main():
     ap.add_argument("--train", type=int, default=200)
     ap.add_argument("--fact-min", type=float, default=1e5)
     ap.add_argument("--fact-max", type=float, default=5e6)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--out", default="gpurun_out/planner")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
@@ -175,15 +202,15 @@ def main():
                         t_heur=np.array([d["t_heur"] for d in data]),
                         seeds=np.array([d["seed"] for d in data]))
     tr, te = data[:args.train], data[args.train:]
-    model, mean, std, losses = train(tr, steps=args.steps)
-    save_model(os.path.join(args.out, "cost_model.txt"), model, mean, std)
-    rl, rh = regrets(te, model, mean, std)
-    rl_tr, rh_tr = regrets(tr, model, mean, std)
+    models, mean, std, info = train(tr, max_steps=args.steps)
+    save_model(os.path.join(args.out, "cost_model.txt"), models, mean, std)
+    rl, rh = regrets(te, models, mean, std)
+    rl_tr, rh_tr = regrets(tr, models, mean, std)
     res = {
         "schemas": args.schemas, "train": len(tr), "test": len(te),
         "fact_rows_range": [args.fact_min, args.fact_max],
         "candidates_per_schema": float(np.mean([len(d["cands"]) for d in data])),
-        "collect_seconds": t1 - t0, "train_losses": losses,
+        "collect_seconds": t1 - t0, "training": info, "ensemble": len(models),
         "test_regret_learned_mean": float(rl.mean()), "test_regret_learned_median": float(np.median(rl)),
         "test_regret_learned_p90": float(np.quantile(rl, 0.9)),
         "test_regret_heuristic_mean": float(rh.mean()), "test_regret_heuristic_median": float(np.median(rh)),

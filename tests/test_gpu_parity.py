@@ -113,16 +113,20 @@ def test_plan_invariance_retailer():
             assert (np.abs(a["sums"] - b["sums"]) <= 1e-4 * scale).all(), plan
 
 
-def test_dt_level_and_cart_variances():
+@pytest.mark.parametrize("n_fact,mode", [(300_000, "auto"), (1_000_000, "auto"), (1_000_000, "generic")])
+def test_dt_level_and_cart_variances(n_fact, mode):
     import torch
-    rels = W.retailer_schema(n_fact=300_000)
+    rels = W.retailer_schema(n_fact=n_fact)
     qs, splits, thr = W.dt_level_batch(rels)
     ref = O.evaluate(rels, qs)
     e = Engine(0)
     for R in rels:
         e.load_relation(R)
     e.add_queries(qs)
-    e.plan(precision="fp32")
+    e.plan(precision="fp32", mode=mode)
+    phys = e.describe()["physical"]
+    if n_fact >= 1_000_000 and mode == "auto":
+        assert phys["filter_family"] == 8 and phys["per_tuple_items"] == 0
     e.run()
     got = e.fetch_all()
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
