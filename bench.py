@@ -98,15 +98,23 @@ class Clocks:
             return {"error": str(e)}
 
 
-def time_runs(eng, torch, stream, steps, warmup):
-    for _ in range(warmup):
+def time_runs(eng, torch, stream, steps, warmup, merge=None):
+    """``merge`` (N > 1): the all-reduce of the ranks' result states, after each run on the
+    same stream; it is part of the step."""
+    def step():
         eng.run(stream)
+        if merge is not None:
+            with torch.cuda.stream(stream):
+                merge()
+
+    for _ in range(warmup):
+        step()
     torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     fact_ms = []
     evs[0].record(stream)
     for i in range(steps):
-        eng.run(stream)
+        step()
         evs[i + 1].record(stream)
         kt = None
         if eng._profiling:
@@ -128,7 +136,9 @@ def bench_lmfao(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    rels, qs = workload(args.fact_rows, seed=args.seed, which=args.workload)
+    # weak scaling: every rank holds a full-size shard of the fact relation of its own (seeded
+    # by rank) and the replicated dimensions; the ranks' result states are summed each step
+    rels, qs = workload(args.fact_rows, seed=args.seed + rank, which=args.workload)
     n_fact = rels[0]["nrows"]
     eng = Engine(local)
     for R in rels:
@@ -147,11 +157,15 @@ def bench_lmfao(args):
     eng.set_profiling(False)
     eng._profiling = False
     # the timed region proper
+    merge = None
     if world > 1:
+        from paper_2008_08657_b300.distributed import merge_state
+        state = eng.result_state()
+        merge = lambda: merge_state(*state)  # noqa: E731
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with Clocks() as clk:
-        ms, _ = time_runs(eng, torch, stream, args.steps, args.warmup)
+        ms, _ = time_runs(eng, torch, stream, args.steps, args.warmup, merge)
     ms_step = float(np.mean(ms))
     if world > 1:
         t = torch.tensor([ms_step], device="cuda")
@@ -191,12 +205,15 @@ def bench_lmfao(args):
         "config": {"workload": f"{WORKLOADS[args.workload][0]}, {n_fact} fact tuples, {len(qs)} queries, "
                                f"{sum(len(q['aggs']) for q in qs)} aggregates", "fact_tuples": n_fact,
                    "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
-                   "segments": info["n_segments"], "segment_relation": desc["physical"]["segment_relation"]},
+                   "segments": info["n_segments"], "segment_relation": desc["physical"]["segment_relation"],
+                   "parallelism": f"dp{world} (fact row shards; all-reduce of the result state each step)"
+                   if world > 1 else "single GPU"},
         "roofline": roofline,
         "vs_plain_fp64_gpu": (fp64_ms / ms_step) if fp64_ms else None,
         "plain_fp64_ms_per_step": fp64_ms,
         "plan_ms": info["plan_ms"],
         "kernel_ms": kernel_ms,
+        "root_pass_shape": desc["physical"].get("root_pass"),
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": info["n_kernels"] * args.steps,

@@ -227,6 +227,22 @@ LMFAO_API int lmfao_fetch(struct lmfao_ctx *ctx, int query_id, lmfao_result *out
 LMFAO_API int lmfao_result_device(struct lmfao_ctx *ctx, int query_id, int64_t *counts, double *sums,
                         int64_t *ncells, void *stream);
 
+/* The plan's result state: every result of the batch (all queries) lives in two device
+ * arrays of a fixed layout that depends only on the batch and the attribute domains,
+ * not on the data or the physical plan: *counts (int64: per dense group cell the COUNT
+ * and the integral sums) and *sums (double: the other sums), with *ncounts and *nsums
+ * elements. Every entry is a sum over the tuples of the join, so when the rows of one
+ * relation are split into disjoint shards, each evaluated by its own context with the
+ * same batch (one GPU per shard), the element-wise sum of the shards' arrays is the
+ * state of the whole relation (the merge of a data-parallel run, Section 2: the join
+ * distributes over a partition of any of its relations). The pointers are owned by the
+ * context, valid until the next lmfao_plan or lmfao_destroy; lmfao_run overwrites them on
+ * its stream, and lmfao_fetch / lmfao_result_device read them, so a caller that sums the
+ * arrays in place (an all-reduce) orders that after the run on the run's stream and
+ * before the fetch. Either pointer argument may be NULL. ERR_NOT_PLANNED without a plan. */
+LMFAO_API int lmfao_result_state(struct lmfao_ctx *ctx, int64_t **counts, int64_t *ncounts, double **sums,
+                                 int64_t *nsums);
+
 /* Text (JSON) description of the current plan into buf (at most len bytes, NUL-
  * terminated); *needed receives the full length + 1. The logical part lists the join
  * tree, the root of every query, the directional views V_{u->v} after merging and the

@@ -1021,14 +1021,20 @@ struct Planner {
         F.b4.push_back(b);
         if ((int)F.b4.size() > FMAXB4) return false;
       } else {
+        // the partial w_s * u_j is an exact integer when the monomial has only indicator
+        // factors (or none): one integral column then serves integral and float items
+        bool mono_int = true;
+        for (int f : F.monos[pd.j]) mono_int = mono_int && P.facs[f].ind;
+        if (it.integral && !mono_int) return false;
         int pos = -1;
-        for (size_t i = 0; i < F.p3.size(); ++i) if (F.p3[i].first == pd.j && F.p3[i].second == it.integral) pos = (int)i;
+        for (size_t i = 0; i < F.p3.size(); ++i) if (F.p3[i].first == pd.j && F.p3[i].second == mono_int) pos = (int)i;
         if (pos < 0) {
           if ((int)F.p3.size() >= FMAXC) return false;
-          F.p3.push_back({pd.j, it.integral});
+          F.p3.push_back({pd.j, mono_int});
           pos = (int)F.p3.size() - 1;
         }
         DB3Item b{};
+        b.pint = mono_int ? 1 : 0;
         const View &v = P.views[P.inner[0]];
         b.w = it.integral ? pd.w : pd.w;  // FP64 view column; integral values are exact there
         (void)v;
@@ -1298,7 +1304,7 @@ void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
     for (int c : P.rowcols) {
       const Column &col = F.cols[c];
       int e = col.dtype == LMFAO_U8 ? 1 : 4;
-      void *p = P.arena.alloc(n * e);
+      void *p = P.arena.alloc(n * e + 16);  // padded: 4-tuple vector loads may read past the end
       in.push_back(dcol(col));
       out.push_back(DCol{p, col.dtype});
       esz.push_back(e);
@@ -1432,6 +1438,7 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   d.phi1f_seg = segf;
   d.phi1i_seg = segi;
   d.lean = F.lean ? 1 : 0;
+  d.vec = (P.segrel >= 0 && d.nk <= 1) ? 1 : 0;  // reorganised (padded) root columns
   for (int si = 0; si < d.nb1; ++si) d.b1code[si] = d.b1[si].ref[0].b;
   if ((double)P.nseg * (segf + segi) * 4 > 6e9) throw Error(LMFAO_ERR_UNSUPPORTED, "grouped per-segment sums exceed 6 GB");
   d.phi1f = (float *)P.arena.alloc(std::max<size_t>(1, (size_t)P.nseg * segf) * 4);
@@ -1448,6 +1455,7 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   int64_t nk3 = std::max<int64_t>(1, d.nkeys);
   const int lsplit = std::max(1, F.b3leaf);
   d.p3f = (double *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3f) * lsplit * 8);
+  d.p3f32 = (float *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3f) * lsplit * 4);
   d.p3i = (unsigned long long *)P.arena.alloc((size_t)nk3 * std::max(1, d.n3i) * lsplit * 8);
   d.ticket = (unsigned int *)P.arena.alloc(16);
   d.thr = cb.thr;
@@ -1490,6 +1498,16 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   // B4: CTA-private outputs mirrored in shared memory per query region
   d.nb4 = (int)F.b4.size();
   {
+    // order the items by filter index: items of every filter (sel -1) first
+    std::stable_sort(F.b4.begin(), F.b4.end(), [](const PhysPlan::Fast::B4 &a, const PhysPlan::Fast::B4 &b) {
+      return a.sel < b.sel;
+    });
+    for (int f = 0; f < FMAXFAM + 2; ++f) d.b4_off[f] = 0;
+    for (int f = -1; f <= FMAXFAM; ++f) {
+      int cnt = 0;
+      for (auto &b : F.b4) cnt += b.sel < f ? 1 : 0;
+      if (f + 1 < FMAXFAM + 2) d.b4_off[f + 1] = cnt;
+    }
     std::vector<DGroupRef> g4;
     std::vector<DMirror> mir;
     std::map<std::pair<int, int>, int> base;  // (query, integral) -> shared offset
@@ -1555,6 +1573,7 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   }
   f.p3f = d.p3f;
   f.p3i = d.p3i;
+  f.p3f32 = (d.smem_p || P.fp64) ? nullptr : d.p3f32;  // FP64 plans keep FP64 global partials
   f.n3 = d.n3;
   f.n3f = d.n3f * lsplit;
   f.n3i = d.n3i * lsplit;
@@ -2203,6 +2222,7 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     if (d.phi1f_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1f, 0, P.nseg * d.phi1f_seg * 4, s));
     if (d.phi1i_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1i, 0, P.nseg * d.phi1i_seg * 4, s));
     if (d.n3f) LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3f * d.b3leaf * 8, s));
+    if (d.n3f && !d.smem_p && !P.fp64) LMFAO_CUDA(cudaMemsetAsync(d.p3f32, 0, d.nkeys * d.n3f * d.b3leaf * 4, s));
     if (d.n3i) LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3i * d.b3leaf * 8, s));
     LMFAO_CUDA(cudaMemsetAsync(d.ticket, 0, 4, s));
     if (d.ni) {
@@ -2493,6 +2513,16 @@ double time_plan(lmfao_ctx *ctx, int warm, int reps) {
   return ms[ms.size() / 2];
 }
 
+// Whether the last evaluation of the current plan passed its device checks (group-by
+// attributes determined by the join keys of their relations, exact 32-bit view counts).
+// A plan whose checks fail on the loaded data cannot be chosen by a planner.
+bool plan_checks_pass(lmfao_ctx *ctx) {
+  int e = 0;
+  LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+  LMFAO_CUDA(cudaMemcpy(&e, ctx->plan->err, 4, cudaMemcpyDeviceToHost));
+  return e == 0;
+}
+
 struct CostModelFile {
   int d = 0, nmodels = 1;
   std::vector<float> mean, std;
@@ -2769,15 +2799,17 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
     if (ctx->device >= 0 && (o.planner == LMFAO_PLAN_EXHAUSTIVE || o.planner == LMFAO_PLAN_LEARNED)) {
       std::vector<Cand> cands = candidates(ctx, o);
       if (cands.empty()) return fail(ctx, LMFAO_ERR_ARG, "no candidate plan");
-      int best = 0;
+      int best = -1;
       if (o.planner == LMFAO_PLAN_EXHAUSTIVE) {
         double bt = 1e300;
         for (size_t c = 0; c < cands.size(); ++c) {
           build_plan(ctx, cand_opts(o, cands[c]), false, nullptr);
           double ms = time_plan(ctx, 1, 3);
+          const bool ok = plan_checks_pass(ctx);
           drop_plan(ctx);
-          if (ms < bt) { bt = ms; best = (int)c; }
+          if (ok && ms < bt) { bt = ms; best = (int)c; }
         }
+        if (best < 0) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "no candidate plan passes its checks on this data");
         predicted = bt;
       } else {
         CostModelFile cm = load_cost_model(o.cost_model);
@@ -2789,8 +2821,18 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
           for (size_t k = 0; k < f.size(); ++k) X.push_back((f[k] - cm.mean[k]) / cm.std[k]);
         }
         std::vector<float> y = predict(cm, X, (int)cands.size());
-        for (size_t c = 1; c < cands.size(); ++c)
-          if (y[c] < y[best]) best = (int)c;
+        // the candidate of least predicted time among those that pass their checks
+        std::vector<int> order(cands.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] < y[b]; });
+        for (int c : order) {
+          build_plan(ctx, cand_opts(o, cands[c]), false, nullptr);
+          enqueue_run(ctx, *ctx->plan, ctx->tree, ctx->stream);
+          const bool ok = plan_checks_pass(ctx);
+          drop_plan(ctx);
+          if (ok) { best = c; break; }
+        }
+        if (best < 0) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "no candidate plan passes its checks on this data");
         predicted = std::exp((double)y[best]);
       }
       build_plan(ctx, cand_opts(o, cands[best]), false, nullptr);
@@ -2929,6 +2971,18 @@ int lmfao_result_device(lmfao_ctx *ctx, int query_id, int64_t *counts, double *s
   });
 }
 
+int lmfao_result_state(lmfao_ctx *ctx, int64_t **counts, int64_t *ncounts, double **sums, int64_t *nsums) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->planned || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
+    PhysPlan &P = *ctx->plan;
+    if (counts) *counts = reinterpret_cast<int64_t *>(P.icnt);
+    if (ncounts) *ncounts = P.nicnt;
+    if (sums) *sums = P.fsum;
+    if (nsums) *nsums = P.nfsum;
+    return LMFAO_OK;
+  });
+}
+
 int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
   return guarded(ctx, [&]() -> int {
     if (!ctx->planned) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
@@ -3002,7 +3056,18 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
-      << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows
+      << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows;
+    if (P.fast.on) {
+      const DFast &d = P.fd;
+      o << ",\"root_pass\":{\"monomials\":" << d.nm << ",\"inner_columns\":" << d.nw << ",\"value_columns\":" << d.nx
+        << ",\"inner_keys\":" << d.nkeys << ",\"inner_codes\":" << d.ncode << ",\"histograms\":" << d.nb1
+        << ",\"hist_cells_per_warp\":" << d.hist_i + d.hist_f << ",\"root_to_inner_columns\":" << d.n3
+        << ",\"root_to_inner_float\":" << d.n3f << ",\"root_to_inner_integral\":" << d.n3i
+        << ",\"shared_partials\":" << d.smem_p << ",\"shared_view\":" << d.smem_view
+        << ",\"smem_bytes\":" << fast_smem(d, P.fp64, P.fast_block) << ",\"block\":" << P.fast_block
+        << ",\"grid\":" << P.fast_grid << ",\"vector_loads\":" << d.vec << "}";
+    }
+    o
       << ",\"view_columns\":{";
     first = true;
     for (int r : t.post) {

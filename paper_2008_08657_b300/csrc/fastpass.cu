@@ -293,11 +293,16 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
           } else {
             val *= wsT;
             if (d.smem_p) atomicAdd(Pf + (int64_t)k * n3f * lsplit + pc, val);
-            else atomicAdd(d.p3f + (int64_t)k * n3f * lsplit + pc, (double)val);
+            else if (sizeof(T) == 8) atomicAdd(d.p3f + (int64_t)k * n3f * lsplit + pc, (double)val);
+            else atomicAdd(d.p3f32 + (int64_t)k * n3f * lsplit + pc, (float)val);
           }
         }
-        for (int i = 0; i < d.nb4; ++i) {  // CTA-private accumulation (no outer dependency)
-          if (d.b4_sel[i] >= 0 && d.b4_sel[i] != leaf) continue;
+        // CTA-private accumulation (no outer dependency): items of every filter, then the
+        // items of this tuple's filter
+        const int b4a = d.nb4 ? d.b4_off[0] : 0, b4b = d.nb4 ? d.b4_off[1] : 0;
+        const int b4c = (d.nb4 && leaf >= 0) ? d.b4_off[leaf + 1] : 0, b4d = (d.nb4 && leaf >= 0) ? d.b4_off[leaf + 2] : 0;
+        for (int ii = b4a; ii < b4b + (b4d - b4c); ++ii) {
+          const int i = ii < b4b ? ii : b4c + (ii - b4b);
           T val = sel<NM, T>(m, d.b4_j[i]) * sel<W, T>(v, d.b4_w[i]);
           if (val == T(0)) continue;
           int64_t cell = 0;
@@ -391,7 +396,22 @@ __device__ __forceinline__ void basis(const T (&x)[NX > 0 ? NX : 1], T (&u)[Basi
     for (int j = i; j < NX; ++j) u[q++] = x[i] * x[j];
 }
 
-template <typename T, int NX, int W>
+// 4 consecutive values of a column at tuple 4q (the column is padded past its end)
+template <typename T>
+__device__ __forceinline__ void load4(const DCol &c, int64_t q, T (&o)[4]) {
+  if (c.dtype == LMFAO_F32) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(c.p) + q);
+    o[0] = (T)v.x; o[1] = (T)v.y; o[2] = (T)v.z; o[3] = (T)v.w;
+  } else if (c.dtype == LMFAO_U8) {
+    const unsigned int v = __ldg(reinterpret_cast<const unsigned int *>(c.p) + q);
+    o[0] = (T)(v & 0xffu); o[1] = (T)((v >> 8) & 0xffu); o[2] = (T)((v >> 16) & 0xffu); o[3] = (T)(v >> 24);
+  } else {
+    const int4 v = __ldg(reinterpret_cast<const int4 *>(c.p) + q);
+    o[0] = (T)v.x; o[1] = (T)v.y; o[2] = (T)v.z; o[3] = (T)v.w;
+  }
+}
+
+template <typename T, int NX, int W, bool VEC>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) lean_pass_kernel(DFast d) {
   constexpr int NM = Basis<NX>::N;
   constexpr int XA = NX > 0 ? NX : 1;
@@ -450,92 +470,148 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) lean_pass_kerne
 #pragma unroll
       for (int w = 0; w < W; ++w) acc[j][w] = T(0);
     const long long rend = wk.r0 + wk.len;
-    int kn[RU];
-    T xn[RU][XA];
+    auto one = [&](const int k, const T (&xt)[XA]) {
+      T v[W];
+      if (d.ni) {
 #pragma unroll
-    for (int u = 0; u < RU; ++u) {
-      const long long r = wk.r0 + lane + 32 * u;
-      const bool ok = r < rend;
-      kn[u] = ok ? (d.ni ? ldi(kc, r) : 0) : -1;
+        for (int w = 0; w < W; ++w) v[w] = (w < nw) ? table[k * nw + w] : T(0);
+      } else {
+        v[0] = T(1);
 #pragma unroll
-      for (int i = 0; i < XA; ++i) xn[u][i] = (ok && NX > 0) ? ldn<T>(xc[i], r) : T(0);
-    }
-    for (long long rb = wk.r0 + lane; rb < rend; rb += 32 * RU) {
-      int kk[RU];
-      T xv[RU][XA];
+        for (int w = 1; w < W; ++w) v[w] = T(0);
+      }
+      if (v[0] == T(0)) return;  // no partner in the inner relation: not in the join
+      T um[NM];
+      basis<T, NX>(xt, um);
+#pragma unroll
+      for (int j = 0; j < NM; ++j)
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[j][w] += um[j] * v[w];
+      const unsigned int cnt = (unsigned int)v[0];
+#pragma unroll
+      for (int s = 0; s < FMAXB1; ++s)
+        if (s < nb1) {
+          const int code = codes[k * ncode + d.b1code[s]];
+          if (code >= 0) atomicAdd(hi + d.b1[s].smem_i + code, cnt);
+        }
+#pragma unroll
+      for (int c = 0; c < FMAXC; ++c)
+        if (c < n3) {
+          const int pc = d.p3col[c];
+          if (d.int3[c]) {
+            if (d.smem_p) atomicAdd(Pi + k * n3i + pc, (unsigned int)ws);
+            else atomicAdd(d.p3i + (int64_t)k * n3i + pc, ws);
+          } else {
+            const T val = wsT * sel<NM, T>(um, d.j3[c]);
+            if (d.smem_p) atomicAdd(Pf + k * n3f + pc, val);
+            else if (sizeof(T) == 8) atomicAdd(d.p3f + (int64_t)k * n3f + pc, (double)val);
+            else atomicAdd(d.p3f32 + (int64_t)k * n3f + pc, (float)val);
+          }
+        }
+    };
+    if (VEC) {
+      // quads of 4 consecutive tuples per lane; the quad of the next step is in flight
+      const int64_t qa = wk.r0 >> 2, qe = (rend + 3) >> 2;
+      int kq[4];
+      T xq[XA][4];
+      auto loadq = [&](int64_t q, int (&kk)[4], T (&xx)[XA][4]) {
+        if (q >= qe) return;
+        if (d.ni) {
+          const int4 v = __ldg(reinterpret_cast<const int4 *>(kc.p) + q);
+          kk[0] = v.x; kk[1] = v.y; kk[2] = v.z; kk[3] = v.w;
+        } else {
+          kk[0] = kk[1] = kk[2] = kk[3] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < XA; ++i)
+          if (NX > 0) load4<T>(xc[i], q, xx[i]);
+      };
+      loadq(qa + lane, kq, xq);
+      for (int64_t q = qa + lane; q < qe; q += 32) {
+        int kk[4];
+        T xx[XA][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          kk[u] = kq[u];
+#pragma unroll
+          for (int i = 0; i < XA; ++i) xx[i][u] = xq[i][u];
+        }
+        loadq(q + 32, kq, xq);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long r = 4 * q + u;
+          if (r < wk.r0 || r >= rend) continue;
+          T xt[XA];
+#pragma unroll
+          for (int i = 0; i < XA; ++i) xt[i] = NX > 0 ? xx[i][u] : T(0);
+          one(kk[u], xt);
+        }
+      }
+    } else {
+      int kn[RU];
+      T xn[RU][XA];
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
-        kk[u] = kn[u];
-#pragma unroll
-        for (int i = 0; i < XA; ++i) xv[u][i] = xn[u][i];
-      }
-#pragma unroll
-      for (int u = 0; u < RU; ++u) {  // prefetch the next step
-        const long long r = rb + 32 * (RU + u);
+        const long long r = wk.r0 + lane + 32 * u;
         const bool ok = r < rend;
         kn[u] = ok ? (d.ni ? ldi(kc, r) : 0) : -1;
 #pragma unroll
         for (int i = 0; i < XA; ++i) xn[u][i] = (ok && NX > 0) ? ldn<T>(xc[i], r) : T(0);
       }
+      for (long long rb = wk.r0 + lane; rb < rend; rb += 32 * RU) {
+        int kk[RU];
+        T xv[RU][XA];
 #pragma unroll
-      for (int u = 0; u < RU; ++u) {
-        const int k = kk[u];
-        if (k < 0) continue;
-        T v[W];
-        if (d.ni) {
+        for (int u = 0; u < RU; ++u) {
+          kk[u] = kn[u];
 #pragma unroll
-          for (int w = 0; w < W; ++w) v[w] = (w < nw) ? table[k * nw + w] : T(0);
-        } else {
-          v[0] = T(1);
-#pragma unroll
-          for (int w = 1; w < W; ++w) v[w] = T(0);
+          for (int i = 0; i < XA; ++i) xv[u][i] = xn[u][i];
         }
-        if (v[0] == T(0)) continue;  // no partner in the inner relation: not in the join
-        T um[NM];
-        basis<T, NX>(xv[u], um);
 #pragma unroll
-        for (int j = 0; j < NM; ++j)
+        for (int u = 0; u < RU; ++u) {  // prefetch the next step
+          const long long r = rb + 32 * (RU + u);
+          const bool ok = r < rend;
+          kn[u] = ok ? (d.ni ? ldi(kc, r) : 0) : -1;
 #pragma unroll
-          for (int w = 0; w < W; ++w) acc[j][w] += um[j] * v[w];
-        const unsigned int cnt = (unsigned int)v[0];
+          for (int i = 0; i < XA; ++i) xn[u][i] = (ok && NX > 0) ? ldn<T>(xc[i], r) : T(0);
+        }
 #pragma unroll
-        for (int s = 0; s < FMAXB1; ++s)
-          if (s < nb1) {
-            const int code = codes[k * ncode + d.b1code[s]];
-            if (code >= 0) atomicAdd(hi + d.b1[s].smem_i + code, cnt);
-          }
-#pragma unroll
-        for (int c = 0; c < FMAXC; ++c)
-          if (c < n3) {
-            const int pc = d.p3col[c];
-            if (d.int3[c]) {
-              if (d.smem_p) atomicAdd(Pi + k * n3i + pc, (unsigned int)ws);
-              else atomicAdd(d.p3i + (int64_t)k * n3i + pc, ws);
-            } else {
-              const T val = wsT * sel<NM, T>(um, d.j3[c]);
-              if (d.smem_p) atomicAdd(Pf + k * n3f + pc, val);
-              else atomicAdd(d.p3f + (int64_t)k * n3f + pc, (double)val);
-            }
-          }
+        for (int u = 0; u < RU; ++u)
+          if (kk[u] >= 0) one(kk[u], xv[u]);
       }
     }
-    // segment sums: warp reduction, one atomic per entry spread over the lanes
-    const int n0 = NM * nw;
-    T ival = T(0);
-    const int my_ij = lane < d.n0i ? d.i0j[lane] : -1, my_iw = lane < d.n0i ? d.i0w[lane] : -1;
+    // segment sums: reduce-scatter over the warp by recursive halving; lane L ends with
+    // the totals of the flat entries [L*F, L*F + F) of acc (entry j*W + w)
+    constexpr int V = NM * W, F = (V + 31) / 32, PV = 32 * F;
+    T r[PV];
 #pragma unroll
-    for (int j = 0; j < NM; ++j)
+    for (int i = 0; i < PV; ++i) r[i] = i < V ? acc[i / W][i % W] : T(0);
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        if (w < nw) {
-          T t = acc[j][w];
+    for (int lvl = 0; lvl < 5; ++lvl) {
+      const int o = 16 >> lvl, h = PV >> (lvl + 1);
+      const bool up = (lane & o) != 0;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-          if (lane == ((j * W + w) & 31) && t != T(0))
-            atomicAdd(reinterpret_cast<T *>(d.phi0f) + (int64_t)wk.seg * n0 + j * nw + w, t);
-          if (j == my_ij && w == my_iw) ival = t;
-        }
+      for (int i = 0; i < h; ++i) {
+        const T send = up ? r[i] : r[i + h];
+        const T keep = up ? r[i + h] : r[i];
+        r[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
+    }
+    const int n0 = NM * nw;
+#pragma unroll
+    for (int e = 0; e < F; ++e) {
+      const int i = lane * F + e, j = i / W, w = i - j * W;
+      if (i < V && w < nw && r[e] != T(0))
+        atomicAdd(reinterpret_cast<T *>(d.phi0f) + (int64_t)wk.seg * n0 + j * nw + w, r[e]);
+    }
+    // integral segment sums (exact small integers carried in T) to their lanes
+    T ival = T(0);
+    const int q = lane < d.n0i ? d.i0j[lane] * W + d.i0w[lane] : 0;
+#pragma unroll
+    for (int e = 0; e < F; ++e) {
+      const T t = __shfl_sync(0xffffffffu, r[e], q / F);
+      if (e == q % F) ival = t;
+    }
     if (lane < d.n0i) {
       unsigned long long it = (unsigned long long)(ival + T(0.5));
       if (it) atomicAdd(d.phi0i + (int64_t)wk.seg * d.n0i + lane, it);
@@ -584,7 +660,9 @@ __global__ void b3_final_kernel(DB3Final d) {
       unsigned long long p = d.p3i[k * d.n3i + item.c];
       if (p) atomicAdd(d.icnt + item.out + cell * item.cellmul, p * (unsigned long long)vv);
     } else {
-      double p = d.p3f[k * d.n3f + item.c];
+      double p = item.pint ? (double)d.p3i[k * d.n3i + item.c]
+                 : d.p3f32   ? (double)d.p3f32[k * d.n3f + item.c]
+                             : d.p3f[k * d.n3f + item.c];
       if (p != 0.0) atomicAdd(d.fsum + item.out + cell * item.cellmul, p * vv);
     }
   }
@@ -656,8 +734,13 @@ bool lean_shape_ok(int nx, int nw) { return nx >= 0 && nx <= 3 && nw >= 1 && nw 
 
 template <typename T, int NX, int W>
 static void go_lean(const DFast &d, int grid, int block, size_t smem, cudaStream_t s) {
-  cudaFuncSetAttribute(lean_pass_kernel<T, NX, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  lean_pass_kernel<T, NX, W><<<grid, block, smem, s>>>(d);
+  if (d.vec) {
+    cudaFuncSetAttribute(lean_pass_kernel<T, NX, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    lean_pass_kernel<T, NX, W, true><<<grid, block, smem, s>>>(d);
+  } else {
+    cudaFuncSetAttribute(lean_pass_kernel<T, NX, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    lean_pass_kernel<T, NX, W, false><<<grid, block, smem, s>>>(d);
+  }
 }
 
 template <typename T, int NX>
@@ -665,6 +748,7 @@ static void lean_w(const DFast &d, int grid, int block, size_t smem, cudaStream_
   if (d.nw <= 1) go_lean<T, NX, 1>(d, grid, block, smem, s);
   else if (d.nw <= 2) go_lean<T, NX, 2>(d, grid, block, smem, s);
   else if (d.nw <= 4) go_lean<T, NX, 4>(d, grid, block, smem, s);
+  else if (d.nw <= 6) go_lean<T, NX, 6>(d, grid, block, smem, s);
   else go_lean<T, NX, 8>(d, grid, block, smem, s);
 }
 

@@ -85,9 +85,11 @@ struct DFast {
   // lean variant: monomials are the full basis of degree <= 2 over the nx value columns
   // (1, x_i, x_i x_j), no indicators, B1 columns are inner COUNTs only
   int lean;
+  int vec;                // root columns padded by 16 bytes: 4-tuple vector loads
   int b1code[FMAXB1];     // inner view code (position in codes) of each B1 set
   double *p3f;            // [nkeys][n3]
   unsigned long long *p3i;
+  float *p3f32;           // FP32 partials when P is not in shared memory (global atomics)
   const float *thr;
   // filter family: the tuple's filter index ("leaf") from predicate bits
   int nfam;                       // 0: no family
@@ -104,6 +106,7 @@ struct DFast {
   int b3leaf;                     // B3 partials split by filter index (1: not split)
   // B4: items accumulated per CTA (no outer dependency, row-level groups)
   int nb4;
+  int b4_off[FMAXFAM + 2];            // B4 items of filter index f: [b4_off[f+1], b4_off[f+2]); -1 first
   int b4_j[FMAXB4], b4_w[FMAXB4], b4_int[FMAXB4], b4_sel[FMAXB4];
   int b4_g0[FMAXB4], b4_ng[FMAXB4];   // group refs (src 2) in grefs4
   int b4_so[FMAXB4];                  // shared-memory output base
@@ -130,6 +133,7 @@ struct DB3Item {
   int c;          // P column (within the float or integral part)
   int leaf;       // filter index of a filter family (-1: none)
   int integral;
+  int pint;       // the P column is integral (also for a float item)
   int ig0, nig;   // group refs (src 3: view code index)
   int64_t out, cellmul;
 };
@@ -141,6 +145,7 @@ struct DB3Final {
   int vncodes;
   const double *p3f;
   const unsigned long long *p3i;
+  const float *p3f32;     // used instead of p3f when non-null
   int n3;
   int n3f, n3i;
   int nitems;

@@ -35,7 +35,7 @@ ENTRY_POINTS = [
     "lmfao_clear_batch", "lmfao_plan", "lmfao_run", "lmfao_fetch", "lmfao_result_device",
     "lmfao_describe_plan", "lmfao_cart_variances", "lmfao_kernel_times", "lmfao_kernel_name",
     "lmfao_set_profiling", "lmfao_cart_variances_noalloc", "lmfao_mlp_param_count", "lmfao_mlp_forward",
-    "lmfao_mlp_loss", "lmfao_mlp_backward", "lmfao_mlp_adam", "lmfao_plan_candidates",
+    "lmfao_mlp_loss", "lmfao_mlp_backward", "lmfao_mlp_adam", "lmfao_plan_candidates", "lmfao_result_state",
 ]
 COST_MODEL_PATH = os.path.join(_HERE, "cost_model.txt")
 
@@ -111,6 +111,8 @@ def library():
             "lmfao_run": (C.c_int, [P, P]),
             "lmfao_fetch": (C.c_int, [P, C.c_int, C.POINTER(Result)]),
             "lmfao_result_device": (C.c_int, [P, C.c_int, P, P, C.POINTER(C.c_int64), P]),
+            "lmfao_result_state": (C.c_int, [P, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                             C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
             "lmfao_describe_plan": (C.c_int, [P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
             "lmfao_cart_variances": (C.c_int, [P, C.POINTER(C.c_int), C.c_int, P, P]),
             "lmfao_kernel_times": (C.c_int, [P, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
@@ -133,6 +135,21 @@ def library():
     return _lib
 
 
+class _DeviceArray:
+    """A borrowed device array, exposed through the CUDA array interface."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _wrap_device(ptr, n, typestr, dtype, device):
+    import torch
+    if n == 0:
+        return torch.zeros(0, dtype=dtype, device=device)
+    return torch.as_tensor(_DeviceArray(ptr, n, typestr), device=device)
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -150,6 +167,7 @@ class Engine:
         rc = self.lib.lmfao_create(C.byref(self.ctx), int(device))
         if rc != OK:
             raise LmfaoError(rc, "lmfao_create failed (no usable CUDA device?)")
+        self.device = int(device)
         self.rel_ids = {}
         self.queries = []
         self._keep = []
@@ -345,6 +363,17 @@ class Engine:
             self.ctx, int(qid), C.c_void_p(counts.data_ptr()) if counts is not None else None,
             C.c_void_p(sums.data_ptr()) if sums is not None else None, C.byref(n), _stream_handle(stream)))
         return n.value
+
+    def result_state(self):
+        """The plan's result arrays (int64 counts, float64 sums) as CUDA tensors that share the
+        engine's memory: sum them over the shards of a data-parallel run before fetching."""
+        import torch
+        pc, ps = C.c_void_p(), C.c_void_p()
+        nc, ns = C.c_int64(), C.c_int64()
+        self._check(self.lib.lmfao_result_state(self.ctx, C.byref(pc), C.byref(nc), C.byref(ps), C.byref(ns)))
+        dev = torch.device("cuda", self.device)
+        return (_wrap_device(pc.value, nc.value, "<i8", torch.int64, dev),
+                _wrap_device(ps.value, ns.value, "<f8", torch.float64, dev))
 
     def describe(self):
         need = C.c_size_t()

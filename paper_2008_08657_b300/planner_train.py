@@ -66,11 +66,17 @@ def measure_schema(seed, torch, stream, fact_range=(1e5, 5e6), reps=5):
         for i, c in enumerate(cands):
             try:
                 eng.plan_candidate(c)
-                times[i] = time_current_plan(eng, torch, stream, reps)
+                t = time_current_plan(eng, torch, stream, reps)
+                eng.fetch(0)  # raises when the plan's device checks fail on this data
+                times[i] = t
             except LmfaoError:
                 pass
-        eng.plan()
-        t_heur = time_current_plan(eng, torch, stream, reps)
+        try:
+            eng.plan()
+            t_heur = time_current_plan(eng, torch, stream, reps)
+            eng.fetch(0)
+        except LmfaoError:
+            t_heur = np.inf
     finally:
         eng.close()
     return {"seed": seed, "cands": cands, "feats": feats, "times": times, "t_heur": t_heur,
@@ -179,7 +185,7 @@ def regrets(data, models, mean, std):
         pred[~ok] = np.inf
         choice = int(np.argmin(pred))
         rl.append(t[choice] / best - 1.0)
-        rh.append(d["t_heur"] / best - 1.0)
+        rh.append(d["t_heur"] / best - 1.0)  # inf when the heuristic plan fails its checks
     return np.array(rl), np.array(rh)
 
 
@@ -213,11 +219,14 @@ def main():
         "collect_seconds": t1 - t0, "training": info, "ensemble": len(models),
         "test_regret_learned_mean": float(rl.mean()), "test_regret_learned_median": float(np.median(rl)),
         "test_regret_learned_p90": float(np.quantile(rl, 0.9)),
-        "test_regret_heuristic_mean": float(rh.mean()), "test_regret_heuristic_median": float(np.median(rh)),
+        "test_regret_heuristic_mean": float(rh[np.isfinite(rh)].mean()),
+        "test_regret_heuristic_median": float(np.median(rh)),
         "test_regret_heuristic_p90": float(np.quantile(rh, 0.9)),
+        "test_heuristic_plan_failed": float(np.mean(~np.isfinite(rh))),
         "test_within_10pct_learned": float(np.mean(rl <= 0.10)),
         "test_within_10pct_heuristic": float(np.mean(rh <= 0.10)),
-        "train_regret_learned_mean": float(rl_tr.mean()), "train_regret_heuristic_mean": float(rh_tr.mean()),
+        "train_regret_learned_mean": float(rl_tr.mean()),
+        "train_regret_heuristic_mean": float(rh_tr[np.isfinite(rh_tr)].mean()),
     }
     with open(os.path.join(args.out, "planner_results.json"), "w") as f:
         json.dump(res, f, indent=1)

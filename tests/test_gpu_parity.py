@@ -197,3 +197,39 @@ def test_device_columns_and_torch_stream():
     for q, g, r in zip(qs, got, ref):
         compare(q, g, r)
     e.close()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_summed_shard_states_equal_the_whole_relation(world):
+    """The data-parallel merge with the engine's own result state: one context per row shard
+    of the fact relation (run one after another on this GPU), states summed element-wise
+    into shard 0's, whose fetch then equals the oracle over the whole relation."""
+    import torch
+    from paper_2008_08657_b300.distributed import shard_relation
+    rels = W.retailer_schema(n_fact=200_000, seed=4)
+    qs = W.retailer_batch()
+    ref = O.evaluate(rels, qs)
+    engines = []
+    try:
+        for r in range(world):
+            e = Engine(0)
+            for R in rels:
+                e.load_relation(shard_relation(R, r, world) if R is rels[0] else R)
+            e.add_queries(qs)
+            e.plan(root=rels[0]["name"])  # a shard may be smaller than Weather: keep the fact root
+            e.run()
+            engines.append(e)
+        torch.cuda.synchronize()
+        c0, s0 = engines[0].result_state()
+        for e in engines[1:]:
+            c, s = e.result_state()
+            assert c.shape == c0.shape and s.shape == s0.shape
+            c0 += c
+            s0 += s
+        torch.cuda.synchronize()
+        got = engines[0].fetch_all()
+    finally:
+        for e in engines:
+            e.close()
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"merged query {i}")

@@ -1,0 +1,73 @@
+"""Learned and exhaustive planning on the GPU (Section 5, the planner's cost model).
+
+Random snowflakes with seeds outside the cost model's training range: the plan the engine
+chooses with the installed cost model is the argmin of the ensemble's prediction computed
+here through the cost model's own CUDA kernels (over the candidates whose device checks
+pass on the data), and every planner's plan matches the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import lmfao_oracle as O
+from paper_2008_08657_b300 import planner_train as PT
+from paper_2008_08657_b300.lmfao import COST_MODEL_PATH, Engine, LmfaoError
+from tests.parity import compare
+
+pytestmark = pytest.mark.gpu
+
+HELD_OUT = [10_001, 10_002, 10_003]
+
+
+def _engine(rels, qs):
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_queries(qs)
+    return e
+
+
+@pytest.mark.parametrize("seed", HELD_OUT)
+def test_learned_choice_is_the_cost_model_argmin(seed):
+    rels, qs = PT.schema_batch(seed, fact_range=(1.5e5, 3e5))
+    models, mean, std = PT.load_model(COST_MODEL_PATH)
+    e = _engine(rels, qs)
+    try:
+        cands, feats = e.plan_candidates()
+        pred = PT.predict(models, feats, mean, std)
+        valid = np.zeros(len(cands), dtype=bool)
+        for i, c in enumerate(cands):  # a plan whose device checks fail cannot be chosen
+            try:
+                e.plan_candidate(c)
+                e.run()
+                e.fetch(0)
+                valid[i] = True
+            except LmfaoError:
+                pass
+        info = e.plan(planner="learned")
+    finally:
+        e.close()
+    assert valid.any()
+    chosen = [i for i, c in enumerate(cands) if c[0] == info["root_rel"] and c[1] == info["segment_rel"]]
+    assert chosen, "the learned plan is not one of the candidates"
+    assert any(valid[i] for i in chosen)
+    # the engine's prediction (exp of the ensemble mean of log-ms) is the least among the
+    # candidates that pass their checks
+    best = float(pred[valid].min())
+    assert info["predicted_ms"] == pytest.approx(float(np.exp(best)), rel=1e-3)
+    assert min(pred[i] for i in chosen if valid[i]) <= best + 1e-3
+
+
+@pytest.mark.parametrize("seed", HELD_OUT)
+@pytest.mark.parametrize("planner", ["learned", "exhaustive", "heuristic"])
+def test_every_planner_matches_the_oracle(seed, planner):
+    rels, qs = PT.schema_batch(seed, fact_range=(1.5e5, 3e5))
+    ref = O.evaluate(rels, qs)
+    e = _engine(rels, qs)
+    try:
+        e.plan(planner=planner)
+        e.run()
+        got = e.fetch_all()
+    finally:
+        e.close()
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"seed {seed} planner {planner} query {i}")
