@@ -58,6 +58,11 @@ def workload(n_fact, seed=0, which="retailer"):
     return rels, W.retailer_batch()
 
 
+def workload_config(args, n_fact, qs):
+    return {"workload": f"{WORKLOADS[args.workload][0]}, {n_fact} fact tuples, {len(qs)} queries, "
+                        f"{sum(len(q['aggs']) for q in qs)} aggregates", "fact_tuples": n_fact}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -202,9 +207,8 @@ def bench_lmfao(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": f"synthetic (seeded, {args.workload}-shaped)",
-        "config": {"workload": f"{WORKLOADS[args.workload][0]}, {n_fact} fact tuples, {len(qs)} queries, "
-                               f"{sum(len(q['aggs']) for q in qs)} aggregates", "fact_tuples": n_fact,
-                   "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
+        "config": {**workload_config(args, n_fact, qs), "precision": args.precision,
+                   "l2": "inputs larger than L2 (no flush)",
                    "segments": info["n_segments"], "segment_relation": desc["physical"]["segment_relation"],
                    "parallelism": f"dp{world} (fact row shards; all-reduce of the result state each step)"
                    if world > 1 else "single GPU"},
@@ -265,8 +269,8 @@ def bench_e2e(args, rels, qs, torch, local):
 
 
 def cpu_baseline(args, sample_rows=300_000):
-    """The oracle as it stands, on a bounded sample of the same workload (first
-    ``sample_rows`` fact tuples with all dimension relations), timed on the host."""
+    """The oracle as it stands, on a bounded sample of the same workload (a seeded fact
+    relation of ``sample_rows`` tuples with the same dimension relations), timed on the host."""
     from oracle import lmfao_oracle as O
     rels, qs = workload(sample_rows, seed=args.seed, which=args.workload)
     t0 = time.perf_counter()
@@ -274,7 +278,8 @@ def cpu_baseline(args, sample_rows=300_000):
     dt = time.perf_counter() - t0
     cores = 1  # numpy evaluation of the oracle runs on one host thread
     return {"value": sample_rows / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{sample_rows} fact tuples of the same schema and batch, {dt:.1f} s",
+            "sample": f"the whole batch over a seeded {sample_rows}-tuple fact relation of the same shape "
+                      f"with the same dimension relations, {dt:.1f} s",
             "host_cpus": os.cpu_count()}
 
 
@@ -299,10 +304,10 @@ def bench_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": f"synthetic (seeded, {args.workload}-shaped)",
-        "config": {"workload": f"{WORKLOADS[args.workload][0]}, sample of {sample} fact tuples per step",
-                   "fact_tuples": sample},
+        "config": workload_config(args, args.fact_rows, qs),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} fact tuples per step"},
+                         "sample": f"each step: the whole batch over a seeded {sample}-tuple fact relation "
+                                   f"of the same shape with the same dimension relations"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
