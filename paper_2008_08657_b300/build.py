@@ -8,8 +8,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblmfao.so")
-SOURCES = ["kernels.cu", "fastpass.cu", "combine.cu", "combine3.cu", "mlp.cu", "engine.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "fastpass.cu", "combine.cu", "combine3.cu", "mlp.cu", "engine.cpp", "noalloc.cu",
+           "codegen.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(NVCC)), "lib64")  # NVRTC (plan-time code generation)
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-diag-suppress", "177",
          "-I", os.path.join(ROOT, "include")]
@@ -38,7 +40,8 @@ def build(force=False, verbose=False):
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as pool:
         for f in [pool.submit(compile_one, s, o) for s, o in zip(SOURCES, objs)]:
             f.result()
-    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB + ".tmp"] + objs
+    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB + ".tmp"] + objs + [
+        "-L" + CUDA_LIB, "-lnvrtc", "-Xlinker", "-rpath=" + CUDA_LIB]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     for o in objs:

@@ -1,0 +1,453 @@
+// Plan-specialised lean root pass, generated as CUDA source and compiled with NVRTC.
+//
+// The generated kernel computes exactly what lean_pass_kernel computes for the same DFast
+// (per-segment sums of basis monomials x inner view columns, per-segment inner-code
+// histograms, root-to-inner partials), with the shape of the batch folded in:
+//   * the inner view rows are staged in shared memory with the histogram codes of the row
+//     packed behind its values (FP32: as int bits in the same 16-byte vectors), so one tuple
+//     reads its row with ceil(row/4) vector loads;
+//   * per tuple the code is straight-line: the basis monomials, one multiply-add per
+//     (monomial, view column), one shared atomic per histogram set and per root-to-inner
+//     column, with every index a constant;
+//   * a work item's full 4-tuple quads are read with 16-byte loads and no range checks; the
+//     at most 6 tuples of its ragged head and tail are taken by single lanes.
+#include "codegen.h"
+
+#include <nvrtc.h>
+
+#include <map>
+#include <mutex>
+#include <sstream>
+
+namespace lmfao {
+
+namespace {
+
+enum Arg {
+  A_NWORK, A_WORK, A_WSEG, A_TICKET, A_TABLE, A_CODES, A_PHI0F, A_PHI0I, A_PHI1I, A_P3F, A_P3I, A_KC, A_X0,
+  A_NARGS = A_X0 + 3
+};
+
+struct GenArgs {
+  unsigned long long v[16];
+};
+static_assert(A_NARGS <= 16, "argument slots");
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Shape {
+  bool fp64;
+  int block, nx, ni, nw, nm, nb1, ncode, n3, n3f, n3i, n0i, hist, rs;
+  long long nkeys, phi1i_seg;
+  int xdt[3];
+  size_t off_tab, off_code, off_pf, off_pi, off_h, smem;
+};
+
+Shape shape_of(const DFast &d, bool fp64, int block) {
+  Shape s{};
+  s.fp64 = fp64;
+  s.block = block;
+  s.nx = d.nx;
+  s.ni = d.ni;
+  s.nw = d.ni ? d.nw : 1;
+  s.nm = 1 + d.nx + d.nx * (d.nx + 1) / 2;
+  s.nb1 = d.nb1;
+  s.ncode = d.ncode;
+  s.n3 = d.n3;
+  s.n3f = d.n3f;
+  s.n3i = d.n3i;
+  s.n0i = d.n0i;
+  s.hist = d.hist_i;
+  s.nkeys = d.ni ? d.nkeys : 0;
+  s.phi1i_seg = d.phi1i_seg;
+  for (int i = 0; i < 3; ++i) s.xdt[i] = i < d.nx ? d.col[d.xslot[i]].dtype : LMFAO_F32;
+  const size_t ts = fp64 ? 8 : 4;
+  s.rs = fp64 ? round_up(s.nw, 2) : round_up(s.nw + s.nb1, 4);
+  size_t off = 0;
+  auto region = [&](size_t bytes) {
+    size_t at = off;
+    off = (off + bytes + 15) & ~(size_t)15;
+    return at;
+  };
+  s.off_tab = region(ts * (size_t)s.nkeys * s.rs);
+  s.off_code = region(fp64 ? 4 * (size_t)s.nkeys * s.nb1 : 0);
+  s.off_pf = region(ts * (size_t)s.nkeys * s.n3f);
+  s.off_pi = region(4 * (size_t)s.nkeys * s.n3i);
+  s.off_h = region(4 * (size_t)(block / 32) * s.hist);
+  s.smem = off;
+  return s;
+}
+
+// The monomial u_j of the degree <= 2 basis over x0..x{nx-1}: 1, x_i, x_i x_j (i <= j).
+std::string basis_expr(int nx, int j) {
+  if (j == 0) return "(T)1";
+  if (j <= nx) return "x" + std::to_string(j - 1);
+  int q = 1 + nx;
+  for (int a = 0; a < nx; ++a)
+    for (int b = a; b < nx; ++b, ++q)
+      if (q == j) return "x" + std::to_string(a) + " * x" + std::to_string(b);
+  return "(T)0";
+}
+
+// one component of a 4-tuple register of a value column
+std::string x_component(int dt, const std::string &reg, int i) {
+  static const char *c[4] = {"x", "y", "z", "w"};
+  if (dt == LMFAO_U8) return "(T)((" + reg + " >> " + std::to_string(8 * i) + ") & 0xffu)";
+  return "(T)" + reg + "." + c[i];
+}
+
+}  // namespace
+
+std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
+  const Shape s = shape_of(d, fp64, block);
+  const int V = s.nm * s.nw, F = (V + 31) / 32, PV = 32 * F;
+  std::ostringstream o;
+  o << "// generated lean root pass\n";
+  o << "typedef " << (fp64 ? "double" : "float") << " T;\n";
+  o << "struct GenArgs { unsigned long long v[16]; };\n";
+  o << "struct Work { long long r0; int seg; int len; };\n";
+  // per-tuple body
+  o << "__device__ __forceinline__ void tuple(const int k";
+  for (int i = 0; i < 3; ++i) o << ", const T x" << i;
+  o << ", T (&acc)[" << V << "], const T *__restrict__ tab, const int *__restrict__ tcode, unsigned int *hist, "
+       "T *Pf, unsigned int *Pi, const T wsT, const unsigned int wsu) {\n";
+  std::vector<std::string> v(s.nw), code(s.nb1);
+  if (s.ni) {
+    if (!fp64) {
+      o << "  const float4 *row = reinterpret_cast<const float4 *>(tab) + k * " << s.rs / 4 << ";\n";
+      static const char *c[4] = {"x", "y", "z", "w"};
+      for (int q = 0; q < s.rs / 4; ++q) o << "  const float4 t" << q << " = row[" << q << "];\n";
+      for (int w = 0; w < s.nw; ++w) v[w] = "t" + std::to_string(w / 4) + "." + c[w % 4];
+      for (int b = 0; b < s.nb1; ++b) {
+        int p = s.nw + b;
+        code[b] = "__float_as_int(t" + std::to_string(p / 4) + "." + c[p % 4] + ")";
+      }
+    } else {
+      o << "  const double2 *row = reinterpret_cast<const double2 *>(tab) + k * " << s.rs / 2 << ";\n";
+      for (int q = 0; q < s.rs / 2; ++q) o << "  const double2 t" << q << " = row[" << q << "];\n";
+      for (int w = 0; w < s.nw; ++w) v[w] = "t" + std::to_string(w / 2) + (w % 2 ? ".y" : ".x");
+      for (int b = 0; b < s.nb1; ++b) code[b] = "tcode[k * " + std::to_string(s.nb1) + " + " + std::to_string(b) + "]";
+    }
+    o << "  if (" << v[0] << " == (T)0) return;  // no partner in the inner relation\n";
+  } else {
+    v[0] = "(T)1";
+  }
+  for (int j = 1; j < s.nm; ++j) o << "  const T u" << j << " = " << basis_expr(s.nx, j) << ";\n";
+  for (int j = 0; j < s.nm; ++j)
+    for (int w = 0; w < s.nw; ++w) {
+      o << "  acc[" << j * s.nw + w << "] += ";
+      if (j == 0) o << v[w] << ";\n";
+      else o << "u" << j << " * " << v[w] << ";\n";
+    }
+  if (s.nb1) {
+    o << "  const unsigned int cnt = (unsigned int)" << v[0] << ";\n";
+    for (int b = 0; b < s.nb1; ++b)
+      o << "  { const int c = " << code[b] << "; if (c >= 0) atomicAdd(hist + " << d.b1[b].smem_i << " + c, cnt); }\n";
+  }
+  for (int c = 0; c < s.n3; ++c) {
+    const int pc = d.p3col[c];
+    if (d.int3[c]) o << "  atomicAdd(Pi + k * " << s.n3i << " + " << pc << ", wsu);\n";
+    else {
+      const int j = d.j3[c];
+      o << "  atomicAdd(Pf + k * " << s.n3f << " + " << pc << ", wsT" << (j ? " * u" + std::to_string(j) : "")
+        << ");\n";
+    }
+  }
+  o << "}\n\n";
+
+  // kernel
+  o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", 1) lmfao_gen_root_pass(const GenArgs a) {\n";
+  o << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n";
+  o << "  const long long nwork = (long long)a.v[" << A_NWORK << "];\n";
+  o << "  const Work *__restrict__ work = (const Work *)a.v[" << A_WORK << "];\n";
+  o << "  const unsigned long long *__restrict__ wseg = (const unsigned long long *)a.v[" << A_WSEG << "];\n";
+  o << "  unsigned int *ticket = (unsigned int *)a.v[" << A_TICKET << "];\n";
+  o << "  const T *__restrict__ gtab = (const T *)a.v[" << A_TABLE << "];\n";
+  o << "  const int *__restrict__ gcod = (const int *)a.v[" << A_CODES << "];\n";
+  o << "  T *phi0f = (T *)a.v[" << A_PHI0F << "];\n";
+  o << "  unsigned long long *phi0i = (unsigned long long *)a.v[" << A_PHI0I << "];\n";
+  o << "  unsigned int *phi1i = (unsigned int *)a.v[" << A_PHI1I << "];\n";
+  o << "  double *p3f = (double *)a.v[" << A_P3F << "];\n";
+  o << "  unsigned long long *p3i = (unsigned long long *)a.v[" << A_P3I << "];\n";
+  o << "  const int *__restrict__ kc = (const int *)a.v[" << A_KC << "];\n";
+  for (int i = 0; i < s.nx; ++i) {
+    if (s.xdt[i] == LMFAO_U8)
+      o << "  const unsigned char *__restrict__ xc" << i << " = (const unsigned char *)a.v[" << A_X0 + i << "];\n";
+    else
+      o << "  const float *__restrict__ xc" << i << " = (const float *)a.v[" << A_X0 + i << "];\n";
+  }
+  o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
+  o << "  T *tab = (T *)(smem + " << s.off_tab << ");\n";
+  o << "  int *tcode = (int *)(smem + " << s.off_code << ");\n";
+  o << "  T *Pf = (T *)(smem + " << s.off_pf << ");\n";
+  o << "  unsigned int *Pi = (unsigned int *)(smem + " << s.off_pi << ");\n";
+  o << "  unsigned int *hist0 = (unsigned int *)(smem + " << s.off_h << ");\n";
+  o << "  unsigned int *hist = hist0 + warp * " << s.hist << ";\n";
+  // staging
+  if (s.ni) {
+    o << "  for (int i = tid; i < " << s.nkeys * s.rs << "; i += " << block << ") {\n";
+    o << "    const int k = i / " << s.rs << ", c = i - k * " << s.rs << ";\n";
+    o << "    T t = (T)0;\n";
+    o << "    if (c < " << s.nw << ") t = gtab[(long long)k * " << s.nw << " + c];\n";
+    if (!fp64)
+      for (int b = 0; b < s.nb1; ++b)
+        o << "    else if (c == " << s.nw + b << ") t = __int_as_float(gcod[(long long)k * " << s.ncode << " + "
+          << d.b1code[b] << "]);\n";
+    o << "    tab[i] = t;\n  }\n";
+    if (fp64 && s.nb1) {
+      o << "  for (int i = tid; i < " << s.nkeys * s.nb1 << "; i += " << block << ") {\n";
+      o << "    const int k = i / " << s.nb1 << ", b = i - k * " << s.nb1 << ";\n";
+      o << "    int c = -1;\n";
+      for (int b = 0; b < s.nb1; ++b)
+        o << "    if (b == " << b << ") c = gcod[(long long)k * " << s.ncode << " + " << d.b1code[b] << "];\n";
+      o << "    tcode[i] = c;\n  }\n";
+    }
+  }
+  o << "  for (int i = tid; i < " << s.nkeys * s.n3f << "; i += " << block << ") Pf[i] = (T)0;\n";
+  o << "  for (int i = tid; i < " << s.nkeys * s.n3i << "; i += " << block << ") Pi[i] = 0u;\n";
+  o << "  for (int i = tid; i < " << (long long)(block / 32) * s.hist << "; i += " << block << ") hist0[i] = 0u;\n";
+  o << "  __syncthreads();\n";
+  // work loop
+  o << "  for (;;) {\n";
+  o << "    long long wi = 0;\n";
+  o << "    if (lane == 0) wi = atomicAdd(ticket, 1u);\n";
+  o << "    wi = __shfl_sync(0xffffffffu, wi, 0);\n";
+  o << "    if (wi >= nwork) break;\n";
+  o << "    const Work wk = work[wi];\n";
+  o << "    const unsigned long long ws = wseg[wk.seg];\n";
+  o << "    if (ws == 0ull) continue;  // no outer partner for the whole segment\n";
+  o << "    const T wsT = (T)ws;\n";
+  o << "    const unsigned int wsu = (unsigned int)ws;\n";
+  o << "    T acc[" << V << "];\n";
+  o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
+  o << "    const long long r0 = wk.r0, rend = r0 + wk.len;\n";
+  o << "    long long qa = (r0 + 3) >> 2, qe = rend >> 2;\n";
+  o << "    const long long he = 4 * qa < rend ? 4 * qa : rend;\n";
+  o << "    if (qe < qa) qe = qa;\n";
+  o << "    const long long te = 4 * qe > he ? 4 * qe : he;\n";
+  // ragged head and tail
+  auto scalar_x = [&](int i) {
+    return std::string(s.xdt[i] == LMFAO_U8 ? "(T)xc" : "(T)xc") + std::to_string(i) + "[r]";
+  };
+  o << "    {\n      long long r = -1;\n";
+  o << "      if (lane < 4) { if (r0 + lane < he) r = r0 + lane; }\n";
+  o << "      else if (lane >= 8 && lane < 12) { if (te + (lane - 8) < rend) r = te + (lane - 8); }\n";
+  o << "      if (r >= 0) tuple(" << (s.ni ? "kc[r]" : "0");
+  for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? scalar_x(i) : std::string("(T)0"));
+  o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n    }\n";
+  // full quads with the next quad in flight
+  auto xreg_type = [&](int i) { return s.xdt[i] == LMFAO_U8 ? std::string("unsigned int") : std::string("float4"); };
+  auto xreg_load = [&](int i, const std::string &q) {
+    if (s.xdt[i] == LMFAO_U8) return "reinterpret_cast<const unsigned int *>(xc" + std::to_string(i) + ")[" + q + "]";
+    return "reinterpret_cast<const float4 *>(xc" + std::to_string(i) + ")[" + q + "]";
+  };
+  o << "    long long q = qa + lane;\n";
+  if (s.ni) o << "    int4 kn = make_int4(0, 0, 0, 0);\n";
+  for (int i = 0; i < s.nx; ++i) o << "    " << xreg_type(i) << " xn" << i << "{};\n";
+  o << "    if (q < qe) {\n";
+  if (s.ni) o << "      kn = reinterpret_cast<const int4 *>(kc)[q];\n";
+  for (int i = 0; i < s.nx; ++i) o << "      xn" << i << " = " << xreg_load(i, "q") << ";\n";
+  o << "    }\n";
+  o << "    for (; q < qe; q += 32) {\n";
+  if (s.ni) o << "      const int4 kk = kn;\n";
+  for (int i = 0; i < s.nx; ++i) o << "      const " << xreg_type(i) << " xk" << i << " = xn" << i << ";\n";
+  o << "      if (q + 32 < qe) {\n";
+  if (s.ni) o << "        kn = reinterpret_cast<const int4 *>(kc)[q + 32];\n";
+  for (int i = 0; i < s.nx; ++i) o << "        xn" << i << " = " << xreg_load(i, "q + 32") << ";\n";
+  o << "      }\n";
+  static const char *comp[4] = {"x", "y", "z", "w"};
+  for (int u = 0; u < 4; ++u) {
+    o << "      tuple(" << (s.ni ? std::string("kk.") + comp[u] : std::string("0"));
+    for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? x_component(s.xdt[i], "xk" + std::to_string(i), u) : "(T)0");
+    o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
+  }
+  o << "    }\n";
+  // per-segment sums: reduce-scatter over the warp
+  o << "    T r_[" << PV << "];\n";
+  o << "#pragma unroll\n    for (int i = 0; i < " << PV << "; ++i) r_[i] = i < " << V << " ? acc[i < " << V
+    << " ? i : 0] : (T)0;\n";
+  o << "#pragma unroll\n    for (int lvl = 0; lvl < 5; ++lvl) {\n";
+  o << "      const int o = 16 >> lvl, h = " << PV << " >> (lvl + 1);\n";
+  o << "      const bool up = (lane & o) != 0;\n";
+  o << "#pragma unroll\n      for (int i = 0; i < h; ++i) {\n";
+  o << "        const T send = up ? r_[i] : r_[i + h];\n";
+  o << "        const T keep = up ? r_[i + h] : r_[i];\n";
+  o << "        r_[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);\n      }\n    }\n";
+  for (int e = 0; e < F; ++e)
+    o << "    { const int i = lane * " << F << " + " << e << "; if (i < " << V << " && r_[" << e
+      << "] != (T)0) atomicAdd(phi0f + (long long)wk.seg * " << V << " + i, r_[" << e << "]); }\n";
+  if (s.n0i) {
+    o << "    {\n      T iv = (T)0;\n";
+    for (int e = 0; e < s.n0i; ++e) {
+      const int q = d.i0j[e] * s.nw + d.i0w[e];
+      o << "      { const T t = __shfl_sync(0xffffffffu, r_[" << q % F << "], " << q / F << "); if (lane == " << e
+        << ") iv = t; }\n";
+    }
+    o << "      if (lane < " << s.n0i << ") {\n";
+    o << "        const unsigned long long it = (unsigned long long)(iv + (T)0.5);\n";
+    o << "        if (it) atomicAdd(phi0i + (long long)wk.seg * " << s.n0i << " + lane, it);\n      }\n    }\n";
+  }
+  if (s.nb1) {
+    o << "    __syncwarp();\n";
+    for (int b = 0; b < s.nb1; ++b) {
+      o << "    for (int i = lane; i < " << d.b1[b].G << "; i += 32) {\n";
+      o << "      const unsigned int x = hist[" << d.b1[b].smem_i << " + i];\n";
+      o << "      if (x) { hist[" << d.b1[b].smem_i << " + i] = 0u; atomicAdd(phi1i + (long long)wk.seg * "
+        << s.phi1i_seg << " + " << d.b1[b].gbase_i << " + i, x); }\n    }\n";
+    }
+    o << "    __syncwarp();\n";
+  }
+  o << "  }\n";
+  // root-to-inner partials: CTA-private -> global
+  o << "  __syncthreads();\n";
+  o << "  for (int i = tid; i < " << s.nkeys * s.n3f << "; i += " << block
+    << ") if (Pf[i] != (T)0) atomicAdd(p3f + i, (double)Pf[i]);\n";
+  o << "  for (int i = tid; i < " << s.nkeys * s.n3i << "; i += " << block
+    << ") if (Pi[i]) atomicAdd(p3i + i, (unsigned long long)Pi[i]);\n";
+  o << "}\n";
+  return o.str();
+}
+
+namespace {
+
+struct Compiled {
+  const void *fn = nullptr;
+  std::string err;
+};
+
+std::mutex cache_mu;
+std::map<std::string, Compiled> cache;  // by source text (the device is the same sm_103a part)
+
+Compiled compile(const std::string &src) {
+  Compiled c;
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "lmfao_gen_root_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    c.err = "nvrtcCreateProgram failed";
+    return c;
+  }
+  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+  nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
+  if (r != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    if (n) nvrtcGetProgramLog(prog, &log[0]);
+    c.err = std::string("NVRTC: ") + nvrtcGetErrorString(r) + ": " + log.substr(0, 400);
+    nvrtcDestroyProgram(&prog);
+    return c;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  std::string cubin(n, '\0');
+  nvrtcGetCUBIN(prog, &cubin[0]);
+  nvrtcDestroyProgram(&prog);
+  cudaLibrary_t lib;
+  if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+    cudaGetLastError();
+    c.err = "cudaLibraryLoadData failed";
+    return c;
+  }
+  cudaKernel_t k;
+  if (cudaLibraryGetKernel(&k, lib, "lmfao_gen_root_pass") != cudaSuccess) {
+    cudaGetLastError();
+    c.err = "cudaLibraryGetKernel failed";
+    return c;
+  }
+  c.fn = (const void *)k;
+  return c;
+}
+
+bool eligible(const DFast &d, std::string &why) {
+  if (!d.lean) why = "not a lean root pass";
+  else if (!d.vec) why = "root columns not reorganised (no vector loads)";
+  else if (d.ni && d.nk != 1) why = "inner key of more than one attribute";
+  else if (d.nfam || d.nb4) why = "filter family";
+  else if (d.nx > 3) why = "more than 3 value columns";
+  else if (!d.ni && (d.nb1 || d.n3 || d.nw != 1)) why = "inner items without an inner relation";
+  else if (d.nm != 1 + d.nx + d.nx * (d.nx + 1) / 2) why = "monomials are not the degree <= 2 basis";
+  if (!why.empty()) return false;
+  for (int i = 0; i < d.nx; ++i) {
+    const int dt = d.col[d.xslot[i]].dtype;
+    if (dt != LMFAO_F32 && dt != LMFAO_U8) {
+      why = "value column type";
+      return false;
+    }
+  }
+  if (d.ni && d.col[d.kslot[0]].dtype != LMFAO_I32) {
+    why = "inner key type";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+GenRootPass gen_root_pass(const DFast &d, bool fp64, int device) {
+  GenRootPass g;
+  (void)device;
+  if (!eligible(d, g.why)) return g;
+  for (int block : {fp64 ? 512 : 1024, 512}) {
+    const Shape s = shape_of(d, fp64, block);
+    if (s.smem > 227 * 1024) {
+      g.why = "shared memory";
+      continue;
+    }
+    const std::string src = gen_root_pass_source(d, fp64, block);
+    Compiled c;
+    {
+      std::lock_guard<std::mutex> lk(cache_mu);
+      auto it = cache.find(src);
+      if (it != cache.end()) c = it->second;
+      else {
+        c = compile(src);
+        cache[src] = c;
+      }
+    }
+    if (!c.fn) {
+      g.why = c.err;
+      return g;
+    }
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, c.fn) != cudaSuccess) {
+      cudaGetLastError();
+      g.why = "cudaFuncGetAttributes failed";
+      return g;
+    }
+    if (fa.localSizeBytes > 0 && block > 512) {  // spills at this block size: fewer threads
+      g.why = "register spills";
+      continue;
+    }
+    if (cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess) {
+      cudaGetLastError();
+      g.why = "shared memory attribute";
+      return g;
+    }
+    g.fn = c.fn;
+    g.block = block;
+    g.smem = s.smem;
+    g.why.clear();
+    return g;
+  }
+  return g;
+}
+
+cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid, cudaStream_t s) {
+  GenArgs a{};
+  a.v[A_NWORK] = (unsigned long long)d.nwork;
+  a.v[A_WORK] = (unsigned long long)d.work;
+  a.v[A_WSEG] = (unsigned long long)d.wseg;
+  a.v[A_TICKET] = (unsigned long long)d.ticket;
+  a.v[A_TABLE] = (unsigned long long)d.table;
+  a.v[A_CODES] = (unsigned long long)d.codes;
+  a.v[A_PHI0F] = (unsigned long long)d.phi0f;
+  a.v[A_PHI0I] = (unsigned long long)d.phi0i;
+  a.v[A_PHI1I] = (unsigned long long)d.phi1i;
+  a.v[A_P3F] = (unsigned long long)d.p3f;
+  a.v[A_P3I] = (unsigned long long)d.p3i;
+  a.v[A_KC] = d.ni ? (unsigned long long)d.col[d.kslot[0]].p : 0ull;
+  for (int i = 0; i < d.nx && i < 3; ++i) a.v[A_X0 + i] = (unsigned long long)d.col[d.xslot[i]].p;
+  void *args[] = {&a};
+  return cudaLaunchKernel(g.fn, dim3(grid), dim3(g.block), args, g.smem, s);
+}
+
+}  // namespace lmfao

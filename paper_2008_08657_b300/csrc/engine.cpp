@@ -1,6 +1,7 @@
 // Host side of the engine: the C ABI of include/lmfao.h, the planner (join tree, view
 // generation, multi-output plan) and the executor that enqueues the kernels.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -1561,6 +1562,25 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   d.smem_view = d.ni && vbytes + (d.smem_p ? pbytes : 0) + hbytes <= 190 * 1024 ? 1 : 0;
   size_t sm = fast_smem(d, P.fp64, P.fast_block);
   P.fast_grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm > 100 * 1024 ? 148 : 296, (P.nwork + 15) / 16));
+  // plan-specialised kernel (code generation) for large root relations; LMFAO_CODEGEN=0
+  // disables it, =1 forces it at any size
+  P.gen = GenRootPass{};
+  if (F.lean) {
+    const char *env = std::getenv("LMFAO_CODEGEN");
+    const int mode = env ? std::atoi(env) : -1;
+    if (mode == 1 || (mode != 0 && ctx->rels[P.root].nrows >= (int64_t(1) << 20))) {
+      P.gen = gen_root_pass(d, P.fp64, ctx->device);
+      if (P.gen.fn) {
+        int per_sm = 1, nsm = 148;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.gen.fn, P.gen.block, P.gen.smem);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        cudaGetLastError();
+        P.fast_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(1, per_sm), P.nwork));
+      }
+    } else {
+      P.gen.why = mode == 0 ? "disabled" : "root relation below 2^20 tuples";
+    }
+  }
   // B3 finalisation
   DB3Final &f = P.b3f;
   f = DB3Final{};
@@ -2230,8 +2250,12 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
       launch_fast_prep(d, v.v64, (int)v.cols.size(), P.fwcol_dev, v.vcodes, (int)v.codes.size(), P.fcodecol_dev,
                        const_cast<void *>(d.table), const_cast<int *>(d.codes), P.fp64, s, P.fibits_dev, P.fnibits);
     }
-    if (!launch_fast_pass(d, P.fp64, P.fast_grid, P.fast_block, s))
+    if (P.gen.fn) {
+      if (launch_gen_root_pass(P.gen, d, P.fast_grid, s) != cudaSuccess)
+        throw Error(LMFAO_ERR_CUDA, "generated root pass: launch failed");
+    } else if (!launch_fast_pass(d, P.fp64, P.fast_grid, P.fast_block, s)) {
       throw Error(LMFAO_ERR_UNSUPPORTED, "internal: no root-pass variant for this shape");
+    }
     mark("fact_pass");
     if (P.b3f.nitems) launch_b3_final(P.b3f, s);
     mark("b3_final");
@@ -3065,7 +3089,10 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
         << ",\"root_to_inner_float\":" << d.n3f << ",\"root_to_inner_integral\":" << d.n3i
         << ",\"shared_partials\":" << d.smem_p << ",\"shared_view\":" << d.smem_view
         << ",\"smem_bytes\":" << fast_smem(d, P.fp64, P.fast_block) << ",\"block\":" << P.fast_block
-        << ",\"grid\":" << P.fast_grid << ",\"vector_loads\":" << d.vec << "}";
+        << ",\"grid\":" << P.fast_grid << ",\"vector_loads\":" << d.vec
+        << ",\"generated\":" << (P.gen.fn ? "true" : "false") << ",\"generated_block\":" << P.gen.block
+        << ",\"generated_smem\":" << P.gen.smem << ",\"not_generated_because\":\"" << json_escape(P.gen.why)
+        << "\"}";
     }
     o
       << ",\"view_columns\":{";

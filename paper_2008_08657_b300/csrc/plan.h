@@ -4,6 +4,7 @@
 #include <array>
 #include <set>
 
+#include "codegen.h"
 #include "fastpass.cuh"
 
 namespace lmfao {
@@ -128,6 +129,7 @@ struct PhysPlan {
   int2 *fibits_dev = nullptr;
   int fnibits = 0;
   int fast_grid = 0, fast_block = 512;
+  GenRootPass gen;                 // plan-specialised root pass (null: the template kernel)
   std::vector<DB1Set> b1sets;
   // device
   DeviceArena arena;

@@ -233,3 +233,47 @@ def test_summed_shard_states_equal_the_whole_relation(world):
             e.close()
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"merged query {i}")
+
+
+_SHAPES = {}
+
+
+def _shape_case(which):
+    """Benchmark-shaped inputs with ragged segments and their oracle results (computed once)."""
+    if which not in _SHAPES:
+        rels = {"star": lambda: W.star_schema(n_fact=60_001, seed=7),
+                "retailer": lambda: W.retailer_schema(n_fact=1_000_003, seed=7),
+                "favorita": lambda: W.favorita_schema(n_fact=2_000_003, seed=7)}[which]()
+        qs = {"star": W.star_batch, "retailer": W.retailer_batch, "favorita": W.favorita_batch}[which]()
+        _SHAPES[which] = (rels, qs, O.evaluate(rels, qs))
+    return _SHAPES[which]
+
+
+@pytest.mark.parametrize("codegen", ["0", "1"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("which", ["star", "retailer", "favorita"])
+def test_generated_and_template_root_pass_match_the_oracle(which, precision, codegen, monkeypatch):
+    """The plan-specialised root pass (compiled at plan time) and the template kernel, on the
+    benchmark shapes with ragged segments (head and tail tuples outside full quads)."""
+    monkeypatch.setenv("LMFAO_CODEGEN", codegen)
+    rels, qs, ref = _shape_case(which)
+    e = Engine(0)
+    try:
+        for R in rels:
+            e.load_relation(R)
+        e.add_queries(qs)
+        e.plan(precision=precision)
+        phys = e.describe()["physical"]
+        assert "root_pass" in phys and phys["lean_pass"], phys
+        rp = phys["root_pass"]
+        e.run()
+        got = e.fetch_all()
+    finally:
+        e.close()
+    if codegen == "0":
+        assert not rp["generated"]
+    else:  # generated unless its table and partials exceed shared memory (FP64 Retailer)
+        assert rp["generated"] or rp["not_generated_because"] == "shared memory", rp["not_generated_because"]
+        assert rp["generated"] or precision == "fp64"
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"{which} {precision} codegen={codegen} query {i}")
