@@ -218,6 +218,10 @@ def bench_lmfao(args):
         "plan_ms": info["plan_ms"],
         "kernel_ms": kernel_ms,
         "root_pass_shape": desc["physical"].get("root_pass"),
+        "combine_shape": {k: desc["physical"].get(k) for k in
+                          ("block_combine", "projection_combine", "projection_entries", "combine_items",
+                           "outer_terms",
+                           "prefix_digits")},
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": info["n_kernels"] * args.steps,

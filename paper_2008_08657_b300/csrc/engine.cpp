@@ -1761,6 +1761,181 @@ void setup_combine2(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPart> &ppart
   int per_sm = sm > 110 * 1024 ? 1 : 2;
   int64_t ranges = std::max<int64_t>(1, std::min<int64_t>(148 * per_sm, (P.nseg + d.tile - 1) / d.tile));
   P.c2_grid = (int)ranges;
+  P.c2h_ent = ent;
+  P.c2h_og_off = og_off;
+  P.c2h_og_refs = og_refs;
+}
+
+// Projection combine (combine4.cu): eligible for a two-digit segment key when every outer
+// cell is a segment digit or an outer view code and the cells of an entry fit a CTA.
+// Returns false otherwise (the entry combine runs).
+bool setup_combine4(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, const std::vector<DSegFac> &segfacs,
+                    const std::vector<DPart> &pparts) {
+  cudaStream_t s = ctx->stream;
+  const DComb2 &c2 = P.c2;
+  const std::vector<DEntry> &ent = P.c2h_ent;
+  const std::vector<int> &og_off = P.c2h_og_off;
+  const std::vector<DGroupRef> &og_refs = P.c2h_og_refs;
+  if (std::getenv("LMFAO_NO_PROJECTION_COMBINE")) return false;
+  if (c2.seg.ndig != 2 || ent.empty() || c2.seg.radix[1] != 1 || c2.seg.radix[0] != c2.seg.dom[1]) return false;
+  auto outer_digits = [&](int o) {
+    unsigned m = 0;
+    for (int i = 0; i < 2; ++i)
+      if (c2.outer[o].dstride[i]) m |= 1u << i;
+    return m;
+  };
+  // when every outer view holds at most one tuple per key, its COUNT is 1 on every live
+  // segment and the COUNT parts of an outer term depend on no digit
+  bool skip_counts = true;
+  for (int c : P.outer) skip_counts = skip_counts && P.views[c].count_bound <= 1.0;
+  auto psi_digits = [&](int t) {
+    unsigned m = 0;
+    const DPsi &p = psi[t];
+    for (int f = p.f0; f < p.f0 + p.nf; ++f) m |= 1u << segfacs[f].digit;
+    for (int i = p.p0; i < p.p0 + p.np; ++i)
+      if (!(skip_counts && pparts[i].col == 0)) m |= outer_digits(pparts[i].branch);
+    return m;
+  };
+  const int nog = (int)og_off.size() - 1;
+  std::vector<unsigned> og_dig(nog, 0);
+  for (int g = 0; g < nog; ++g)
+    for (int r = og_off[g]; r < og_off[g + 1]; ++r) {
+      const DGroupRef &q = og_refs[r];
+      if (q.src == 0) og_dig[g] |= 1u << q.a;
+      else if (q.src == 1) og_dig[g] |= outer_digits(q.a);
+      else return false;
+    }
+  // compact cells of each outer-cell set (domains from the query of an entry that uses it)
+  std::vector<long long> cstride(std::max<size_t>(1, og_refs.size()), 1), cdom(std::max<size_t>(1, og_refs.size()), 1);
+  std::vector<long long> ncells(nog, 1);
+  std::vector<bool> og_done(nog, false);
+  for (const DEntry &e : ent) {
+    if (og_done[e.og]) continue;
+    int qi = -1;
+    for (size_t k = 0; k < P.qout.size(); ++k) {
+      const QueryOut &q = P.qout[k];
+      const int64_t base = e.integral ? q.io : q.fo;
+      const int64_t len = e.integral ? q.cells * (1 + q.naggs) : q.cells * q.naggs;
+      if (e.out >= base && e.out < base + len) qi = (int)k;
+    }
+    if (qi < 0) return false;
+    const QueryOut &q = P.qout[qi];
+    std::vector<int64_t> qs(q.dom.size(), 1);
+    for (int i = (int)q.dom.size() - 2; i >= 0; --i) qs[i] = qs[i + 1] * q.dom[i + 1];
+    long long cs = 1;
+    for (int r = og_off[e.og + 1] - 1; r >= og_off[e.og]; --r) {
+      long long dm = 1;
+      for (size_t i = 0; i < q.dom.size(); ++i)
+        if (qs[i] == og_refs[r].stride && q.dom[i] > 1) dm = q.dom[i];
+      cdom[r] = dm;
+      cstride[r] = cs;
+      cs *= dm;
+    }
+    ncells[e.og] = cs;
+    og_done[e.og] = true;
+  }
+  // jobs (Y columns) and entry classes
+  std::map<std::pair<int, int>, int> jobs;
+  std::vector<int2> job;
+  std::vector<DEntry4> e012[3], e3;
+  long long max_cells = 1;
+  for (const DEntry &e : ent) {
+    const bool yint = e.integral || e.yint;
+    auto key = std::make_pair(yint ? 1 : 0, e.ycol);
+    auto it = jobs.find(key);
+    if (it == jobs.end()) {
+      it = jobs.emplace(key, (int)job.size()).first;
+      job.push_back(make_int2(key.first, key.second));
+    }
+    const unsigned dep = psi_digits(e.psi) | og_dig[e.og];
+    DEntry4 x{};
+    x.psi = e.psi;
+    x.og = e.og;
+    x.cls = dep == 0 ? 0 : dep == 1 ? 1 : dep == 2 ? 2 : 3;
+    x.flags = (e.integral ? 1 : 0) | (yint ? 2 : 0);
+    x.job = it->second;
+    x.out = e.out;
+    x.cellmul = e.cellmul;
+    x.icell = e.icell;
+    if (x.cls == 3) {
+      e3.push_back(x);
+    } else {
+      e012[x.cls].push_back(x);
+      max_cells = std::max(max_cells, ncells[e.og]);
+    }
+  }
+  if (max_cells > 6144) return false;
+  const int nj = (int)job.size();
+  std::stable_sort(e3.begin(), e3.end(), [](const DEntry4 &a, const DEntry4 &b) { return a.job < b.job; });
+  // per-class tables of the outer terms and cells the entries read
+  std::map<int, int> tm[4], gm[4];
+  std::vector<int> tv[4], gv[4];
+  auto tabulate = [&](DEntry4 &x) {
+    const int c = x.cls == 0 ? 0 : x.cls;
+    if (c == 0) return;
+    auto ti = tm[c].find(x.psi);
+    if (ti == tm[c].end()) { ti = tm[c].emplace(x.psi, (int)tv[c].size()).first; tv[c].push_back(x.psi); }
+    auto gi = gm[c].find(x.og);
+    if (gi == gm[c].end()) { gi = gm[c].emplace(x.og, (int)gv[c].size()).first; gv[c].push_back(x.og); }
+    x.psi = ti->second;
+    x.tog = gi->second;
+  };
+  for (DEntry4 &x : e3) tabulate(x);
+  for (int c = 1; c < 3; ++c)
+    for (DEntry4 &x : e012[c]) tabulate(x);
+  // class 3 slots: per tile of 256 entries (one thread each), the cells of its entries
+  int max_slots3 = 0;
+  for (size_t i = 0, used = 0; i < e3.size(); ++i) {
+    if (i % 256 == 0) used = 0;
+    e3[i].sbase = (int)used;
+    used += (size_t)ncells[e3[i].og];
+    max_slots3 = std::max(max_slots3, (int)used);
+  }
+  if (max_slots3 > 12 * 1024) return false;
+  std::vector<int> e3_off(nj + 1, 0);
+  for (const DEntry4 &x : e3) e3_off[x.job + 1]++;
+  for (int j = 0; j < nj; ++j) e3_off[j + 1] += e3_off[j];
+  std::vector<DEntry4> all;
+  for (int c = 0; c < 3; ++c) all.insert(all.end(), e012[c].begin(), e012[c].end());
+  DComb4 &d = P.c4;
+  d = DComb4{};
+  d.c = c2;
+  d.dom0 = (int)c2.seg.dom[0];
+  d.dom1 = (int)c2.seg.dom[1];
+  d.njobs = nj;
+  d.job = P.arena.upload(job, s);
+  d.nent012 = (int)all.size();
+  d.ent = P.arena.upload(all.empty() ? std::vector<DEntry4>{DEntry4{}} : all, s);
+  d.nent3 = (int)e3.size();
+  d.ent3 = P.arena.upload(e3.empty() ? std::vector<DEntry4>{DEntry4{}} : e3, s);
+  d.e3_off = P.arena.upload(e3_off, s);
+  for (int c = 1; c <= 3; ++c) {
+    DTab4 &tb = d.tab[c];
+    const int64_t nv = c == 1 ? d.dom0 : c == 2 ? d.dom1 : P.nseg;
+    tb.nt = (int)tv[c].size();
+    tb.ng = (int)gv[c].size();
+    tb.t = P.arena.upload(tv[c].empty() ? std::vector<int>{0} : tv[c], s);
+    tb.g = P.arena.upload(gv[c].empty() ? std::vector<int>{0} : gv[c], s);
+    tb.pf = (double *)P.arena.alloc((size_t)nv * std::max(1, tb.nt) * 8);
+    tb.pi = (unsigned long long *)P.arena.alloc((size_t)nv * std::max(1, tb.nt) * 8);
+    tb.cell = (long long *)P.arena.alloc((size_t)nv * std::max(1, tb.ng) * 8);
+  }
+  d.skip_counts = skip_counts ? 1 : 0;
+  d.max_slots3 = max_slots3;
+  d.need_d0 = e012[1].empty() ? 0 : 1;
+  d.need_d1 = e012[2].empty() ? 0 : 1;
+  d.yd0_f = (double *)P.arena.alloc((size_t)d.dom0 * nj * 8);
+  d.yd0_i = (unsigned long long *)P.arena.alloc((size_t)d.dom0 * nj * 8);
+  d.yd1_f = (double *)P.arena.alloc((size_t)d.dom1 * nj * 8);
+  d.yd1_i = (unsigned long long *)P.arena.alloc((size_t)d.dom1 * nj * 8);
+  d.yall_f = (double *)P.arena.alloc((size_t)nj * 8);
+  d.yall_i = (unsigned long long *)P.arena.alloc((size_t)nj * 8);
+  d.og_ncells = P.arena.upload(ncells, s);
+  d.og_cstride = P.arena.upload(cstride, s);
+  d.og_dom = P.arena.upload(cdom, s);
+  d.max_cells = (int)max_cells;
+  P.use_c4 = true;
+  return true;
 }
 
 // Prefix-block combine (combine3.cu): eligible when the segment key has a proper prefix,
@@ -2199,7 +2374,9 @@ void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   P.cb_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 2));
   setup_combine2(ctx, P, pparts);
   P.use_c3 = false;
+  P.use_c4 = false;
   if (!P.no_c3) setup_combine3(ctx, P, psi, segfacs, pparts);
+  if (!P.use_c3) setup_combine4(ctx, P, psi, segfacs, pparts);
   (void)t;
 }
 
@@ -2265,7 +2442,22 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   }
   if (!P.comb.empty()) {
     if (P.use_c3) launch_combine3(P.c3, P.fp64, P.c3_grid, P.c3_block, s);
-    else launch_combine2(P.c2, P.fp64, P.c2_grid, P.c2_block, s);
+    else if (P.use_c4) {
+      const DComb4 &c4 = P.c4;
+      if (c4.need_d0) {
+        LMFAO_CUDA(cudaMemsetAsync(c4.yd0_f, 0, (size_t)c4.dom0 * c4.njobs * 8, s));
+        LMFAO_CUDA(cudaMemsetAsync(c4.yd0_i, 0, (size_t)c4.dom0 * c4.njobs * 8, s));
+      }
+      if (c4.need_d1) {
+        LMFAO_CUDA(cudaMemsetAsync(c4.yd1_f, 0, (size_t)c4.dom1 * c4.njobs * 8, s));
+        LMFAO_CUDA(cudaMemsetAsync(c4.yd1_i, 0, (size_t)c4.dom1 * c4.njobs * 8, s));
+      }
+      LMFAO_CUDA(cudaMemsetAsync(c4.yall_f, 0, (size_t)c4.njobs * 8, s));
+      LMFAO_CUDA(cudaMemsetAsync(c4.yall_i, 0, (size_t)c4.njobs * 8, s));
+      launch_combine4(c4, P.fp64, s);
+    } else {
+      launch_combine2(P.c2, P.fp64, P.c2_grid, P.c2_block, s);
+    }
   }
   mark("combine");
   LMFAO_CUDA(cudaGetLastError());
@@ -3076,6 +3268,8 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false")
       << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false")
       << ",\"block_combine\":" << (P.use_c3 ? "true" : "false") << ",\"prefix_digits\":" << P.prefix_len
+      << ",\"projection_combine\":" << (!P.use_c3 && P.use_c4 ? "true" : "false")
+      << ",\"projection_entries\":[" << P.c4.nent012 << "," << P.c4.nent3 << "," << P.c4.njobs << "]"
       << ",\"filter_family\":" << P.fast.fam_k << ",\"cta_items\":" << P.fast.b4.size()
       << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()

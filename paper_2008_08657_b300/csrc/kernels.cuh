@@ -154,6 +154,57 @@ struct DComb2 {
 size_t combine2_smem(const DComb2 &d, bool fp64);
 void launch_combine2(const DComb2 &d, bool fp64, int grid, int block, cudaStream_t s);
 
+// Projection combine for a two-digit segment key (major digit d0, minor digit d1; segment =
+// d0 * dom1 + d1). An entry SUM_s psi(s) * Y_c(s) into cell og(s) is classified by the
+// digits its outer term and outer cells depend on:
+//   class 0 (none):  psi = 1, one cell: SUM_s Y_c(s);
+//   class 1 (d0):    SUM_d0 psi(d0) * Yd0[d0][c],  Yd0[d0][c] = SUM_d1 Y_c(d0, d1);
+//   class 2 (d1):    SUM_d1 psi(d1) * Yd1[d1][c],  Yd1[d1][c] = SUM_d0 Y_c(d0, d1);
+//   class 3 (both):  per segment.
+// The projections Yd0 / Yd1 are the views from the root to the outer relations keyed by one
+// digit (Fig. 2's views toward other roots); every Y column is streamed once per projection
+// and the entries then read only the small projections. Sums run over the segments whose
+// outer partners all exist (w_s != 0); float columns are projected in FP64, integral ones in
+// INT64.
+struct DEntry4 {
+  int psi, og, cls, flags;  // psi: column of the class's term table; og: the outer-cell set;
+                            // flags: 1 integral output, 2 integral Y column
+  int job, tog;             // Y column job; column of the class's cell table
+  int sbase, pad;           // class 3: first slot in the CTA's slots of the entry's tile
+  long long out, cellmul, icell;
+};
+// Outer terms and cells of one entry class, tabulated per value of its digit(s): terms in
+// FP64 and exactly (integral terms), cells as compact indices over the cell set's attributes.
+struct DTab4 {
+  int nt, ng;               // tabulated terms and cell sets
+  const int *t, *g;         // their ids
+  double *pf;               // [nvalues][nt]
+  unsigned long long *pi;
+  long long *cell;          // [nvalues][ng] (-1: a code is missing, or class 3 and w_s = 0)
+};
+struct DComb4 {
+  DComb2 c;                 // segments, outer views, psi terms, outer-cell sets, Y columns
+  int dom0, dom1;
+  int njobs;
+  const int2 *job;          // (integral Y column, column index within its kind)
+  const DEntry4 *ent;       // entries of classes 0..2
+  int nent012;
+  int nent3;
+  const DEntry4 *ent3;      // class 3 entries, grouped by job: job j has [e3_off[j], e3_off[j+1])
+  const int *e3_off;
+  DTab4 tab[4];             // classes 1 (per d0), 2 (per d1), 3 (per segment); [0] unused
+  int max_slots3;           // shared slots of one tile of 256 class 3 entries
+  double *yd0_f, *yd1_f, *yall_f;             // [dom0][njobs], [dom1][njobs], [njobs]
+  unsigned long long *yd0_i, *yd1_i, *yall_i;
+  int need_d0, need_d1;
+  int skip_counts;          // every outer COUNT is 0 or 1: on live segments the COUNT parts of
+                            // an outer term are 1 and are left out of it
+  const long long *og_ncells;                 // per outer-cell set: compact cells
+  const long long *og_cstride, *og_dom;       // per outer group ref: compact stride and domain
+  int max_cells;
+};
+void launch_combine4(const DComb4 &d, bool fp64, cudaStream_t s);
+
 struct DSegWeight {
   int64_t nseg;
   DSegment seg;

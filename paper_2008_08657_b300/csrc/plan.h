@@ -148,6 +148,11 @@ struct PhysPlan {
   DCombine cb{};
   DComb2 c2{};
   int c2_grid = 0, c2_block = 512;
+  std::vector<DEntry> c2h_ent;     // host copies of the entry combine's entries and outer-cell sets
+  std::vector<int> c2h_og_off;
+  std::vector<DGroupRef> c2h_og_refs;
+  DComb4 c4{};                     // projection combine (two-digit segment keys)
+  bool use_c4 = false;
   DComb3 c3{};
   bool use_c3 = false, no_c3 = false;
   int c3_grid = 0, c3_block = 512;

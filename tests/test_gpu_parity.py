@@ -277,3 +277,38 @@ def test_generated_and_template_root_pass_match_the_oracle(which, precision, cod
         assert rp["generated"] or precision == "fp64"
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"{which} {precision} codegen={codegen} query {i}")
+
+
+_FAV = {}
+
+
+@pytest.mark.parametrize("projection", [True, False])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_favorita_projection_and_entry_combine(precision, projection, monkeypatch):
+    """Favorita with the (date, store) segment key: outer store groups change inside every
+    date block, so the combine is the projection combine (per-date and per-store projections
+    of the per-segment sums, per-segment store x holiday cells) or, with it switched off, the
+    entry combine. The batch adds the Section 2 queries Q1-Q3 (Q2 has a factor on the date
+    key digit)."""
+    if projection is False:
+        monkeypatch.setenv("LMFAO_NO_PROJECTION_COMBINE", "1")
+    if not _FAV:
+        rels = W.favorita_schema(n_fact=700_001, seed=3)
+        qs = W.favorita_batch() + W.favorita_example_queries()
+        _FAV["case"] = (rels, qs, O.evaluate(rels, qs))
+    rels, qs, ref = _FAV["case"]
+    e = Engine(0)
+    try:
+        for R in rels:
+            e.load_relation(R)
+        e.add_queries(qs)
+        e.plan(precision=precision)
+        phys = e.describe()["physical"]
+        e.run()
+        got = e.fetch_all()
+    finally:
+        e.close()
+    assert phys["segment_relation"] == "Transactions" and not phys["block_combine"], phys
+    assert phys["projection_combine"] == projection
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"{precision} projection={projection} query {i}")
