@@ -58,6 +58,25 @@ def workload(n_fact, seed=0, which="retailer"):
     return rels, W.retailer_batch()
 
 
+def measured_traffic(workload_name, n_fact, root_pass):
+    """DRAM bytes per root-pass launch from the committed ncu summary of the same kernel, scaled
+    from the captured fact size to n_fact by the per-tuple column bytes (the per-segment parts
+    do not change with the fact size). None when no capture of this kernel and workload exists."""
+    path = os.path.join(ROOT, "profiles", "root_pass_retailer_40m.md")
+    if not root_pass or not root_pass.get("generated") or not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        for line in f:
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line.split()[1:])
+            if kv.get("kernel") != "lmfao_gen_root_pass" or kv.get("workload") != workload_name:
+                return None, None
+            t = int(kv["read"]) + int(kv["write"]) + (n_fact - int(kv["tuples"])) * int(kv["bytes_per_tuple"])
+            return t, f"ncu capture at {kv['tuples']} fact tuples ({os.path.basename(path)}), scaled by tuples"
+    return None, None
+
+
 def workload_config(args, n_fact, qs):
     return {"workload": f"{WORKLOADS[args.workload][0]}, {n_fact} fact tuples, {len(qs)} queries, "
                         f"{sum(len(q['aggs']) for q in qs)} aggregates", "fact_tuples": n_fact}
@@ -197,6 +216,10 @@ def bench_lmfao(args):
     roofline = {"bound": "hbm", "kernel": "fact_pass", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
                 "algorithmic_bytes": fbytes, "kernel_ms": fms, "traffic": None}
+    traffic, tsrc = measured_traffic(args.workload, n_fact, desc["physical"].get("root_pass"))
+    if traffic is not None:
+        roofline["traffic"] = traffic
+        roofline["traffic_source"] = tsrc
     # end to end through the C ABI: pinned host -> device copies, load, plan, run, fetch
     e2e = None
     if not args.skip_e2e:

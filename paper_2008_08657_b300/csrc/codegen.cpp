@@ -207,61 +207,74 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "  for (int i = tid; i < " << s.nkeys * s.n3i << "; i += " << block << ") Pi[i] = 0u;\n";
   o << "  for (int i = tid; i < " << (long long)(block / 32) * s.hist << "; i += " << block << ") hist0[i] = 0u;\n";
   o << "  __syncthreads();\n";
-  // work loop
-  o << "  for (;;) {\n";
-  o << "    long long wi = 0;\n";
-  o << "    if (lane == 0) wi = atomicAdd(ticket, 1u);\n";
-  o << "    wi = __shfl_sync(0xffffffffu, wi, 0);\n";
-  o << "    if (wi >= nwork) break;\n";
-  o << "    const Work wk = work[wi];\n";
-  o << "    const unsigned long long ws = wseg[wk.seg];\n";
-  o << "    if (ws == 0ull) continue;  // no outer partner for the whole segment\n";
-  o << "    const T wsT = (T)ws;\n";
-  o << "    const unsigned int wsu = (unsigned int)ws;\n";
-  o << "    T acc[" << V << "];\n";
-  o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
-  o << "    const long long r0 = wk.r0, rend = r0 + wk.len;\n";
-  o << "    long long qa = (r0 + 3) >> 2, qe = rend >> 2;\n";
-  o << "    const long long he = 4 * qa < rend ? 4 * qa : rend;\n";
-  o << "    if (qe < qa) qe = qa;\n";
-  o << "    const long long te = 4 * qe > he ? 4 * qe : he;\n";
-  // ragged head and tail
-  auto scalar_x = [&](int i) {
-    return std::string(s.xdt[i] == LMFAO_U8 ? "(T)xc" : "(T)xc") + std::to_string(i) + "[r]";
-  };
-  o << "    {\n      long long r = -1;\n";
-  o << "      if (lane < 4) { if (r0 + lane < he) r = r0 + lane; }\n";
-  o << "      else if (lane >= 8 && lane < 12) { if (te + (lane - 8) < rend) r = te + (lane - 8); }\n";
-  o << "      if (r >= 0) tuple(" << (s.ni ? "kc[r]" : "0");
-  for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? scalar_x(i) : std::string("(T)0"));
-  o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n    }\n";
-  // full quads with the next quad in flight
+  // work loop: the ticket, record and outer weight of the next work item and the first quad
+  // of each lane in it are requested while the current item is processed
+  auto scalar_x = [&](int i) { return "(T)xc" + std::to_string(i) + "[r]"; };
   auto xreg_type = [&](int i) { return s.xdt[i] == LMFAO_U8 ? std::string("unsigned int") : std::string("float4"); };
   auto xreg_load = [&](int i, const std::string &q) {
     if (s.xdt[i] == LMFAO_U8) return "reinterpret_cast<const unsigned int *>(xc" + std::to_string(i) + ")[" + q + "]";
     return "reinterpret_cast<const float4 *>(xc" + std::to_string(i) + ")[" + q + "]";
   };
-  o << "    long long q = qa + lane;\n";
-  if (s.ni) o << "    int4 kn = make_int4(0, 0, 0, 0);\n";
-  for (int i = 0; i < s.nx; ++i) o << "    " << xreg_type(i) << " xn" << i << "{};\n";
-  o << "    if (q < qe) {\n";
-  if (s.ni) o << "      kn = reinterpret_cast<const int4 *>(kc)[q];\n";
-  for (int i = 0; i < s.nx; ++i) o << "      xn" << i << " = " << xreg_load(i, "q") << ";\n";
-  o << "    }\n";
-  o << "    for (; q < qe; q += 32) {\n";
-  if (s.ni) o << "      const int4 kk = kn;\n";
-  for (int i = 0; i < s.nx; ++i) o << "      const " << xreg_type(i) << " xk" << i << " = xn" << i << ";\n";
-  o << "      if (q + 32 < qe) {\n";
-  if (s.ni) o << "        kn = reinterpret_cast<const int4 *>(kc)[q + 32];\n";
-  for (int i = 0; i < s.nx; ++i) o << "        xn" << i << " = " << xreg_load(i, "q + 32") << ";\n";
-  o << "      }\n";
+  auto quad_load = [&](const std::string &q, const std::string &ind) {
+    if (s.ni) o << ind << "kn = reinterpret_cast<const int4 *>(kc)[" << q << "];\n";
+    for (int i = 0; i < s.nx; ++i) o << ind << "xn" << i << " = " << xreg_load(i, q) << ";\n";
+  };
+  o << "  long long wi;\n";
+  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
+  o << "    wi = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
+  o << "  Work wk = {0, 0, 0};\n  unsigned long long ws = 0ull;\n";
+  o << "  if (wi < nwork) { wk = work[wi]; ws = wseg[wk.seg]; }\n";
+  o << "  long long qa = (wk.r0 + 3) >> 2, qe = (wk.r0 + wk.len) >> 2;\n";
+  o << "  if (qe < qa) qe = qa;\n";
+  if (s.ni) o << "  int4 kn = make_int4(0, 0, 0, 0);\n";
+  for (int i = 0; i < s.nx; ++i) o << "  " << xreg_type(i) << " xn" << i << "{};\n";
+  o << "  long long q = qa + lane;\n";
+  o << "  if (q < qe) {\n";
+  quad_load("q", "    ");
+  o << "  }\n";
+  o << "  while (wi < nwork) {\n";
+  o << "    unsigned int tnext = 0u;\n";
+  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // read after the tuples of this item\n";
+  o << "    const T wsT = (T)ws;\n";
+  o << "    const unsigned int wsu = (unsigned int)ws;\n";
+  o << "    T acc[" << V << "];\n";
+  o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
+  o << "    if (ws != 0ull) {  // else no outer partner for the whole segment\n";
+  o << "      const long long r0 = wk.r0, rend = r0 + wk.len;\n";
+  o << "      const long long he = 4 * qa < rend ? 4 * qa : rend;\n";
+  o << "      const long long te = 4 * qe > he ? 4 * qe : he;\n";
+  // ragged head and tail
+  o << "      {\n        long long r = -1;\n";
+  o << "        if (lane < 4) { if (r0 + lane < he) r = r0 + lane; }\n";
+  o << "        else if (lane >= 8 && lane < 12) { if (te + (lane - 8) < rend) r = te + (lane - 8); }\n";
+  o << "        if (r >= 0) tuple(" << (s.ni ? "kc[r]" : "0");
+  for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? scalar_x(i) : std::string("(T)0"));
+  o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n      }\n";
+  // full quads with the next quad in flight
+  o << "      for (; q < qe; q += 32) {\n";
+  if (s.ni) o << "        const int4 kk = kn;\n";
+  for (int i = 0; i < s.nx; ++i) o << "        const " << xreg_type(i) << " xk" << i << " = xn" << i << ";\n";
+  o << "        if (q + 32 < qe) {\n";
+  quad_load("q + 32", "          ");
+  o << "        }\n";
   static const char *comp[4] = {"x", "y", "z", "w"};
   for (int u = 0; u < 4; ++u) {
-    o << "      tuple(" << (s.ni ? std::string("kk.") + comp[u] : std::string("0"));
+    o << "        tuple(" << (s.ni ? std::string("kk.") + comp[u] : std::string("0"));
     for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? x_component(s.xdt[i], "xk" + std::to_string(i), u) : "(T)0");
     o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
   }
+  o << "      }\n    }\n";
+  // the next item: its loads overlap with the segment sums of this one
+  o << "    const long long wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
+  o << "    Work wkn = {0, 0, 0};\n    unsigned long long wsn = 0ull;\n";
+  o << "    if (wn < nwork) { wkn = work[wn]; wsn = wseg[wkn.seg]; }\n";
+  o << "    long long qan = (wkn.r0 + 3) >> 2, qen = (wkn.r0 + wkn.len) >> 2;\n";
+  o << "    if (qen < qan) qen = qan;\n";
+  o << "    q = qan + lane;\n";
+  o << "    if (q < qen) {\n";
+  quad_load("q", "      ");
   o << "    }\n";
+  o << "    if (ws != 0ull) {\n";
   // per-segment sums: reduce-scatter over the warp
   o << "    T r_[" << PV << "];\n";
   o << "#pragma unroll\n    for (int i = 0; i < " << PV << "; ++i) r_[i] = i < " << V << " ? acc[i < " << V
@@ -297,6 +310,8 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     }
     o << "    __syncwarp();\n";
   }
+  o << "    }\n";
+  o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
   o << "  }\n";
   // root-to-inner partials: CTA-private -> global
   o << "  __syncthreads();\n";
