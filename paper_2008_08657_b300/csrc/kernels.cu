@@ -1,6 +1,6 @@
 // CUDA kernels of the engine (sm_103a).
 //
-//  view_kernel        -- the view of a non-root relation r (Section 2): one pass over r,
+//  view_kernel        -- the view of a non-root relation r (Section 2): one pass over r per column,
 //                        lookups into its children's views, accumulation of every needed
 //                        product column per join key into a dense key-indexed array.
 //  fact_pass          -- the root group (Section 2 multi-output plan; Fig. 3 loop nest with
@@ -95,54 +95,47 @@ __device__ __forceinline__ int64_t outer_key(const DOuter &o, const DSegment &s,
 }
 
 // ------------------------------------------------------------------ view kernel
-constexpr int VIEW_CHUNK = 16;  // view columns per thread
-
-__global__ void view_kernel(DViewKernel d) {
-  // one thread per (tuple, chunk of VIEW_CHUNK columns): wide views (hundreds of product
-  // columns) spread over many threads instead of looping per tuple
-  const int nchunk = (d.ncols + VIEW_CHUNK - 1) / VIEW_CHUNK;
-  const int64_t total = d.nrows * nchunk;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-    const int64_t r = idx / nchunk;
-    const int chunk = (int)(idx - r * nchunk);
-    int64_t k = 0;
-    for (int i = 0; i < d.nk; ++i) k += (int64_t)ld_i32(d.in[d.kcol[i]], r) * d.kstride[i];
-    int64_t ck[MAXCH];
-    double w = 1.0;
-    for (int c = 0; c < d.nchild; ++c) {
-      const DViewRef &v = d.child[c];
-      int64_t kk = 0;
-      for (int i = 0; i < v.nk; ++i) kk += (int64_t)ld_i32(d.in[v.kcol[i]], r) * v.kstride[i];
-      ck[c] = kk;
-      w *= __ldg(v.v64 + kk * v.ncols);
+// grid (tiles of rows, column groups): CTA (x, y) computes view columns y, y + gridDim.y, ...
+// for a tile of rows of r (one thread per row: coalesced reads of r's columns, uniform column
+// descriptors); the last column group also writes the group codes
+__global__ void __launch_bounds__(256) view_kernel(DViewKernel d) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrows) return;
+  int64_t k = 0;
+  for (int i = 0; i < d.nk; ++i) k += (int64_t)ld_i32(d.in[d.kcol[i]], r) * d.kstride[i];
+  int64_t ck[MAXCH];
+  double w = 1.0;
+  for (int c = 0; c < d.nchild; ++c) {
+    const DViewRef &v = d.child[c];
+    int64_t kk = 0;
+    for (int i = 0; i < v.nk; ++i) kk += (int64_t)ld_i32(d.in[v.kcol[i]], r) * v.kstride[i];
+    ck[c] = kk;
+    w *= __ldg(v.v64 + kk * v.ncols);
+  }
+  if (w == 0.0) return;  // the tuple has no partner in some child: it does not join
+  for (int j = blockIdx.y; j < d.ncols; j += gridDim.y) {
+    double val = 1.0;
+    for (int f = d.col_fac_off[j]; f < d.col_fac_off[j + 1]; ++f) val *= fac_at<double>(d.in, d.facs[f], r);
+    for (int p = d.col_part_off[j]; p < d.col_part_off[j + 1]; ++p) {
+      const int2 pp = d.parts[p];
+      val *= __ldg(d.child[pp.x].v64 + ck[pp.x] * d.child[pp.x].ncols + pp.y);
     }
-    if (w == 0.0) continue;  // the tuple has no partner in some child: it does not join
-    double *row = d.v64 + k * d.ncols;
-    const int j1 = min(d.ncols, (chunk + 1) * VIEW_CHUNK);
-    for (int j = chunk * VIEW_CHUNK; j < j1; ++j) {
-      double val = 1.0;
-      for (int f = d.col_fac_off[j]; f < d.col_fac_off[j + 1]; ++f) val *= fac_at<double>(d.in, d.facs[f], r);
-      for (int p = d.col_part_off[j]; p < d.col_part_off[j + 1]; ++p) {
-        int2 pp = d.parts[p];
-        val *= __ldg(d.child[pp.x].v64 + ck[pp.x] * d.child[pp.x].ncols + pp.y);
-      }
-      if (d.unique) row[j] = val;
-      else if (val != 0.0) atomicAdd(row + j, val);
+    double *cell = d.v64 + k * d.ncols + j;
+    if (d.unique) *cell = val;
+    else if (val != 0.0) atomicAdd(cell, val);
+  }
+  if (blockIdx.y != gridDim.y - 1 || d.ncodes == 0) return;
+  for (int c = 0; c < d.ncodes; ++c) {
+    int4 cd = d.code_desc[c];
+    int code;
+    if (cd.x >= 0) {
+      code = code_at(d.in[cd.x], r, cd.y, d.thr + cd.z, cd.w);
+    } else {
+      int2 ch = d.code_child[c];
+      code = __ldg(d.child[ch.x].codes + ck[ch.x] * d.child[ch.x].ncodes + ch.y);
     }
-    if (chunk != 0) continue;
-    for (int c = 0; c < d.ncodes; ++c) {
-      int4 cd = d.code_desc[c];
-      int code;
-      if (cd.x >= 0) {
-        code = code_at(d.in[cd.x], r, cd.y, d.thr + cd.z, cd.w);
-      } else {
-        int2 ch = d.code_child[c];
-        code = __ldg(d.child[ch.x].codes + ck[ch.x] * d.child[ch.x].ncodes + ch.y);
-      }
-      int old = atomicCAS(d.codes + k * d.ncodes + c, -1, code);
-      if (old != -1 && old != code) atomicOr(d.err, 1);
-    }
+    int old = atomicCAS(d.codes + k * d.ncodes + c, -1, code);
+    if (old != -1 && old != code) atomicOr(d.err, 1);
   }
 }
 
@@ -613,8 +606,8 @@ static int grid_for(int64_t n, int block) {
 
 void launch_view_kernel(const DViewKernel &d, cudaStream_t s) {
   if (d.nrows == 0) return;
-  int64_t n = d.nrows * ((d.ncols + VIEW_CHUNK - 1) / VIEW_CHUNK);
-  view_kernel<<<grid_for(n, 128), 128, 0, s>>>(d);
+  const int groups = std::max(1, std::min(d.ncols, 65535));
+  view_kernel<<<dim3((unsigned)((d.nrows + 255) / 256), groups), 256, 0, s>>>(d);
 }
 
 void launch_view_finish(const double *v64, float *v32, uint32_t *vint, const int *intcols, int ncols, int nint,
