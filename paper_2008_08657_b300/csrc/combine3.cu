@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
   const int bs = blockDim.x, tid = threadIdx.x;
   const int m = (int)d.m, ny = d.nyf + d.nyi;
   // shared layout (8-byte arrays first)
-  unsigned long long *ysi = reinterpret_cast<unsigned long long *>(smem);  // m x nyi
+  long long *kmin = reinterpret_cast<long long *>(smem);                    // nouter x m: minor-digit key parts
+  unsigned long long *ysi = reinterpret_cast<unsigned long long *>(kmin + (size_t)d.nouter * m);  // m x nyi
   unsigned long long *bti = ysi + (size_t)m * d.nyi;                        // m x nbi
   unsigned long long *zi = bti + (size_t)m * d.nbi;                         // nbi x nyi
   unsigned long long *ati = zi + (size_t)d.nbi * d.nyi;                     // na
@@ -75,6 +76,15 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
   T *mf = at + d.na;                                                        // mirror
   __shared__ long long akey[MAXOUT];
   __shared__ int block_live;
+  // view-key contribution of the minor digits of the j-th segment of any block (a block is
+  // m consecutive segments starting at a multiple of m, so these digits depend on j alone)
+  for (int idx = tid; idx < d.nouter * m; idx += bs) {
+    const int o = idx / m, j = idx - o * m;
+    long long k = 0;
+    for (int i = 0; i < d.seg.ndig; ++i)
+      if (d.outer[o].dstride[i] && d.seg.radix[i] < d.m) k += ((j / d.seg.radix[i]) % d.seg.dom[i]) * d.outer[o].dstride[i];
+    kmin[idx] = k;
+  }
 
   for (int i = tid; i < d.mirror_i; i += bs) mi[i] = 0ull;
   for (int i = tid; i < d.mirror_f; i += bs) mf[i] = T(0);
@@ -122,6 +132,15 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
     __syncthreads();
     if (tid == 0) block_live = 0;
     __syncthreads();
+    // 0. view keys of the block's prefix digits
+    if (tid < d.nouter) {
+      const DOuter &o = d.outer[tid];
+      int64_t k = 0;
+      for (int i = 0; i < d.seg.ndig; ++i)
+        if (o.dstride[i]) k += digit3(d.seg, s0, i) * o.dstride[i];
+      akey[tid] = k;
+    }
+    __syncthreads();
     // 1. staged B columns and Y rows of the block
     for (int idx = tid; idx < m * d.nbst; idx += bs) {
       int s = idx / d.nbst, j = idx - s * d.nbst;
@@ -131,9 +150,7 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
         block_live = 1;
         int2 sc = d.bstage[j];
         const DOuter &o = d.outer[sc.x];
-        int64_t k = 0;
-        for (int i = 0; i < d.seg.ndig; ++i)
-          if (o.dstride[i]) k += digit3(d.seg, seg, i) * o.dstride[i];
+        const int64_t k = akey[sc.x] + kmin[(size_t)sc.x * m + s];
         v = (T)__ldg(o.v.v64 + k * o.v.ncols + sc.y);
       }
       bsv[idx] = v;
@@ -153,13 +170,6 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
         v = (T)u;
       }
       ysf[idx] = v;
-    }
-    if (tid < d.nouter) {
-      const DOuter &o = d.outer[tid];
-      int64_t k = 0;
-      for (int i = 0; i < d.seg.ndig; ++i)
-        if (o.dstride[i]) k += digit3(d.seg, s0, i) * o.dstride[i];
-      akey[tid] = k;
     }
     __syncthreads();
     if (!block_live) continue;  // no segment of the block joins its outer views
@@ -190,11 +200,35 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
     }
     __syncthreads();
     // 3. Z = B^T Y over the block's segments; A terms
-    for (int o = tid; o < d.nb * ny; o += bs) {
-      int b = o / ny, c = o - b * ny;
-      T z = T(0);
-      for (int s = 0; s < m; ++s) z += bt[(size_t)s * d.nb + b] * ysf[(size_t)s * ny + c];
-      zf[o] = z;
+    {
+      const int nq = (ny + 3) >> 2;  // four Y columns per thread: 5 shared loads per 4 FMA
+      for (int o = tid; o < d.nb * nq; o += bs) {
+        const int b = o / nq, c0 = 4 * (o - b * nq);
+        T z0 = T(0), z1 = T(0), z2 = T(0), z3 = T(0);
+        if (c0 + 3 < ny) {
+          for (int s = 0; s < m; ++s) {
+            const T bv = bt[(size_t)s * d.nb + b];
+            const T *y = ysf + (size_t)s * ny + c0;
+            z0 += bv * y[0];
+            z1 += bv * y[1];
+            z2 += bv * y[2];
+            z3 += bv * y[3];
+          }
+        } else {
+          for (int s = 0; s < m; ++s) {
+            const T bv = bt[(size_t)s * d.nb + b];
+            const T *y = ysf + (size_t)s * ny + c0;
+            z0 += bv * y[0];
+            if (c0 + 1 < ny) z1 += bv * y[1];
+            if (c0 + 2 < ny) z2 += bv * y[2];
+          }
+        }
+        T *zo = zf + (size_t)b * ny + c0;
+        zo[0] = z0;
+        if (c0 + 1 < ny) zo[1] = z1;
+        if (c0 + 2 < ny) zo[2] = z2;
+        if (c0 + 3 < ny) zo[3] = z3;
+      }
     }
     for (int o = tid; o < d.nbi * d.nyi; o += bs) {
       int b = o / d.nyi, c = o - b * d.nyi;
@@ -242,7 +276,7 @@ __global__ void __launch_bounds__(512) combine3_kernel(DComb3 d) {
 size_t combine3_smem(const DComb3 &d, bool fp64) {
   size_t ts = fp64 ? 8 : 4;
   const size_t m = (size_t)d.m, ny = (size_t)d.nyf + d.nyi;
-  size_t b = 8 * (m * d.nyi + m * d.nbi + (size_t)d.nbi * d.nyi + d.na + d.nog + d.mirror_i);
+  size_t b = 8 * ((size_t)d.nouter * m + m * d.nyi + m * d.nbi + (size_t)d.nbi * d.nyi + d.na + d.nog + d.mirror_i);
   b += ts * (m * ny + m * d.nbst + m * d.nb + (size_t)d.nb * ny + d.nast + d.na + d.mirror_f);
   return b;
 }

@@ -2153,7 +2153,7 @@ bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   d.mirror_f = fcells;
   d.mirror_i = icells;
   d.nmirror = (int)mirrors.size();
-  if (combine3_smem(d, P.fp64) > 200 * 1024) return false;
+  if (combine3_smem(d, P.fp64) > 222 * 1024) return false;  // + static shared memory < 227 KB
   d.bstage = P.arena.upload(bstage.empty() ? std::vector<int2>{make_int2(0, 0)} : bstage, s);
   d.bterm = P.arena.upload(bdesc.empty() ? std::vector<DPsi>{DPsi{}} : bdesc, s);
   d.bpart = P.arena.upload(bpart.empty() ? std::vector<int>{0} : bpart, s);
