@@ -4,8 +4,9 @@
 // (per-segment sums of basis monomials x inner view columns, per-segment inner-code
 // histograms, root-to-inner partials), with the shape of the batch folded in:
 //   * the inner view rows are staged in shared memory with the histogram codes of the row
-//     packed behind its values (FP32: as int bits in the same 16-byte vectors), so one tuple
-//     reads its row with ceil(row/4) vector loads;
+//     packed behind its values (FP32: as int bits in the same 16-byte vectors), as planes of
+//     16-byte parts, so one tuple reads its row with ceil(row/4) vector loads that spread over
+//     all shared-memory banks;
 //   * per tuple the code is straight-line: the basis monomials, one multiply-add per
 //     (monomial, view column), one shared atomic per histogram set and per root-to-inner
 //     column, with every index a constant;
@@ -114,17 +115,21 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   std::vector<std::string> v(s.nw), code(s.nb1);
   if (s.ni) {
     if (!fp64) {
-      o << "  const float4 *row = reinterpret_cast<const float4 *>(tab) + k * " << s.rs / 4 << ";\n";
+      // planar rows: 16-byte part q of row k at plane q, element k (consecutive keys in
+      // consecutive bank groups, so a warp's random rows spread over all banks)
       static const char *c[4] = {"x", "y", "z", "w"};
-      for (int q = 0; q < s.rs / 4; ++q) o << "  const float4 t" << q << " = row[" << q << "];\n";
+      for (int q = 0; q < s.rs / 4; ++q)
+        o << "  const float4 t" << q << " = reinterpret_cast<const float4 *>(tab)[" << (long long)q * s.nkeys
+          << " + k];\n";
       for (int w = 0; w < s.nw; ++w) v[w] = "t" + std::to_string(w / 4) + "." + c[w % 4];
       for (int b = 0; b < s.nb1; ++b) {
         int p = s.nw + b;
         code[b] = "__float_as_int(t" + std::to_string(p / 4) + "." + c[p % 4] + ")";
       }
     } else {
-      o << "  const double2 *row = reinterpret_cast<const double2 *>(tab) + k * " << s.rs / 2 << ";\n";
-      for (int q = 0; q < s.rs / 2; ++q) o << "  const double2 t" << q << " = row[" << q << "];\n";
+      for (int q = 0; q < s.rs / 2; ++q)
+        o << "  const double2 t" << q << " = reinterpret_cast<const double2 *>(tab)[" << (long long)q * s.nkeys
+          << " + k];\n";
       for (int w = 0; w < s.nw; ++w) v[w] = "t" + std::to_string(w / 2) + (w % 2 ? ".y" : ".x");
       for (int b = 0; b < s.nb1; ++b) code[b] = "tcode[k * " + std::to_string(s.nb1) + " + " + std::to_string(b) + "]";
     }
@@ -193,7 +198,10 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
       for (int b = 0; b < s.nb1; ++b)
         o << "    else if (c == " << s.nw + b << ") t = __int_as_float(gcod[(long long)k * " << s.ncode << " + "
           << d.b1code[b] << "]);\n";
-    o << "    tab[i] = t;\n  }\n";
+    {
+      const int vw = fp64 ? 2 : 4;  // elements per 16-byte part
+      o << "    tab[(c / " << vw << ") * " << s.nkeys * vw << " + k * " << vw << " + c % " << vw << "] = t;\n  }\n";
+    }
     if (fp64 && s.nb1) {
       o << "  for (int i = tid; i < " << s.nkeys * s.nb1 << "; i += " << block << ") {\n";
       o << "    const int k = i / " << s.nb1 << ", b = i - k * " << s.nb1 << ";\n";
