@@ -16,6 +16,7 @@
 
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <sstream>
@@ -405,9 +406,80 @@ bool eligible(const DFast &d, std::string &why) {
 
 }  // namespace
 
-GenRootPass gen_root_pass(const DFast &d, bool fp64, int device) {
+namespace {
+
+// compile (or take from the cache) and check one generated source
+bool finish(GenRootPass &g, const std::string &src, int block, size_t smem) {
+  Compiled c;
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    auto it = cache.find(src);
+    if (it != cache.end()) c = it->second;
+    else {
+      c = compile(src);
+      cache[src] = c;
+    }
+  }
+  if (!c.fn) {
+    g.why = c.err;
+    return false;
+  }
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, c.fn) != cudaSuccess) {
+    cudaGetLastError();
+    g.why = "cudaFuncGetAttributes failed";
+    return false;
+  }
+  if (fa.localSizeBytes > 0 && block > 512) {
+    g.why = "register spills";
+    return false;
+  }
+  if (cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    g.why = "shared memory attribute";
+    return false;
+  }
+  g.fn = c.fn;
+  g.block = block;
+  g.smem = smem;
+  g.why.clear();
+  return true;
+}
+
+GenRootPass gen_family(const DFast &d, bool fp64, const std::vector<float> &thr) {
   GenRootPass g;
+  g.family = true;
+  // host copies of the CTA-private items' group references and output regions
+  int nref4 = 0;
+  for (int i = 0; i < d.nb4; ++i) nref4 = std::max(nref4, d.b4_g0[i] + d.b4_ng[i]);
+  std::vector<DGroupRef> grefs4(nref4);
+  std::vector<DMirror> mirror(d.nb4mirror);
+  if ((nref4 && cudaMemcpy(grefs4.data(), d.grefs4, nref4 * sizeof(DGroupRef), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (d.nb4mirror &&
+       cudaMemcpy(mirror.data(), d.b4mirror, d.nb4mirror * sizeof(DMirror), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    cudaGetLastError();
+    g.why = "descriptor copy failed";
+    return g;
+  }
+  if (!family_eligible(d, g.why, grefs4)) return g;
+  for (int block : {fp64 ? 512 : 1024, 512}) {
+    const FamilyLayout L = family_layout(d, fp64, block);
+    if (L.smem > 227 * 1024) {
+      g.why = "shared memory";
+      continue;
+    }
+    if (finish(g, gen_family_source(d, fp64, block, thr, grefs4, mirror), block, L.smem)) return g;
+    if (g.why != "register spills") return g;
+  }
+  return g;
+}
+
+}  // namespace
+
+GenRootPass gen_root_pass(const DFast &d, bool fp64, int device, const std::vector<float> &thr) {
   (void)device;
+  if (!d.lean || d.nfam || d.nb4) return gen_family(d, fp64, thr);
+  GenRootPass g;
   if (!eligible(d, g.why)) return g;
   for (int block : {fp64 ? 512 : 1024, 512}) {
     const Shape s = shape_of(d, fp64, block);
@@ -415,41 +487,8 @@ GenRootPass gen_root_pass(const DFast &d, bool fp64, int device) {
       g.why = "shared memory";
       continue;
     }
-    const std::string src = gen_root_pass_source(d, fp64, block);
-    Compiled c;
-    {
-      std::lock_guard<std::mutex> lk(cache_mu);
-      auto it = cache.find(src);
-      if (it != cache.end()) c = it->second;
-      else {
-        c = compile(src);
-        cache[src] = c;
-      }
-    }
-    if (!c.fn) {
-      g.why = c.err;
-      return g;
-    }
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, c.fn) != cudaSuccess) {
-      cudaGetLastError();
-      g.why = "cudaFuncGetAttributes failed";
-      return g;
-    }
-    if (fa.localSizeBytes > 0 && block > 512) {  // spills at this block size: fewer threads
-      g.why = "register spills";
-      continue;
-    }
-    if (cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem) != cudaSuccess) {
-      cudaGetLastError();
-      g.why = "shared memory attribute";
-      return g;
-    }
-    g.fn = c.fn;
-    g.block = block;
-    g.smem = s.smem;
-    g.why.clear();
-    return g;
+    if (finish(g, gen_root_pass_source(d, fp64, block), block, s.smem)) return g;
+    if (g.why != "register spills") return g;
   }
   return g;
 }
@@ -470,7 +509,39 @@ cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid,
   a.v[A_KC] = d.ni ? (unsigned long long)d.col[d.kslot[0]].p : 0ull;
   for (int i = 0; i < d.nx && i < 3; ++i) a.v[A_X0 + i] = (unsigned long long)d.col[d.xslot[i]].p;
   void *args[] = {&a};
-  return cudaLaunchKernel(g.fn, dim3(grid), dim3(g.block), args, g.smem, s);
+  if (!g.family) return cudaLaunchKernel(g.fn, dim3(grid), dim3(g.block), args, g.smem, s);
+  struct { unsigned long long v[32]; } f{};
+  f.v[F_NWORK] = (unsigned long long)d.nwork;
+  f.v[F_WORK] = (unsigned long long)d.work;
+  f.v[F_WSEG] = (unsigned long long)d.wseg;
+  f.v[F_TICKET] = (unsigned long long)d.ticket;
+  f.v[F_TABLE] = (unsigned long long)d.table;
+  f.v[F_CODES] = (unsigned long long)d.codes;
+  f.v[F_PHI0F] = (unsigned long long)d.phi0f;
+  f.v[F_PHI0I] = (unsigned long long)d.phi0i;
+  f.v[F_PHI1F] = (unsigned long long)d.phi1f;
+  f.v[F_PHI1I] = (unsigned long long)d.phi1i;
+  f.v[F_P3F] = (unsigned long long)d.p3f;
+  f.v[F_P3F32] = (unsigned long long)d.p3f32;
+  f.v[F_P3I] = (unsigned long long)d.p3i;
+  f.v[F_FSUM] = (unsigned long long)d.fsum;
+  f.v[F_ICNT] = (unsigned long long)d.icnt;
+  f.v[F_KC] = d.ni ? (unsigned long long)d.col[d.kslot[0]].p : 0ull;
+  for (int i = 0; i < d.nx && i < 6; ++i) f.v[F_X0 + i] = (unsigned long long)d.col[d.xslot[i]].p;
+  // outer views of the predicate bits, in the order the generator assigned their slots
+  int used[MAXOUT] = {0}, nov = 0;
+  for (int b = 0; b < (d.nfam ? d.nob : 0); ++b) {
+    const int ov = d.obit_outer[b];
+    bool seen = false;
+    for (int j = 0; j < nov; ++j) seen = seen || used[j] == ov;
+    if (!seen && nov < 6) {
+      used[nov] = ov;
+      f.v[F_OV0 + nov] = (unsigned long long)d.outer[ov].v.v64;
+      ++nov;
+    }
+  }
+  void *fargs[] = {&f};
+  return cudaLaunchKernel(g.fn, dim3(grid), dim3(g.block), fargs, g.smem, s);
 }
 
 }  // namespace lmfao

@@ -19,13 +19,31 @@ struct GenRootPass {
   const void *fn = nullptr;  // kernel handle (cudaKernel_t) or null: the template kernel runs
   int block = 0;
   size_t smem = 0;
+  bool family = false;       // generated from the general shape (codegen_family.cpp)
   std::string why;           // why the kernel was not generated (empty when it was)
 };
 
-// Generate (or take from the cache) the kernel for the lean root pass described by d.
-// Returns a null handle, with the reason, when the shape is outside what is generated or
-// when compilation fails; the caller then launches the template kernel.
-GenRootPass gen_root_pass(const DFast &d, bool fp64, int device);
+// Generate (or take from the cache) the kernel for the specialised root pass described by d:
+// the lean generator for lean passes, the general one otherwise; thr are the host copies of
+// the bucket thresholds the pass reads. Returns a null handle, with the reason, when the shape
+// is outside what is generated or when compilation fails; the caller then launches the
+// template kernel.
+GenRootPass gen_root_pass(const DFast &d, bool fp64, int device, const std::vector<float> &thr);
+
+// General shape (codegen_family.cpp): shared-memory layout, argument slots, eligibility
+// and source.
+struct FamilyLayout {
+  int rs;
+  size_t off_tab, off_code, off_pf, off_pi, off_h, off_b4f, off_b4i, smem;
+};
+enum FamArg {
+  F_NWORK, F_WORK, F_WSEG, F_TICKET, F_TABLE, F_CODES, F_PHI0F, F_PHI0I, F_PHI1F, F_PHI1I, F_P3F, F_P3F32, F_P3I,
+  F_FSUM, F_ICNT, F_KC, F_X0, F_OV0 = F_X0 + 6, F_NARGS = F_OV0 + 6
+};
+FamilyLayout family_layout(const DFast &d, bool fp64, int block);
+bool family_eligible(const DFast &d, std::string &why, const std::vector<DGroupRef> &grefs4);
+std::string gen_family_source(const DFast &d, bool fp64, int block, const std::vector<float> &thr,
+                              const std::vector<DGroupRef> &grefs4, const std::vector<DMirror> &mirror);
 
 // Launch a generated root pass on stream s over `grid` CTAs.
 cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid, cudaStream_t s);

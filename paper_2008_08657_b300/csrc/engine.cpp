@@ -1565,11 +1565,11 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   // plan-specialised kernel (code generation) for large root relations; LMFAO_CODEGEN=0
   // disables it, =1 forces it at any size
   P.gen = GenRootPass{};
-  if (F.lean) {
+  {
     const char *env = std::getenv("LMFAO_CODEGEN");
     const int mode = env ? std::atoi(env) : -1;
     if (mode == 1 || (mode != 0 && ctx->rels[P.root].nrows >= (int64_t(1) << 20))) {
-      P.gen = gen_root_pass(d, P.fp64, ctx->device);
+      P.gen = gen_root_pass(d, P.fp64, ctx->device, P.thr);
       if (P.gen.fn) {
         int per_sm = 1, nsm = 148;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.gen.fn, P.gen.block, P.gen.smem);

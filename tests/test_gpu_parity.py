@@ -46,6 +46,26 @@ def test_tiny_schemas_match_oracle(seed, precision, mode, segment):
         compare(q, g, r, where=f"seed {seed} query {i}")
 
 
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("segment", ["R1", "R2", "R4"])
+def test_tiny_schemas_generated_root_pass(seed, precision, segment, monkeypatch):
+    """Tiny schemas (duplicate and dangling keys, group-bys, buckets, filters) with the root
+    pass generated at plan time at any size; shapes outside the generator keep the template."""
+    monkeypatch.setenv("LMFAO_CODEGEN", "1")
+    shared3 = seed % 2 == 1
+    if segment == "R4" and not shared3:
+        pytest.skip("R4 exists only in the five-relation variant")
+    rels = W.tiny_schema(seed, shared3=shared3, fd=True)
+    qs = W.tiny_queries(seed, rels, nq=6, group_attrs=TINY_GROUPS, bucket_attrs=TINY_BUCKETS)
+    ref = O.evaluate(rels, qs)
+    parent = [-1, 0, 0, 2, 0][:len(rels)]
+    got, _ = run_engine(rels, qs, precision=precision, mode="factorised", root="R0", segment=segment,
+                        join_parent=parent)
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"seed {seed} query {i}")
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_star_config_full_size(precision):
     rels = W.star_schema()
@@ -113,9 +133,13 @@ def test_plan_invariance_retailer():
             assert (np.abs(a["sums"] - b["sums"]) <= 1e-4 * scale).all(), plan
 
 
-@pytest.mark.parametrize("n_fact,mode", [(300_000, "auto"), (1_000_000, "auto"), (1_000_000, "generic")])
-def test_dt_level_and_cart_variances(n_fact, mode):
+@pytest.mark.parametrize("n_fact,mode,codegen", [(300_000, "auto", "0"), (1_000_000, "auto", "0"),
+                                                 (1_000_000, "auto", "1"), (1_000_000, "generic", "0")])
+def test_dt_level_and_cart_variances(n_fact, mode, codegen, monkeypatch):
+    """A decision-tree level (8 leaves as a filter family); codegen "1" runs the root pass
+    generated at plan time, "0" the template kernel."""
     import torch
+    monkeypatch.setenv("LMFAO_CODEGEN", codegen)
     rels = W.retailer_schema(n_fact=n_fact)
     qs, splits, thr = W.dt_level_batch(rels)
     ref = O.evaluate(rels, qs)
@@ -127,6 +151,7 @@ def test_dt_level_and_cart_variances(n_fact, mode):
     phys = e.describe()["physical"]
     if n_fact >= 1_000_000 and mode == "auto":
         assert phys["filter_family"] == 8 and phys["per_tuple_items"] == 0
+        assert phys["root_pass"]["generated"] == (codegen == "1"), phys["root_pass"]["not_generated_because"]
     e.run()
     got = e.fetch_all()
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
