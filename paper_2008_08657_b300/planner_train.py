@@ -196,7 +196,7 @@ def main():
     ap.add_argument("--fact-min", type=float, default=1e5)
     ap.add_argument("--fact-max", type=float, default=5e6)
     ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--out", default="gpurun_out/planner")
+    ap.add_argument("--out", default="planner_out")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     t0 = time.time()
