@@ -3064,7 +3064,13 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
       info->n_segments = P ? P->nseg : 0;
       info->n_views = (int)ctx->logical.views.size();
       info->n_groups = (int)ctx->logical.groups.size();
-      info->n_kernels = P ? (int)P->vk.size() * 2 + 2 + (P->comb.empty() ? 0 : 1) + (P->fast.on ? 2 : 0) : 0;
+      int combine_kernels = P && !P->comb.empty() ? 1 : 0;
+      if (P && !P->comb.empty() && !P->use_c3 && P->use_c4) {  // projection combine: several kernels
+        const DComb4 &c4 = P->c4;
+        combine_kernels = 1 + ((c4.need_d1 || c4.nent3) ? 1 : 0) + (c4.nent3 ? 1 : 0) + (c4.nent012 ? 1 : 0);
+        for (int c = 1; c <= 3; ++c) combine_kernels += (c4.tab[c].nt + c4.tab[c].ng) ? 1 : 0;
+      }
+      info->n_kernels = P ? (int)P->vk.size() * 2 + 2 + combine_kernels + (P->fast.on ? 2 : 0) : 0;
       info->mode = P ? P->mode : 0;
       info->predicted_ms = predicted;
       info->plan_ms = P ? P->plan_ms : 0;
