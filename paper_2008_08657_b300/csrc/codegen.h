@@ -34,6 +34,7 @@ GenRootPass gen_root_pass(const DFast &d, bool fp64, int device, const std::vect
 // and source.
 struct FamilyLayout {
   int rs;
+  bool pi_smem;  // integral root-to-inner partials in shared memory (also when the float ones are not)
   size_t off_tab, off_code, off_pf, off_pi, off_h, off_b4f, off_b4i, smem;
 };
 enum FamArg {

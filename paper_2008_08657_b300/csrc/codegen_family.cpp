@@ -8,7 +8,10 @@
 // columns, the predicate bits of the tuple's filter (outer bits once per segment, inner bits
 // from the inner row, root bits per tuple) and its leaf, bucket codes of root columns as
 // comparisons against the constant thresholds (once per tuple and column), and the scatter of
-// each histogram set, root-to-inner column and CTA-private item with constant offsets.
+// each histogram set, root-to-inner column and CTA-private item with constant offsets. The
+// integral root-to-inner partials stay in shared memory when they fit even if the float ones
+// do not (a decision-tree level: 3,700 items x 8 leaves), which removes one global atomic per
+// tuple and column.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -55,14 +58,21 @@ FamilyLayout family_layout(const DFast &d, bool fp64, int block) {
     return at;
   };
   const int ls = std::max(1, d.b3leaf);
-  L.off_tab = region(ts * (size_t)nkeys * L.rs);
-  L.off_code = region(fp64 ? 4 * (size_t)nkeys * d.ncode : 0);
-  L.off_pf = region(d.smem_p ? ts * (size_t)nkeys * d.n3f * ls : 0);
-  L.off_pi = region(d.smem_p ? 4 * (size_t)nkeys * d.n3i * ls : 0);
-  L.off_h = region(4 * (size_t)(block / 32) * (d.hist_f + d.hist_i));
-  L.off_b4f = region(ts * (size_t)d.b4_fcells);
-  L.off_b4i = region(4 * (size_t)d.b4_icells);
-  L.smem = off;
+  const size_t pi_bytes = 4 * (size_t)nkeys * d.n3i * ls;
+  for (int pass = 0; pass < 2; ++pass) {
+    // first try the integral partials in shared memory even when the float ones do not fit
+    L.pi_smem = d.smem_p || (pass == 0 && d.n3i > 0);
+    off = 0;
+    L.off_tab = region(ts * (size_t)nkeys * L.rs);
+    L.off_code = region(fp64 ? 4 * (size_t)nkeys * d.ncode : 0);
+    L.off_pf = region(d.smem_p ? ts * (size_t)nkeys * d.n3f * ls : 0);
+    L.off_pi = region(L.pi_smem ? pi_bytes : 0);
+    L.off_h = region(4 * (size_t)(block / 32) * (d.hist_f + d.hist_i));
+    L.off_b4f = region(ts * (size_t)d.b4_fcells);
+    L.off_b4i = region(4 * (size_t)d.b4_icells);
+    L.smem = off;
+    if (d.smem_p || !L.pi_smem || L.smem <= 200 * 1024) break;
+  }
   return L;
 }
 
@@ -172,10 +182,10 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     if (fp64 && d.ncode)
       o << "  for (int i = tid; i < " << nkeys * d.ncode << "; i += " << block << ") tcode[i] = gcod[i];\n";
   }
-  if (d.smem_p) {
+  if (d.smem_p)
     o << "  for (int i = tid; i < " << nkeys * d.n3f * ls << "; i += " << block << ") Pf[i] = (T)0;\n";
+  if (L.pi_smem)
     o << "  for (int i = tid; i < " << nkeys * d.n3i * ls << "; i += " << block << ") Pi[i] = 0u;\n";
-  }
   o << "  for (int i = tid; i < " << (long long)(block / 32) * (d.hist_f + d.hist_i) << "; i += " << block
     << ") hf0[i] = 0.f;\n";
   o << "  for (int i = tid; i < " << d.b4_fcells << "; i += " << block << ") b4f[i] = (T)0;\n";
@@ -286,7 +296,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
       o << "      { const T val = " << sel_u(d.j3[c]) << "; if (val != (T)0) {";
       if (d.int3[c]) {
         o << " const unsigned long long iv = (unsigned long long)val * ws;";
-        if (d.smem_p) o << " atomicAdd(Pi + (long long)k * " << d.n3i * ls << " + " << pc << ", (unsigned int)iv);";
+        if (L.pi_smem) o << " atomicAdd(Pi + (long long)k * " << d.n3i * ls << " + " << pc << ", (unsigned int)iv);";
         else o << " atomicAdd(p3i + (long long)k * " << d.n3i * ls << " + " << pc << ", iv);";
       } else {
         if (d.smem_p) o << " atomicAdd(Pf + (long long)k * " << d.n3f * ls << " + " << pc << ", val * wsT);";
@@ -459,12 +469,12 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n  }\n";
   // end of the CTA: shared partials and CTA-private items to the outputs
   o << "  __syncthreads();\n";
-  if (d.smem_p) {
+  if (d.smem_p)
     o << "  for (int i = tid; i < " << nkeys * d.n3f * ls << "; i += " << block
       << ") if (Pf[i] != (T)0) atomicAdd(p3f + i, (double)Pf[i]);\n";
+  if (L.pi_smem)
     o << "  for (int i = tid; i < " << nkeys * d.n3i * ls << "; i += " << block
       << ") if (Pi[i]) atomicAdd(p3i + i, (unsigned long long)Pi[i]);\n";
-  }
   for (const DMirror &mr : mirror) {
     if (mr.integral)
       o << "  for (int i = tid; i < " << mr.len << "; i += " << block << ") if (b4i[" << mr.soff
