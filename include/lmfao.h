@@ -196,7 +196,13 @@ LMFAO_API int lmfao_clear_batch(struct lmfao_ctx *ctx);
  * directional views and their merging, view groups; then the physical plan: the root
  * relation reorganised as a trie ordered by its segment key, view layouts, kernel
  * sequence. opts may be NULL (heuristic FP32). info may be NULL. May launch device
- * work (reorganisation, autotuning) on the context's internal stream and waits for it. */
+ * work (reorganisation, autotuning) on the context's internal stream and waits for it.
+ * For a root relation of at least 2^20 tuples the root pass is generated for the batch
+ * and compiled with NVRTC (Fig. 1's code generation; about 0.3 s per new shape, cached
+ * for the life of the process; a shape outside the generators uses the built-in kernel).
+ * Environment: LMFAO_CODEGEN=0 never generates, =1 generates at any size;
+ * LMFAO_NO_PROJECTION_COMBINE selects the entry-wise combine where the projection
+ * combine would run. */
 LMFAO_API int lmfao_plan(struct lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *info);
 
 /* Candidate physical plans of the current batch (root relation, segment relation, root
