@@ -2326,52 +2326,11 @@ void setup_passes(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   cb.n0i = fp.n0i;
   cb.phi0f = P.phi0f;
   cb.phi0i = P.phi0i;
-  cb.nitems = (int)P.comb.size();
-  cb.items = P.arena.upload(P.comb, s);
   cb.grefs = fp.grefs;
   cb.thr = fp.thr;
   cb.fsum = P.fsum;
   cb.icnt = P.icnt;
   if (P.fast.on) setup_fast(ctx, P, t, cb);
-  // mirror outputs of queries with outer-grouped items in shared memory while they fit
-  std::vector<int> item_smem(P.comb.size(), -1);
-  std::vector<DMirror> mirrors;
-  std::map<int64_t, int> fmir, imir;  // query output base -> smem offset
-  int fcells = 0, icells = 0;
-  const int budget_cells = 12 * 1024;
-  for (size_t i = 0; i < P.comb.size(); ++i) {
-    const DCombItem &it = P.comb[i];
-    if (it.nog == 0 && it.block < 0) continue;
-    // find the query owning this output
-    for (auto &q : P.qout) {
-      int64_t base = it.integral ? q.io : q.fo;
-      int64_t len = it.integral ? q.cells * (1 + q.naggs) : q.cells * q.naggs;
-      if (it.out < base || it.out >= base + len) continue;
-      auto &mp = it.integral ? imir : fmir;
-      int &cells = it.integral ? icells : fcells;
-      auto f = mp.find(base);
-      if (f == mp.end()) {
-        if (cells + len > budget_cells) break;
-        mp[base] = cells;
-        mirrors.push_back(DMirror{base, cells, (int)len, it.integral, 0});
-        f = mp.find(base);
-        cells += (int)len;
-      }
-      item_smem[i] = f->second + (int)(it.out - base);
-      break;
-    }
-  }
-  cb.item_smem = P.arena.upload(item_smem, s);
-  cb.smem_fcells = fcells;
-  cb.smem_icells = icells;
-  cb.nmirror = (int)mirrors.size();
-  cb.mirror = P.arena.upload(mirrors, s);
-  cb.tile = 32;
-  while (cb.tile > 1 && combine_smem(cb, P.fp64) > 200 * 1024) cb.tile /= 2;
-  P.cb_smem = combine_smem(cb, P.fp64);
-  P.cb_block = 256;
-  int64_t ntiles = (P.nseg + cb.tile - 1) / cb.tile;
-  P.cb_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 2));
   setup_combine2(ctx, P, pparts);
   P.use_c3 = false;
   P.use_c4 = false;

@@ -8,9 +8,6 @@
 //                        root relation, reorganised as segments; per tuple the inner view
 //                        lookups and row terms; per segment the sums PHI (the view from
 //                        the root to the segment relation); per tuple the direct items.
-//  combine            -- SUM over segments of psi(seg) * PHI(seg): outer view lookups once
-//                        per segment, FP32 (or FP64) products, per-CTA partial sums,
-//                        FP64 / INT64 cross-CTA reduction.
 //  reorganisation     -- segment ids, histogram and scatter (plan time).
 #include <cuda_runtime.h>
 
@@ -366,135 +363,6 @@ __global__ void __launch_bounds__(256) fact_pass_kernel(DFactPass d) {
   }
 }
 
-// ------------------------------------------------------------------ combine
-// Tile of d.tile segments per iteration: psi of every outer term and the PHI rows are
-// staged in shared memory; each thread owns items and sums over the tile's segments.
-template <typename T>
-__global__ void __launch_bounds__(256) combine_kernel(DCombine d) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int bs = blockDim.x, tid = threadIdx.x, TS = d.tile;
-  unsigned long long *psii = reinterpret_cast<unsigned long long *>(smem);     // TS x npsi
-  unsigned long long *phii = psii + (size_t)TS * d.npsi;                      // TS x n0i
-  unsigned long long *acci = phii + (size_t)TS * d.n0i;                       // nitems
-  unsigned long long *outi = acci + d.nitems;                                 // smem_icells
-  T *psif = reinterpret_cast<T *>(outi + d.smem_icells);                      // TS x npsi
-  T *phif = psif + (size_t)TS * d.npsi;                                       // TS x n0f
-  T *accf = phif + (size_t)TS * d.n0f;                                        // nitems
-  T *outf = accf + d.nitems;                                                  // smem_fcells
-
-  for (int i = tid; i < d.nitems; i += bs) { acci[i] = 0; accf[i] = T(0); }
-  for (int i = tid; i < d.smem_icells; i += bs) outi[i] = 0;
-  for (int i = tid; i < d.smem_fcells; i += bs) outf[i] = T(0);
-
-  const int64_t ntiles = (d.nseg + TS - 1) / TS;
-  for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
-    const int64_t seg0 = tl * TS;
-    __syncthreads();
-    for (int idx = tid; idx < TS * d.npsi; idx += bs) {
-      int s = idx / d.npsi, t = idx - s * d.npsi;
-      int64_t seg = seg0 + s;
-      T pf = T(0);
-      unsigned long long pi = 0;
-      if (seg < d.nseg && d.wseg[seg]) eval_psi<T>(d.psi[t], d.segfacs, d.psiparts, d.outer, d.seg, seg, pf, pi);
-      psif[idx] = pf;
-      psii[idx] = pi;
-    }
-    for (int idx = tid; idx < TS * d.n0f; idx += bs) {
-      int s = idx / d.n0f;
-      int64_t seg = seg0 + s;
-      phif[idx] = seg < d.nseg ? reinterpret_cast<const T *>(d.phi0f)[seg * d.n0f + (idx - s * d.n0f)] : T(0);
-    }
-    for (int idx = tid; idx < TS * d.n0i; idx += bs) {
-      int s = idx / d.n0i;
-      int64_t seg = seg0 + s;
-      phii[idx] = seg < d.nseg ? d.phi0i[seg * d.n0i + (idx - s * d.n0i)] : 0ull;
-    }
-    __syncthreads();
-    for (int it = tid; it < d.nitems; it += bs) {
-      const DCombItem item = d.items[it];
-      const int so = d.item_smem[it];
-      if (item.block >= 0) {  // B1: per-segment sums grouped by the inner group codes
-        const DB1Set S = d.sets[item.block];
-        for (int s = 0; s < TS; ++s) {
-          int64_t seg = seg0 + s;
-          if (seg >= d.nseg) break;
-          T pf = psif[s * d.npsi + item.psi];
-          unsigned long long pi = psii[s * d.npsi + item.psi];
-          if (item.integral ? (pi == 0) : (pf == T(0))) continue;
-          bool ok = true;
-          int64_t oc = item.nog ? outer_cell(d.grefs + item.og0, item.nog, d.outer, d.seg, seg, ok) : 0;
-          if (!ok) continue;
-          for (int g = 0; g < S.G; ++g) {
-            int64_t cell = oc;
-            for (int i = 0; i < S.nref; ++i) cell += ((g / S.radix[i]) % S.dom[i]) * d.grefs[item.ig0 + i].stride;
-            if (item.yint && !item.integral) {
-              unsigned int ph = d.phi1i[seg * d.phi1i_seg + S.gbase_i + (int64_t)g * S.ni + item.col];
-              if (!ph) continue;
-              T v = pf * (T)ph;
-              if (so >= 0) atomicAdd(outf + so + cell * item.cellmul, v);
-              else atomic_add_out<T>(d.fsum + item.out + cell * item.cellmul, v);
-            } else if (item.integral) {
-              unsigned int ph = d.phi1i[seg * d.phi1i_seg + S.gbase_i + (int64_t)g * S.ni + item.col];
-              if (!ph) continue;
-              unsigned long long v = pi * ph;
-              if (so >= 0) atomicAdd(outi + so + cell * item.cellmul, v);
-              else atomicAdd(d.icnt + item.out + cell * item.cellmul, v);
-            } else {
-              float ph = d.phi1f[seg * d.phi1f_seg + S.gbase_f + (int64_t)g * S.nf + item.col];
-              if (ph == 0.f) continue;
-              T v = pf * (T)ph;
-              if (so >= 0) atomicAdd(outf + so + cell * item.cellmul, v);
-              else atomic_add_out<T>(d.fsum + item.out + cell * item.cellmul, v);
-            }
-          }
-        }
-        continue;
-      }
-      for (int s = 0; s < TS; ++s) {
-        int64_t seg = seg0 + s;
-        if (seg >= d.nseg) break;
-        if (item.integral) {
-          unsigned long long v = psii[s * d.npsi + item.psi];
-          if (!v) continue;
-          v *= phii[s * d.n0i + item.col];
-          if (!v) continue;
-          if (item.nog == 0) { acci[it] += v; continue; }
-          bool ok = true;
-          int64_t cell = outer_cell(d.grefs + item.og0, item.nog, d.outer, d.seg, seg, ok);
-          if (!ok) continue;
-          if (so >= 0) atomicAdd(outi + so + cell * item.cellmul, v);
-          else atomicAdd(d.icnt + item.out + cell * item.cellmul, v);
-        } else {
-          T v = psif[s * d.npsi + item.psi];
-          if (v == T(0)) continue;
-          v *= phif[s * d.n0f + item.col];
-          if (v == T(0)) continue;
-          if (item.nog == 0) { accf[it] += v; continue; }
-          bool ok = true;
-          int64_t cell = outer_cell(d.grefs + item.og0, item.nog, d.outer, d.seg, seg, ok);
-          if (!ok) continue;
-          if (so >= 0) atomicAdd(outf + so + cell * item.cellmul, v);
-          else atomic_add_out<T>(d.fsum + item.out + cell * item.cellmul, v);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  for (int it = tid; it < d.nitems; it += bs) {
-    const DCombItem item = d.items[it];
-    if (item.block >= 0) continue;
-    if (item.integral) { if (acci[it]) atomicAdd(d.icnt + item.out, acci[it]); }
-    else if (accf[it] != T(0)) atomic_add_out<T>(d.fsum + item.out, accf[it]);
-  }
-  for (int m = 0; m < d.nmirror; ++m) {
-    DMirror mr = d.mirror[m];
-    for (int i = tid; i < mr.len; i += bs) {
-      if (mr.integral) { if (outi[mr.soff + i]) atomicAdd(d.icnt + mr.gout + i, outi[mr.soff + i]); }
-      else if (outf[mr.soff + i] != T(0)) atomic_add_out<T>(d.fsum + mr.gout + i, outf[mr.soff + i]);
-    }
-  }
-}
-
 // ------------------------------------------------------------------ reorganisation
 __global__ void segment_id_kernel(DCol c0, DCol c1, DCol c2, DCol c3, int ncols, int64_t r0, int64_t r1,
                                   int64_t r2, int64_t r3, int64_t n, int *segid) {
@@ -655,23 +523,6 @@ void launch_fact_pass(const DFactPass &d, bool fp64, int nb0, int grid, int bloc
   size_t smem = fact_pass_smem(d, fp64, block);
   if (fp64) launch_fp<double>(d, nb0, grid, block, smem, s);
   else launch_fp<float>(d, nb0, grid, block, smem, s);
-}
-
-size_t combine_smem(const DCombine &d, bool fp64) {
-  size_t ts = fp64 ? 8 : 4;
-  size_t b = 8 * ((size_t)d.tile * d.npsi + (size_t)d.tile * d.n0i + d.nitems + d.smem_icells);
-  b += ts * ((size_t)d.tile * d.npsi + (size_t)d.tile * d.n0f + d.nitems + d.smem_fcells);
-  return b;
-}
-
-void launch_combine(const DCombine &d, bool fp64, int grid, int block, size_t smem, cudaStream_t s) {
-  if (fp64) {
-    cudaFuncSetAttribute(combine_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    combine_kernel<double><<<grid, block, smem, s>>>(d);
-  } else {
-    cudaFuncSetAttribute(combine_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    combine_kernel<float><<<grid, block, smem, s>>>(d);
-  }
 }
 
 void launch_segment_ids(const DCol *cols, int ncols, const int64_t *radix, int64_t n, int *segid, cudaStream_t s) {

@@ -83,6 +83,9 @@ struct DB1Set {
   int64_t gbase_f, gbase_i;
 };
 
+// What every combine reads: the segments and their outer views, the outer terms psi, the
+// per-segment sums PHI0 / PHI1 and the outputs (the block, projection and entry combines take
+// their own descriptors from it).
 struct DCombine {
   int64_t nseg;
   const unsigned long long *wseg;
@@ -96,14 +99,8 @@ struct DCombine {
   int n0f, n0i;
   const void *phi0f;
   const unsigned long long *phi0i;
-  int nitems;
-  const DCombItem *items;
   const DGroupRef *grefs;
   const float *thr;
-  const int *item_smem;   // per item: smem output offset for grouped items (-1: global)
-  int smem_fcells, smem_icells;
-  int nmirror;
-  const DMirror *mirror;
   int nsets;
   const DB1Set *sets;
   const float *phi1f;
@@ -111,7 +108,6 @@ struct DCombine {
   int64_t phi1f_seg, phi1i_seg;
   double *fsum;
   unsigned long long *icnt;
-  int tile;
 };
 
 // One output entry of the combine: psi term x one Y column, written to
@@ -219,7 +215,6 @@ void launch_view_finish(const double *v64, float *v32, uint32_t *vint, const int
                         int ncols, int nint, int64_t nkeys, int *err, cudaStream_t s);
 void launch_segment_weights(const DSegWeight &d, cudaStream_t s);
 void launch_fact_pass(const DFactPass &d, bool fp64, int nb0, int grid, int block, cudaStream_t s);
-void launch_combine(const DCombine &d, bool fp64, int grid, int block, size_t smem, cudaStream_t s);
 void launch_segment_ids(const DCol *cols, int ncols, const int64_t *radix, int64_t n, int *segid,
                         cudaStream_t s);
 void launch_histogram(const int *segid, int64_t n, unsigned int *hist, cudaStream_t s);

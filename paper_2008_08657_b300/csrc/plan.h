@@ -10,7 +10,6 @@
 namespace lmfao {
 
 size_t fact_pass_smem(const DFactPass &d, bool fp64, int block);
-size_t combine_smem(const DCombine &d, bool fp64);
 
 // Join tree over the relations (Section 2 "the backbone of this plan is a join tree").
 struct JoinTree {
@@ -157,8 +156,7 @@ struct PhysPlan {
   bool use_c3 = false, no_c3 = false;
   int c3_grid = 0, c3_block = 512;
   DSegWeight sw{};
-  size_t cb_smem = 0;
-  int fp_grid = 0, fp_block = 256, cb_grid = 0, cb_block = 256;
+  int fp_grid = 0, fp_block = 256;
   std::vector<std::string> kernel_names;
   double plan_ms = 0;
 };
