@@ -108,6 +108,24 @@ int main() {
       if (!family_eligible(d, why, g4)) printf("dt_level%s FAIL not eligible: %s\n", sfx.c_str(), why.c_str());
       else check(("dt_level" + sfx).c_str(), gen_family_source(d, fp64, block, thr, g4, mir));
     }
+    {  // general pass without an inner relation: two value columns (float and uint8), an
+       // indicator factor and CTA-private items grouped by buckets of both columns
+      DFast d = lean_base();
+      d.lean = 0; d.smem_p = 0;
+      d.ni = 0; d.nx = 2; d.xslot[0] = 1; d.xslot[1] = 2; d.nw = 1; d.nm = 4;
+      d.mexp[1][0] = 1; d.mexp[2][1] = 1; d.mexp[3][0] = 2;
+      d.nind = 1; d.ind[0] = DFac{1, 1, 1, LMFAO_GT, 0.25f}; d.ind_mono[0] = 2;
+      d.nb4 = 2; d.b4_off[0] = 0; d.b4_off[1] = 2;
+      std::vector<DGroupRef> g4{DGroupRef{2, 1, 0, LMFAO_GB_BUCKET, 3, 4, 1}, DGroupRef{2, 2, 0, LMFAO_GB_BUCKET, 0, 3, 1}};
+      d.b4_j[0] = 0; d.b4_int[0] = 1; d.b4_g0[0] = 0; d.b4_ng[0] = 1; d.b4_so[0] = 0; d.b4_cellmul[0] = 1;
+      d.b4_j[1] = 3; d.b4_g0[1] = 1; d.b4_ng[1] = 1; d.b4_so[1] = 0; d.b4_cellmul[1] = 1;
+      d.b4_fcells = 8; d.b4_icells = 8;
+      std::vector<DMirror> mir{DMirror{0, 0, 8, 1, 0}, DMirror{0, 0, 8, 0, 0}};
+      std::vector<float> thr{0.5f, 1.5f, 2.5f, -1.f, 0.f, 1.f, 2.f};
+      std::string why;
+      if (!family_eligible(d, why, g4)) printf("general_no_inner%s FAIL not eligible: %s\n", sfx.c_str(), why.c_str());
+      else check(("general_no_inner" + sfx).c_str(), gen_family_source(d, fp64, block, thr, g4, mir));
+    }
   }
   return 0;
 }

@@ -1,7 +1,8 @@
 """The plan-time code generators (CPU): sources written for representative shapes (the
-Retailer- and Favorita-like lean passes, a pass without an inner relation, and a
-decision-tree level with leaf bits, leaf histograms, leaf-split partials and per-leaf
-CTA-private bucket items) compile with NVRTC for sm_103a, in FP32 and FP64, without register
+Retailer- and Favorita-like lean passes, a pass without an inner relation, a decision-tree
+level with leaf bits, leaf histograms, leaf-split partials and per-leaf CTA-private bucket
+items, and a general pass with an indicator factor and CTA-private items grouped by root
+buckets) compile with NVRTC for sm_103a, in FP32 and FP64, without register
 spills. Needs nvcc and NVRTC, not a GPU."""
 import os
 import shutil
@@ -33,7 +34,8 @@ def results():
     return {line.split()[0]: line.split()[1:] for line in out.splitlines() if line.strip()}
 
 
-SHAPES = [f"{s}_{p}" for s in ("lean_retailer", "lean_favorita", "lean_no_inner", "dt_level") for p in ("fp32", "fp64")]
+SHAPES = [f"{s}_{p}" for s in ("lean_retailer", "lean_favorita", "lean_no_inner", "dt_level", "general_no_inner")
+          for p in ("fp32", "fp64")]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
