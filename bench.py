@@ -221,6 +221,7 @@ def bench_lmfao(args):
         roofline["traffic"] = traffic
         roofline["traffic_source"] = tsrc
     # end to end through the C ABI: pinned host -> device copies, load, plan, run, fetch
+    got = eng.fetch_all() if rank == 0 and args.parity else None
     e2e = None
     if not args.skip_e2e:
         e2e = bench_e2e(args, rels, qs, torch, local)
@@ -249,7 +250,17 @@ def bench_lmfao(args):
         "e2e": e2e,
         "gpu_launches": info["n_kernels"] * args.steps,
     }
-    if rank == 0 and not args.skip_cpu:
+    if got is not None:
+        # every aggregate against the oracle over the whole workload, on all host cores; the same
+        # run is the CPU baseline
+        par = full_parity(rels, qs, got)
+        out["parity"] = par
+        out["cpu_baseline"] = {"value": n_fact / par["oracle_s"], "unit": UNIT, "cores": par["oracle_cores"],
+                               "kind": "oracle",
+                               "sample": f"the whole workload ({n_fact} fact tuples, {par['oracle_chunks']} chunks "
+                                         f"of 1M tuples over {par['oracle_cores']} processes), "
+                                         f"{par['oracle_s']} s"}
+    elif rank == 0 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(out))
@@ -310,6 +321,60 @@ def cpu_baseline(args, sample_rows=300_000):
             "host_cpus": os.cpu_count()}
 
 
+def _family(q, agg):
+    """Aggregate family for the error report: grouped or not (and how), and the degree of
+    the product (COUNT = 0, SUM(x) = 1, SUM(x_i x_j) = 2, ...)."""
+    deg = sum(int(p) if fn == "pow" else 1 for _a, fn, p in agg)
+    gb = q.get("groupby", [])
+    kind = "ungrouped" if not gb else ("bucketed" if any(k == "bucket" for _a, k, _t in gb) else
+                                       f"grouped{len(gb)}")
+    if q.get("filters"):
+        kind += "+filter"
+    return f"{kind}:deg{deg}"
+
+
+def parity_report(qs, got, ref, oracle_s, processes, chunks):
+    """Every aggregate of the engine's results against the chunked FP64/INT64 oracle: group
+    keys and counts bit-exact, integral aggregates exact, and per family the largest error
+    relative to the sum of absolute terms of the aggregate (the tolerance measure)."""
+    fam = {}
+    keys_ok = counts_ok = True
+    worst = 0.0
+    for q, g, r in zip(qs, got, ref):
+        if g["keys"].shape != r["keys"].shape or not np.array_equal(g["keys"], r["keys"]):
+            keys_ok = False
+            continue
+        counts_ok &= bool(np.array_equal(g["counts"], r["counts"]))
+        for j, agg in enumerate(q["aggs"]):
+            name = _family(q, agg)
+            f = fam.setdefault(name, {"aggregates": 0, "max_rel_err": 0.0, "exact": True})
+            f["aggregates"] += 1
+            gj, rj, aj = g["sums"][:, j], r["sums"][:, j], r["abs"][:, j]
+            if not agg or all(fn == "ind" for _a, fn, _p in agg):
+                f["exact"] &= bool(np.array_equal(gj, rj))
+                counts_ok &= bool(np.array_equal(gj, rj))
+                continue
+            err = np.abs(gj - rj)
+            nz = aj > 0
+            e = float((err[nz] / aj[nz]).max()) if nz.any() else 0.0
+            if (~nz).any() and float(err[~nz].max()) > 1e-9:
+                e = float("inf")
+            f["max_rel_err"] = max(f["max_rel_err"], e)
+            worst = max(worst, e)
+    return {"families": fam, "group_keys_equal": keys_ok, "counts_exact": counts_ok, "max_rel_err": worst,
+            "tolerance": 1e-5, "within_tolerance": keys_ok and counts_ok and worst <= 1e-5,
+            "oracle": "chunked FP64/INT64 oracle over the whole workload", "oracle_chunks": chunks,
+            "oracle_cores": processes, "oracle_s": round(oracle_s, 1)}
+
+
+def full_parity(rels, qs, got):
+    from oracle import lmfao_oracle as O
+    procs = max(1, os.cpu_count() or 1)
+    ref, secs = O.evaluate_chunked(rels, qs, root=0, processes=procs)
+    chunks = -(-rels[0]["nrows"] // O.CHUNK)
+    return parity_report(qs, got, ref, secs, procs, chunks)
+
+
 def bench_reference(args):
     """Reference arm: the CPU oracle on a bounded sample per step (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -331,7 +396,7 @@ def bench_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": f"synthetic (seeded, {args.workload}-shaped)",
-        "config": workload_config(args, args.fact_rows, qs),
+        "config": workload_config(args, sample, qs),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"each step: the whole batch over a seeded {sample}-tuple fact relation "
                                    f"of the same shape with the same dimension relations"},
@@ -353,6 +418,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-parity", dest="parity", action="store_false",
+                    help="skip the comparison of every aggregate with the oracle over the whole workload")
     args = ap.parse_args()
     if args.fact_rows is None:
         args.fact_rows = WORKLOADS[args.workload][1]

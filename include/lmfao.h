@@ -106,7 +106,12 @@ typedef struct lmfao_predicate {  /* attr op t, compared on the stored FP32/inte
 } lmfao_predicate;
 
 /* ---- planning ---------------------------------------------------------------------- */
-enum { LMFAO_FP64 = 0, LMFAO_FP32 = 1, LMFAO_SPLIT_TF32 = 2 };  /* arithmetic of the path */
+/* Arithmetic of the path. FP64: the plain FP64 form (every product and sum in FP64).
+ * FP32: per-tuple products and per-segment sums in FP32, cross-CTA reductions in FP64,
+ * counts exact. SPLIT_BF16: as FP32, with the dense cross-relation contraction on the
+ * tensor cores, each FP32 operand split into two BF16 terms (three products, FP32
+ * accumulation). A precision this build does not evaluate gives LMFAO_ERR_UNSUPPORTED. */
+enum { LMFAO_FP64 = 0, LMFAO_FP32 = 1, LMFAO_SPLIT_BF16 = 2 };
 enum {
   LMFAO_PLAN_HEURISTIC = 0,   /* rule-based choices (largest relation as root, ...)        */
   LMFAO_PLAN_EXHAUSTIVE = 1,  /* time every candidate plan on the device, keep the fastest */
@@ -120,13 +125,14 @@ enum {
 enum { LMFAO_MODE_AUTO = 0, LMFAO_MODE_FACTORISED = 1, LMFAO_MODE_PER_TUPLE = 2, LMFAO_MODE_GENERIC = 3 };
 
 typedef struct lmfao_plan_opts {
-  int32_t precision;        /* LMFAO_FP64 (plain form), LMFAO_FP32, LMFAO_SPLIT_TF32     */
+  int32_t precision;        /* LMFAO_FP64 (plain form), LMFAO_FP32, LMFAO_SPLIT_BF16     */
   int32_t planner;          /* LMFAO_PLAN_*                                              */
   int32_t root_rel;         /* FORCED: relation id of the root relation (-1: default)   */
   int32_t segment_rel;      /* FORCED: child of the root whose join key orders the root
                                relation into segments (-1: none, -2: default)            */
   int32_t mode;             /* LMFAO_MODE_*: factorised views or per-tuple evaluation   */
-  int32_t autotune;         /* nonzero: time launch shapes once and keep the fastest    */
+  int32_t autotune;         /* nonzero: time launch shapes once and keep the fastest
+                               (LMFAO_ERR_UNSUPPORTED where this build has no tuner)     */
   const int32_t *join_parent; /* host, nullable: parent relation id per relation (-1 for
                                the tree root) to impose a join tree instead of GYO       */
   const int32_t *query_root;  /* host, nullable: logical root relation per query (-1:
@@ -257,10 +263,12 @@ LMFAO_API int lmfao_describe_plan(struct lmfao_ctx *ctx, char *buf, size_t len, 
 
 /* CART split variances (Section 3, decision trees) of bucketed queries, in FP64 on the
  * device: each query q in qids (host array of n ids) must have exactly one BUCKET
- * group-by with B = nthresholds + 1 buckets and aggregates (COUNT, SUM(y), SUM(y^2)).
- * For every threshold k < B - 1 the left fragment is buckets 0..k and the right the
- * rest; VARIANCE(T) = SUM(y^2) - SUM(y)^2 / |T| (0 if T is empty). `out` (device,
- * n x (B-1) x 2 doubles: left, right) is written asynchronously on `stream`. */
+ * group-by with B = nthresholds + 1 buckets (the same B for all) and exactly three
+ * aggregates, COUNT, SUM(y) and SUM(y^2) of one value attribute y, in any order (y^2
+ * written as y^2 or y * y); anything else gives LMFAO_ERR_ARG. For every threshold
+ * k < B - 1 the left fragment is buckets 0..k and the right the rest; VARIANCE(T) =
+ * SUM(y^2) - SUM(y)^2 / |T| (0 if T is empty). `out` (device, n x (B-1) x 2 doubles:
+ * left, right) is written asynchronously on `stream`. */
 LMFAO_API int lmfao_cart_variances(struct lmfao_ctx *ctx, const int *qids, int n, double *out, void *stream);
 
 /* Allocation-free variant of lmfao_cart_variances (same arguments, same results), for
@@ -272,8 +280,12 @@ LMFAO_API int lmfao_cart_variances(struct lmfao_ctx *ctx, const int *qids, int n
  * LMFAO_NOALLOC_MAX_QUERIES entries (192 KiB, held on every device that loads the
  * library until the process exits); n above that limit gives LMFAO_ERR_ARG. The first
  * call on a device looks up the array's device address, so make that first call before
- * any stream capture. All calls on a device share the array: calls whose work overlaps
- * on the GPU race on it. No cudaMalloc, cudaFree or other allocating routine is called. */
+ * any stream capture. Each call fills the descriptors on the host under a process-wide
+ * lock and copies them into the array with cudaMemcpyAsync on `stream` before its kernel,
+ * so calls from several host threads do not mix their descriptors; but all calls on a
+ * device share the one device array, so calls whose work overlaps on the GPU (other
+ * streams, other contexts) race on it. No cudaMalloc, cudaFree or other allocating
+ * routine is called. */
 #define LMFAO_NOALLOC_MAX_QUERIES 4096
 LMFAO_API int lmfao_cart_variances_noalloc(struct lmfao_ctx *ctx, const int *qids, int n, double *out,
                                            void *stream);

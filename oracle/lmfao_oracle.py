@@ -216,3 +216,116 @@ def cart_variances(result):
     left = var(cn[:-1], cs[:-1], cs2[:-1])
     right = var(cn[-1] - cn[:-1], cs[-1] - cs[:-1], cs2[-1] - cs2[:-1])
     return left, right
+
+
+# ---------------------------------------------------------------------------------------
+# Full-size evaluation: the join distributes over a partition of any one relation, so the
+# batch over D is the sum of the batch over the joins of consecutive row chunks of the fact
+# relation with the other relations (fixed 1M-tuple chunks, summed in chunk order, so the
+# result does not depend on the number of processes).
+# ---------------------------------------------------------------------------------------
+
+CHUNK = 1_000_000
+
+
+def _chunk_rels(rels, root, lo, hi):
+    R = rels[root]
+    part = dict(R, nrows=hi - lo, columns=[dict(c, data=c["data"][lo:hi]) for c in R["columns"]])
+    return [part if i == root else X for i, X in enumerate(rels)]
+
+
+def merge_results(queries, parts):
+    """Sum per-chunk results (lists of per-query results, in chunk order) into one result
+    per query: groups are the union of the chunks' groups, in ascending key order."""
+    out = []
+    for qi, q in enumerate(queries):
+        rs = [p[qi] for p in parts]
+        if not q.get("groupby"):
+            counts = np.zeros(1, dtype=np.int64)
+            sums = np.zeros((1, len(q["aggs"])))
+            abs_ = np.zeros((1, len(q["aggs"])))
+            for r in rs:
+                counts += r["counts"]
+                sums += r["sums"]
+                abs_ += r["abs"]
+            out.append({"keys": np.zeros((1, 0), dtype=np.int64), "counts": counts, "sums": sums, "abs": abs_})
+            continue
+        keys = np.concatenate([r["keys"] for r in rs], axis=0)
+        uk, inv = np.unique(keys, axis=0, return_inverse=True)
+        inv = inv.reshape(-1)
+        ng = len(uk)
+        counts = np.bincount(inv, weights=np.concatenate([r["counts"] for r in rs]).astype(np.float64),
+                             minlength=ng)
+        counts = np.rint(counts).astype(np.int64)
+        S = np.concatenate([r["sums"] for r in rs], axis=0)
+        A = np.concatenate([r["abs"] for r in rs], axis=0)
+        sums = np.stack([np.bincount(inv, weights=S[:, j], minlength=ng) for j in range(S.shape[1])], axis=1) \
+            if S.shape[1] else np.zeros((ng, 0))
+        abs_ = np.stack([np.bincount(inv, weights=A[:, j], minlength=ng) for j in range(A.shape[1])], axis=1) \
+            if A.shape[1] else np.zeros((ng, 0))
+        keep = counts > 0
+        out.append({"keys": uk[keep].astype(np.int64), "counts": counts[keep], "sums": sums[keep], "abs": abs_[keep]})
+    return out
+
+
+_W = {}  # worker state: the relations (fact columns attached from shared memory) and the batch
+
+
+def _worker_init(spec, others, queries, root, chunk):
+    from multiprocessing import shared_memory
+    cols, shms = [], []
+    for attr_meta, name, dtype, n in spec["cols"]:
+        shm = shared_memory.SharedMemory(name=name)
+        shms.append(shm)
+        cols.append(dict(attr_meta, data=np.ndarray((n,), dtype=dtype, buffer=shm.buf)))
+    fact = dict(spec["rel"], columns=cols)
+    rels = list(others)
+    rels.insert(root, fact)
+    _W.update(rels=rels, queries=queries, root=root, shms=shms, chunk=chunk)
+
+
+def _worker_chunk(i):
+    rels, root, chunk = _W["rels"], _W["root"], _W["chunk"]
+    n = rels[root]["nrows"]
+    lo, hi = i * chunk, min(n, (i + 1) * chunk)
+    return i, evaluate(_chunk_rels(rels, root, lo, hi), _W["queries"])
+
+
+def evaluate_chunked(rels, queries, root=0, processes=1, chunk=CHUNK):
+    """The batch over the natural join of ``rels``, evaluated over consecutive chunks of
+    ``chunk`` rows of relation ``root`` and summed in chunk order (``merge_results``).
+    With ``processes`` > 1 the chunks are spread over that many spawned processes that
+    read the root relation's columns from shared memory (the sum order stays the chunk
+    order). Returns (results, seconds)."""
+    import time
+    n = rels[root]["nrows"]
+    nchunks = max(1, -(-n // chunk))
+    t0 = time.perf_counter()
+    if processes <= 1 or nchunks == 1:
+        parts = [evaluate(_chunk_rels(rels, root, i * chunk, min(n, (i + 1) * chunk)), queries)
+                 for i in range(nchunks)]
+        return merge_results(queries, parts), time.perf_counter() - t0
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    R = rels[root]
+    shms, spec_cols = [], []
+    try:
+        for c in R["columns"]:
+            a = np.ascontiguousarray(c["data"])
+            shm = shared_memory.SharedMemory(create=True, size=max(1, a.nbytes))
+            shms.append(shm)
+            np.ndarray(a.shape, dtype=a.dtype, buffer=shm.buf)[:] = a
+            meta = {k: v for k, v in c.items() if k != "data"}
+            spec_cols.append((meta, shm.name, a.dtype.str, len(a)))
+        spec = {"rel": {k: v for k, v in R.items() if k != "columns"}, "cols": spec_cols}
+        others = [X for i, X in enumerate(rels) if i != root]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(processes, initializer=_worker_init, initargs=(spec, others, queries, root, chunk)) as pool:
+            parts = [None] * nchunks
+            for i, res in pool.imap_unordered(_worker_chunk, range(nchunks)):
+                parts[i] = res
+    finally:
+        for shm in shms:
+            shm.close()
+            shm.unlink()
+    return merge_results(queries, parts), time.perf_counter() - t0

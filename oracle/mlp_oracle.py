@@ -53,3 +53,16 @@ def gradient(x, t, p):
     gW1 = x.T @ dz1
     gb1 = dz1.sum(axis=0)
     return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, [gb3]])
+
+
+def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, "Adam: A Method for Stochastic Optimization", 2015,
+    Algorithm 1): exponential moving averages of the gradient and of its square, bias
+    correction by 1 - beta^step, and p - lr * m_hat / (sqrt(v_hat) + eps). Returns the new
+    (p, m, v) in float64."""
+    p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

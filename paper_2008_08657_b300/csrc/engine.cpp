@@ -2469,6 +2469,18 @@ lmfao_plan_opts default_opts() {
   return o;
 }
 
+// Options this engine does not evaluate are refused rather than replaced by others.
+void check_plan_opts(const lmfao_ctx *ctx, const lmfao_plan_opts &o) {
+  (void)ctx;
+  if (o.precision != LMFAO_FP64 && o.precision != LMFAO_FP32)
+    throw Error(o.precision == LMFAO_SPLIT_BF16 ? LMFAO_ERR_UNSUPPORTED : LMFAO_ERR_ARG,
+                o.precision == LMFAO_SPLIT_BF16 ? "precision LMFAO_SPLIT_BF16 is not available in this build"
+                                                : "unknown precision " + std::to_string(o.precision));
+  if (o.autotune) throw Error(LMFAO_ERR_UNSUPPORTED, "autotuning is not available in this build");
+  if (o.planner < LMFAO_PLAN_HEURISTIC || o.planner > LMFAO_PLAN_FORCED)
+    throw Error(LMFAO_ERR_ARG, "unknown planner " + std::to_string(o.planner));
+}
+
 std::vector<int> parent_links(lmfao_ctx *ctx, const lmfao_plan_opts &o) {
   int n = (int)ctx->rels.size();
   std::vector<int> par;
@@ -2760,6 +2772,64 @@ std::vector<float> predict(const CostModelFile &cm, const std::vector<float> &X,
 // ======================================================================================
 // C ABI
 // ======================================================================================
+namespace lmfao {
+
+// SUM(y) has one factor y (or y^1); SUM(y^2) has y^2 or y * y. Returns the attribute in *attr
+// and the power (1 or 2), or 0 when the aggregate is neither.
+static int single_attr_power(const std::vector<FactorIn> &fs, std::string *attr) {
+  int pw = 0;
+  for (const FactorIn &f : fs) {
+    if (!attr->empty() && f.attr != *attr) return 0;
+    *attr = f.attr;
+    pw += f.fn == LMFAO_FN_POW ? f.param : 1;
+  }
+  return fs.empty() ? 0 : pw;
+}
+
+int cart_descriptors(const lmfao_ctx *ctx, const int *qids, int n, int64_t *desc) {
+  if (!ctx->ran || !ctx->plan) throw Error(LMFAO_ERR_NOT_PLANNED, "no run yet");
+  const PhysPlan &P = *ctx->plan;
+  int nb = 0;
+  for (int i = 0; i < n; ++i) {
+    const int q = qids[i];
+    if (q < 0 || q >= (int)ctx->queries.size()) throw Error(LMFAO_ERR_ARG, "bad query id " + std::to_string(q));
+    const QueryIn &Q = ctx->queries[q];
+    const char *shape = "CART variances need one BUCKET group-by and aggregates COUNT, SUM(y), SUM(y^2) of one "
+                        "attribute y (in any order)";
+    if (Q.gb.size() != 1 || Q.gb[0].kind != LMFAO_GB_BUCKET || Q.aggs.size() != 3)
+      throw Error(LMFAO_ERR_ARG, std::string(shape) + " (query " + std::to_string(q) + ")");
+    int ic = -1, i1 = -1, i2 = -1;
+    std::string y;
+    for (int a = 0; a < 3; ++a) {
+      std::string attr = y;
+      const int pw = Q.aggs[a].empty() ? -1 : single_attr_power(Q.aggs[a], &attr);
+      if (pw == -1 && ic < 0) ic = a;
+      else if (pw == 1 && i1 < 0) { i1 = a; y = attr; }
+      else if (pw == 2 && i2 < 0) { i2 = a; y = attr; }
+      else throw Error(LMFAO_ERR_ARG, std::string(shape) + " (query " + std::to_string(q) + ")");
+    }
+    const QueryOut &qo = P.qout[q];
+    if (qo.integral[i1] || qo.integral[i2])
+      throw Error(LMFAO_ERR_ARG, std::string(shape) + ": y must be a value attribute (query " + std::to_string(q) + ")");
+    const int b = (int)Q.gb[0].thr.size() + 1;
+    if (i && b != nb) throw Error(LMFAO_ERR_ARG, "all queries need the same number of buckets");
+    nb = b;
+    if ((int)qo.cells != nb) throw Error(LMFAO_ERR_ARG, "all queries need the same number of buckets");
+    if (desc) {
+      int64_t *d = desc + (size_t)i * kCartDescWords;
+      d[0] = qo.io;
+      d[1] = qo.fo;
+      d[2] = qo.cells;
+      d[3] = qo.naggs;
+      d[4] = i1;
+      d[5] = i2;
+    }
+  }
+  return nb;
+}
+
+}  // namespace lmfao
+
 extern "C" {
 
 int lmfao_create(lmfao_ctx **out, int device) {
@@ -2970,6 +3040,7 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
     if (ctx->rels.empty()) return fail(ctx, LMFAO_ERR_ARG, "no relations loaded");
     lmfao_plan_opts o = default_opts();
     if (opts) o = *opts;
+    check_plan_opts(ctx, o);
     double predicted = -1;
     if (ctx->device >= 0 && (o.planner == LMFAO_PLAN_EXHAUSTIVE || o.planner == LMFAO_PLAN_LEARNED)) {
       std::vector<Cand> cands = candidates(ctx, o);
@@ -3274,28 +3345,14 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
 
 int lmfao_cart_variances(lmfao_ctx *ctx, const int *qids, int n, double *out, void *stream) {
   return guarded(ctx, [&]() -> int {
-    if (!ctx->ran || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
     if (n < 0 || (n && (!qids || !out))) return fail(ctx, LMFAO_ERR_ARG, "bad arguments");
+    std::vector<int64_t> qd((size_t)std::max(n, 0) * kCartDescWords);
+    const int nb = cart_descriptors(ctx, qids, n, qd.data());
+    if (!n || nb < 2) return LMFAO_OK;
     PhysPlan &P = *ctx->plan;
-    std::vector<int64_t> qd;
-    int nb_max = 0;
-    for (int i = 0; i < n; ++i) {
-      int q = qids[i];
-      if (q < 0 || q >= (int)ctx->queries.size()) return fail(ctx, LMFAO_ERR_ARG, "bad query id");
-      const QueryIn &Q = ctx->queries[q];
-      if (Q.gb.size() != 1 || Q.gb[0].kind != LMFAO_GB_BUCKET || Q.aggs.size() != 3)
-        return fail(ctx, LMFAO_ERR_ARG, "CART variances need one BUCKET group-by and aggregates COUNT, SUM(y), SUM(y^2)");
-      nb_max = std::max(nb_max, (int)Q.gb[0].thr.size() + 1);
-    }
-    for (int i = 0; i < n; ++i) {
-      const QueryOut &q = P.qout[qids[i]];
-      if ((int)q.cells != nb_max) return fail(ctx, LMFAO_ERR_ARG, "all queries need the same number of buckets");
-      qd.insert(qd.end(), {q.io, q.fo, q.cells, q.naggs, 1, 2});
-    }
-    if (!n || nb_max < 2) return LMFAO_OK;
     int64_t *dq = P.arena.upload(qd, ctx->stream);
     LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
-    launch_cart_variances(P.icnt, P.fsum, dq, n, nb_max, out, (cudaStream_t)stream);
+    launch_cart_variances(P.icnt, P.fsum, dq, n, nb, out, (cudaStream_t)stream);
     LMFAO_CUDA(cudaGetLastError());
     return LMFAO_OK;
   });

@@ -16,6 +16,12 @@
 // streams, or contexts used from several threads) race on it. Each call overwrites the
 // descriptors it uses before its kernel reads them, and the kernel reads nothing else
 // from the array, so no clearing is needed between calls.
+//
+// On the host side the descriptors are built in one process-wide staging array and copied
+// with cudaMemcpyAsync from it; a mutex is held from the first descriptor written until that
+// copy has returned (a copy from pageable memory has left the source buffer when it returns),
+// so calls from several host threads, on the same device or on different ones, do not mix
+// their descriptors.
 #include <mutex>
 #include <unordered_map>
 
@@ -23,22 +29,21 @@
 
 namespace {
 
-constexpr int kDescWords = 6;
+constexpr int kDescWords = lmfao::kCartDescWords;
 
 // Descriptor scratch: [query][icnt base, fsum base, buckets, aggregates, SUM(y) index, SUM(y^2) index].
 static __device__ __align__(256) long long g_cart_desc[LMFAO_NOALLOC_MAX_QUERIES * kDescWords];
 
-// Host-side copy of the descriptors (the source of the host-to-device copy).
-long long g_host_desc[LMFAO_NOALLOC_MAX_QUERIES * kDescWords];
+// Host staging copy of the descriptors (the source of the host-to-device copy); guarded by g_mu.
+int64_t g_host_desc[LMFAO_NOALLOC_MAX_QUERIES * kDescWords];
 
-std::mutex g_mu;
+std::mutex g_mu;                          // guards g_host_desc and g_addr
 std::unordered_map<int, void *> g_addr;  // device -> device address of g_cart_desc
 
-// Device address of the scratch array on `device`, which must be the current device.
-// The name g_cart_desc in host code is only a host-side stand-in for the symbol; kernels
-// must receive the address obtained here.
-void *scratch_address(int device) {
-  std::lock_guard<std::mutex> lock(g_mu);
+// Device address of the scratch array on `device`, which must be the current device; the
+// caller holds g_mu. The name g_cart_desc in host code is only a host-side stand-in for the
+// symbol; kernels must receive the address obtained here.
+void *scratch_address_locked(int device) {
   auto it = g_addr.find(device);
   if (it != g_addr.end()) return it->second;
   void *p = nullptr;
@@ -59,51 +64,31 @@ extern "C" int lmfao_cart_variances_noalloc(lmfao_ctx *ctx, const int *qids, int
   try {
     ctx->last_error.clear();
     if (ctx->device < 0) throw lmfao::Error(LMFAO_ERR_NOT_PLANNED, "host-only context");
-    if (cudaSetDevice(ctx->device) != cudaSuccess) {
-      cudaGetLastError();
-      throw lmfao::Error(LMFAO_ERR_CUDA, "cudaSetDevice failed");
-    }
-    if (!ctx->ran || !ctx->plan) throw lmfao::Error(LMFAO_ERR_NOT_PLANNED, "no run yet");
     if (n < 0 || (n && (!qids || !out))) throw lmfao::Error(LMFAO_ERR_ARG, "bad arguments");
     if (n > LMFAO_NOALLOC_MAX_QUERIES)
       throw lmfao::Error(LMFAO_ERR_ARG, "lmfao_cart_variances_noalloc takes at most " +
                                             std::to_string(LMFAO_NOALLOC_MAX_QUERIES) + " queries per call (got " +
                                             std::to_string(n) + ")");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+      cudaGetLastError();
+      throw lmfao::Error(LMFAO_ERR_CUDA, "cudaSetDevice failed");
+    }
+    // the same checks as lmfao_cart_variances, without writing descriptors yet
+    const int nb = lmfao::cart_descriptors(ctx, qids, n, nullptr);
+    if (!n || nb < 2) return LMFAO_OK;
     lmfao::PhysPlan &P = *ctx->plan;
-    int nb_max = 0;
-    for (int i = 0; i < n; ++i) {
-      int q = qids[i];
-      if (q < 0 || q >= (int)ctx->queries.size()) throw lmfao::Error(LMFAO_ERR_ARG, "bad query id");
-      const lmfao::QueryIn &Q = ctx->queries[q];
-      if (Q.gb.size() != 1 || Q.gb[0].kind != LMFAO_GB_BUCKET || Q.aggs.size() != 3)
-        throw lmfao::Error(LMFAO_ERR_ARG,
-                           "CART variances need one BUCKET group-by and aggregates COUNT, SUM(y), SUM(y^2)");
-      nb_max = std::max(nb_max, (int)Q.gb[0].thr.size() + 1);
-    }
-    for (int i = 0; i < n; ++i) {
-      const lmfao::QueryOut &q = P.qout[qids[i]];
-      if ((int)q.cells != nb_max) throw lmfao::Error(LMFAO_ERR_ARG, "all queries need the same number of buckets");
-      long long *d = g_host_desc + (size_t)i * kDescWords;
-      d[0] = q.io;
-      d[1] = q.fo;
-      d[2] = q.cells;
-      d[3] = q.naggs;
-      d[4] = 1;
-      d[5] = 2;
-    }
-    if (!n || nb_max < 2) return LMFAO_OK;
-    // First call on this device: look up the array's device address (the device is current).
-    void *desc = scratch_address(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    // The copy from pageable host memory is staged before cudaMemcpyAsync returns, so the
-    // host buffer may be rewritten by the next call.
-    cudaError_t e = cudaMemcpyAsync(desc, g_host_desc, (size_t)n * kDescWords * sizeof(long long),
+    std::lock_guard<std::mutex> lock(g_mu);
+    // First call on this device: look up the array's device address (the device is current).
+    void *desc = scratch_address_locked(ctx->device);
+    lmfao::cart_descriptors(ctx, qids, n, g_host_desc);
+    cudaError_t e = cudaMemcpyAsync(desc, g_host_desc, (size_t)n * kDescWords * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       throw lmfao::Error(LMFAO_ERR_CUDA, std::string("descriptor copy failed: ") + cudaGetErrorString(e));
     }
-    lmfao::launch_cart_variances(P.icnt, P.fsum, (const int64_t *)desc, n, nb_max, out, s);
+    lmfao::launch_cart_variances(P.icnt, P.fsum, (const int64_t *)desc, n, nb, out, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) throw lmfao::Error(LMFAO_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
     return LMFAO_OK;

@@ -162,3 +162,16 @@ struct PhysPlan {
 };
 
 }  // namespace lmfao
+
+struct lmfao_ctx;
+namespace lmfao {
+// Words per CART query descriptor: icnt base, fsum base, buckets, aggregates, index of SUM(y),
+// index of SUM(y^2).
+constexpr int kCartDescWords = 6;
+// Checks the arguments of a CART split-variance call (Section 3, decision trees) against the
+// context's last run: every query id valid, one BUCKET group-by, exactly three aggregates that
+// are COUNT, SUM(y) and SUM(y^2) of one attribute y (in any order), and the same number of
+// buckets for all queries. Writes n descriptors of kCartDescWords words into desc (host, may
+// be null) and returns the bucket count. Throws Error(LMFAO_ERR_ARG / ERR_NOT_PLANNED).
+int cart_descriptors(const lmfao_ctx *ctx, const int *qids, int n, int64_t *desc);
+}  // namespace lmfao

@@ -24,7 +24,7 @@ HOST, DEVICE, ADOPT_DEVICE = 0, 1, 2
 FN_ID, FN_POW = 0, 1
 GB_VALUE, GB_BUCKET = 0, 1
 OPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3, "eq": 4, "ne": 5}
-PRECISION = {"fp64": 0, "fp32": 1, "split_tf32": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "split_bf16": 2}
 PLANNER = {"heuristic": 0, "exhaustive": 1, "learned": 2, "forced": 3}
 MODE = {"auto": 0, "factorised": 1, "per_tuple": 2, "generic": 3}
 ROLE = {"key": KEY, "cat": CAT, "cont": CONT}

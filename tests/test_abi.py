@@ -66,3 +66,21 @@ def test_create_on_missing_device_fails_cleanly():
     ctx = L.C.c_void_p()
     rc = lib.lmfao_create(L.C.byref(ctx), 4096)
     assert rc == L.ERR_CUDA and not ctx.value
+
+
+def test_options_without_an_implementation_are_refused():
+    """A precision or tuning request this build cannot honour is refused with
+    ERR_UNSUPPORTED (never silently replaced by another mode); unknown values are ERR_ARG."""
+    e = L.Engine(device=-1)
+    for R in W.star_schema(n_fact=100):
+        e.load_relation(R)
+    e.add_query({"aggs": [[]], "groupby": [], "filters": []})
+    e.plan(precision="fp32")
+    lib = L.library()
+    o = L.PlanOpts()
+    o.precision, o.planner, o.root_rel, o.segment_rel = 7, 0, -1, -2
+    info = L.PlanInfo()
+    assert lib.lmfao_plan(e.ctx, L.C.byref(o), L.C.byref(info)) == L.ERR_ARG
+    o.precision, o.planner = 1, 9
+    assert lib.lmfao_plan(e.ctx, L.C.byref(o), L.C.byref(info)) == L.ERR_ARG
+    e.close()

@@ -19,7 +19,8 @@ def test_reference_arm_prints_the_contract_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
-    assert line["config"]["fact_tuples"] == 84_000_000  # the GPU arm's workload; the sample is in cpu_baseline
+    # the config names the sample this arm evaluates per step (not the GPU arm's 84M tuples)
+    assert line["config"]["fact_tuples"] == 5000 and "5000 fact tuples" in line["config"]["workload"]
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
 
@@ -31,3 +32,27 @@ def test_traffic_from_the_committed_capture_scales_with_tuples():
     assert src and t40 > 40_000_000 * 8 and t84 - t40 == 44_000_000 * 8
     assert bench.measured_traffic("retailer", 84_000_000, {"generated": False}) == (None, None)
     assert bench.measured_traffic("favorita", 84_000_000, {"generated": True}) == (None, None)
+
+
+def test_parity_report_flags_errors_per_family():
+    """The bench's parity summary: exact counts, per-family relative error against the sum of
+    absolute terms, and a planted error in one aggregate shows up in its family only."""
+    import numpy as np
+    import bench
+    from oracle import lmfao_oracle as O
+    from paper_2008_08657_b300 import workloads as W
+    rels = W.star_schema(n_fact=3000, seed=1)
+    qs = W.star_batch()
+    ref = O.evaluate(rels, qs)
+    got = [{k: v.copy() for k, v in r.items()} for r in ref]
+    rep = bench.parity_report(qs, got, ref, 1.0, 2, 1)
+    assert rep["within_tolerance"] and rep["counts_exact"] and rep["max_rel_err"] == 0.0
+    j = next(j for j, a in enumerate(qs[0]["aggs"]) if len(a) == 2)
+    got[0]["sums"][0, j] += 1e-3 * ref[0]["abs"][0, j]
+    rep = bench.parity_report(qs, got, ref, 1.0, 2, 1)
+    assert not rep["within_tolerance"]
+    fam = bench._family(qs[0], qs[0]["aggs"][j])
+    assert abs(rep["families"][fam]["max_rel_err"] - 1e-3) < 1e-9
+    assert all(f["max_rel_err"] == 0.0 for n, f in rep["families"].items() if n != fam)
+    got[0]["counts"][0] += 1
+    assert not bench.parity_report(qs, got, ref, 1.0, 2, 1)["counts_exact"]

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import lmfao_oracle as O
 from paper_2008_08657_b300 import workloads as W
-from paper_2008_08657_b300.lmfao import Engine, LmfaoError, ERR_UNSUPPORTED
+from paper_2008_08657_b300.lmfao import ERR_ARG, ERR_UNSUPPORTED, Engine, LmfaoError
 from tests.parity import compare
 
 pytestmark = pytest.mark.gpu
@@ -169,6 +169,44 @@ def test_dt_level_and_cart_variances(n_fact, mode, codegen, monkeypatch):
         scale = np.abs(ref[qi]["abs"][:, 2]).sum() + 1.0
         assert np.abs(L - left).max() <= 1e-5 * scale
         assert np.abs(R_ - right).max() <= 1e-5 * scale
+    e.close()
+
+
+def test_cart_variances_check_and_map_their_aggregates():
+    """lmfao_cart_variances needs COUNT, SUM(y), SUM(y^2) of one attribute: the three in any
+    order give the same variances; other aggregates are refused with ERR_ARG."""
+    import torch
+    rels = W.retailer_schema(n_fact=50_000, seed=2)
+    ycol, x = "y", "i1"
+    item = next(R for R in rels if R["name"] == "Item")
+    xthr = [float(v) for v in np.quantile(next(c["data"] for c in item["columns"] if c["attr"] == x),
+                                          [0.25, 0.5, 0.75])]
+    gb = [(x, "bucket", xthr)]
+    canon = {"aggs": [[], [(ycol, "id", 1)], [(ycol, "pow", 2)]], "groupby": gb, "filters": []}
+    perm = {"aggs": [[(ycol, "id", 1), (ycol, "id", 1)], [], [(ycol, "id", 1)]], "groupby": gb, "filters": []}
+    other = {"aggs": [[], [(x, "id", 1)], [(ycol, "pow", 2)]], "groupby": gb, "filters": []}
+    four = {"aggs": [[], [(ycol, "id", 1)], [(ycol, "pow", 2)], []], "groupby": gb, "filters": []}
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_queries([canon, perm, other, four])
+    e.plan(precision="fp32")
+    e.run()
+    ref = O.evaluate(rels, [canon])[0]
+    left, right = O.cart_variances(ref)
+    out = torch.zeros((2, len(xthr), 2), dtype=torch.float64, device="cuda")
+    e.cart_variances([0, 1], out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    scale = np.abs(ref["abs"][:, 2]).sum() + 1.0
+    for k in range(2):
+        assert np.abs(got[k, :len(left), 0] - left).max() <= 1e-5 * scale
+        assert np.abs(got[k, :len(right), 1] - right).max() <= 1e-5 * scale
+    for bad in (2, 3):
+        for call in (e.cart_variances, e.cart_variances_noalloc):
+            with pytest.raises(LmfaoError) as ei:
+                call([0, bad], out)
+            assert ei.value.code == ERR_ARG
     e.close()
 
 

@@ -219,15 +219,16 @@ def test_join_order_does_not_matter():
             np.testing.assert_allclose(ra["sums"], rb["sums"], rtol=1e-12, atol=1e-12)
 
 
-def test_oracle_against_factorised_views_favorita():
-    """Q1-Q3 of Section 2 by the view decomposition of Fig. 2 and the loop nest of Fig. 3.
+def test_oracle_against_views_of_section_2_favorita():
+    """Q1-Q3 of Section 2 computed from directional views along the join tree of Fig. 2
+    instead of the materialised join.
 
-    Views (join tree of Fig. 2, child -> parent): V_R->T(store) and V_O->T(date) feed
-    V_T->S(date, store) = [count, SUM(price)]; V_H->S(date) and V_I->S(item) are counts.
-    Q1 = SUM(units) and Q2 = SUM(item * date) GROUP BY store are computed at Sales by
-    iterating its tuples grouped by item, then date, then store, looking up each incoming
-    view once per key value; V_S->I(item) = SUM over the rest of the join of
-    [units, units * price] feeds Q3 = SUM(units * price) GROUP BY class at Items.
+    A view from relation X toward its neighbour Y is the aggregate over the part of the join
+    on X's side of the edge, grouped by the attributes X shares with Y (Section 2, views);
+    here each one is a numpy group-by sum over X's tuples weighted by the views into X.
+    Q1 and Q2 (rooted at Sales) weight every Sales tuple by the product of the views into
+    Sales; Q3 (rooted at Items) groups by class the view from Sales to Items, which carries
+    SUM(units * price) over everything on the Sales side of that edge.
     """
     rels = W.favorita_schema(n_fact=3000, seed=4)
     S, T, R, Oi, H, I = rels
@@ -238,50 +239,47 @@ def test_oracle_against_factorised_views_favorita():
         return {c["attr"]: c["data"] for c in X["columns"]}
 
     s, t, r, o, h, it = map(cols, (S, T, R, Oi, H, I))
-    # leaf views
-    V_RT = np.bincount(r["store"], minlength=W.N_STORE).astype(float)
-    V_OT_cnt = np.bincount(o["date"], minlength=W.N_FDATE).astype(float)
-    V_OT_price = np.bincount(o["date"], weights=o["price"].astype(float), minlength=W.N_FDATE)
-    V_HS = np.bincount(h["date"], minlength=W.N_FDATE).astype(float)
-    V_IS = np.bincount(it["item"], minlength=W.N_FITEM).astype(float)
-    # V_T->S(date, store) over T joined with its incoming views
-    V_TS = {}
-    for d, st in zip(t["date"], t["store"]):
-        c, p = V_TS.get((int(d), int(st)), (0.0, 0.0))
-        w = V_RT[st]
-        V_TS[(int(d), int(st))] = (c + w * V_OT_cnt[d], p + w * V_OT_price[d])
-    # Group 6 at Sales: trie order item -> date -> store
-    order = np.lexsort((s["store"], s["date"], s["item"]))
-    Q1 = 0.0
-    Q2 = {}
-    V_SI = {}
-    i_prev = None
-    for k in order:
-        i, d, st, u = int(s["item"][k]), int(s["date"][k]), int(s["store"][k]), float(s["units"][k])
-        a1 = V_IS[i]
-        a3 = V_HS[d]
-        a5c, a5p = V_TS.get((d, st), (0.0, 0.0))
-        Q1 += u * a1 * a3 * a5c
-        if a1 * a3 * a5c:
-            Q2[st] = Q2.get(st, 0.0) + i * d * a1 * a3 * a5c
-        b = V_SI.get(i, (0.0, 0.0))
-        V_SI[i] = (b[0] + u * a3 * a5c, b[1] + u * a3 * a5p)
-        i_prev = i
-    # Group 7 at Items: Q3(class) = SUM over items of V_S->I[units*price]
-    Q3 = {}
-    for i, cl in zip(it["item"], it["class"]):
-        if int(i) in V_SI and V_SI[int(i)][0] != 0:
-            Q3[int(cl)] = Q3.get(int(cl), 0.0) + V_SI[int(i)][1]
-    assert i_prev is not None
+    nd, ns, ni = W.N_FDATE, W.N_STORE, W.N_FITEM
+    # views toward Transactions: StoRes by store (COUNT), Oil by date (COUNT, SUM(price))
+    r_cnt = np.bincount(r["store"], minlength=ns).astype(float)
+    o_cnt = np.bincount(o["date"], minlength=nd).astype(float)
+    o_price = np.bincount(o["date"], weights=o["price"].astype(float), minlength=nd)
+    # view Transactions -> Sales by (date, store): COUNT and SUM(price) over T, R, O
+    tkey = t["date"].astype(np.int64) * ns + t["store"]
+    tw = r_cnt[t["store"]]
+    t_cnt = np.bincount(tkey, weights=tw * o_cnt[t["date"]], minlength=nd * ns)
+    t_price = np.bincount(tkey, weights=tw * o_price[t["date"]], minlength=nd * ns)
+    # views Holidays -> Sales by date and Items -> Sales by item (COUNT)
+    h_cnt = np.bincount(h["date"], minlength=nd).astype(float)
+    i_cnt = np.bincount(it["item"], minlength=ni).astype(float)
+    # at Sales: every Sales tuple occurs (product of the COUNT views into Sales) times in D
+    skey = s["date"].astype(np.int64) * ns + s["store"]
+    units = s["units"].astype(float)
+    mult = i_cnt[s["item"]] * h_cnt[s["date"]] * t_cnt[skey]
+    Q1 = float((units * mult).sum())
+    gdate = s["item"].astype(float) * s["date"].astype(float)
+    q2_cnt = np.bincount(s["store"], weights=mult, minlength=ns)
+    q2_sum = np.bincount(s["store"], weights=gdate * mult, minlength=ns)
+    # view Sales -> Items by item: COUNT and SUM(units * price) over Sales, T, R, O, H
+    side = h_cnt[s["date"]]
+    si_cnt = np.bincount(s["item"], weights=side * t_cnt[skey], minlength=ni)
+    si_up = np.bincount(s["item"], weights=units * side * t_price[skey], minlength=ni)
+    # at Items: Q3 GROUP BY class
+    q3_cnt = np.bincount(it["class"], weights=si_cnt[it["item"]], minlength=337)
+    q3_sum = np.bincount(it["class"], weights=si_up[it["item"]], minlength=337)
+
     assert abs(res[0]["sums"][0, 0] - Q1) <= 1e-9 * res[0]["abs"][0, 0]
+    assert res[0]["counts"][0] == int(round(mult.sum()))
     keys2 = [int(k[0]) for k in res[1]["keys"]]
-    assert keys2 == sorted(Q2)
+    assert keys2 == [int(k) for k in np.nonzero(q2_cnt)[0]]
     for g, k in enumerate(keys2):
-        assert abs(res[1]["sums"][g, 0] - Q2[k]) <= 1e-9 * max(1.0, res[1]["abs"][g, 0])
+        assert res[1]["counts"][g] == int(round(q2_cnt[k]))
+        assert abs(res[1]["sums"][g, 0] - q2_sum[k]) <= 1e-9 * max(1.0, res[1]["abs"][g, 0])
     keys3 = [int(k[0]) for k in res[2]["keys"]]
-    assert set(keys3) <= set(Q3)
+    assert keys3 == [int(k) for k in np.nonzero(q3_cnt)[0]]
     for g, k in enumerate(keys3):
-        assert abs(res[2]["sums"][g, 0] - Q3[k]) <= 1e-9 * max(1.0, res[2]["abs"][g, 0])
+        assert res[2]["counts"][g] == int(round(q3_cnt[k]))
+        assert abs(res[2]["sums"][g, 0] - q3_sum[k]) <= 1e-9 * max(1.0, res[2]["abs"][g, 0])
 
 
 def test_planted_mistake_is_caught():
@@ -295,3 +293,32 @@ def test_planted_mistake_is_caught():
     assert_matches_brute(good, bf)
     with pytest.raises(AssertionError):
         assert_matches_brute(bad, bf)
+
+
+@pytest.mark.parametrize("processes", [1, 3])
+def test_chunked_evaluation_equals_the_whole_join(processes):
+    """The join distributes over a partition of the fact relation: the chunked evaluation
+    (chunks summed in order, optionally over spawned processes) gives the same groups and
+    counts as the unchunked one, and sums equal up to rounding order; chunks that contribute
+    nothing to a group, empty chunks and a ragged last chunk are covered."""
+    rels = W.star_schema(n_fact=5003, seed=3)
+    qs = W.star_batch() + [{"aggs": [[], [("y", "id", 1)]], "groupby": [("c1", "value", None)],
+                            "filters": [("y", "gt", 1.5)]}]
+    whole = O.evaluate(rels, qs)
+    got, secs = O.evaluate_chunked(rels, qs, root=0, processes=processes, chunk=1000)
+    assert secs >= 0
+    for a, b in zip(got, whole):
+        np.testing.assert_array_equal(a["keys"], b["keys"])
+        np.testing.assert_array_equal(a["counts"], b["counts"])
+        np.testing.assert_allclose(a["sums"], b["sums"], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(a["abs"], b["abs"], rtol=1e-12, atol=1e-12)
+    # the tiny brute-force schemas (duplicate and dangling keys) split into 4-row chunks
+    for seed in range(6):
+        rels = W.tiny_schema(seed, empty_ok=False)
+        qs = W.tiny_queries(seed, rels, nq=3)
+        whole = O.evaluate(rels, qs)
+        got, _ = O.evaluate_chunked(rels, qs, root=0, processes=1, chunk=4)
+        for a, b in zip(got, whole):
+            np.testing.assert_array_equal(a["keys"], b["keys"])
+            np.testing.assert_array_equal(a["counts"], b["counts"])
+            np.testing.assert_allclose(a["sums"], b["sums"], rtol=1e-12, atol=1e-12)

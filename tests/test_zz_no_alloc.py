@@ -1,5 +1,6 @@
 """The allocation-free CART entry point (lmfao_cart_variances_noalloc) returns what the
-allocating one (lmfao_cart_variances) returns, on two calls in a row.
+allocating one (lmfao_cart_variances) returns, on two calls in a row (the second on a
+stream of its own), and the device's free memory does not change during those calls.
 
 Callers that cannot allocate device memory when they evaluate splits (a fixed device
 budget owned by their framework's caching allocator, or a loop that must avoid the
@@ -34,10 +35,21 @@ def test_noalloc_cart_variances_match_allocating_entry_point():
     e.cart_variances(ids, ref)
     torch.cuda.synchronize()
     ref = ref.cpu().numpy()
+    outs = [torch.full((len(ids), nb - 1, 2), float("nan"), dtype=torch.float64, device="cuda") for _ in range(3)]
+    side = torch.cuda.Stream()
+    e.cart_variances_noalloc(ids, outs[2])  # first call on the device: looks up the array's address
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     for call, order in enumerate((ids, ids[::-1])):
-        out = torch.full((len(order), nb - 1, 2), float("nan"), dtype=torch.float64, device="cuda")
-        e.cart_variances_noalloc(order, out)
+        out = outs[call]
+        if call == 1:  # the second call on a stream of its own
+            side.wait_stream(torch.cuda.current_stream())
+            e.cart_variances_noalloc(order, out, stream=side)
+            side.synchronize()
+        else:
+            e.cart_variances_noalloc(order, out)
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, "device memory changed during the call"
         got = out.cpu().numpy()
         want = ref if call == 0 else ref[::-1]
         np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL, err_msg=f"call {call}")
