@@ -29,6 +29,14 @@ METRIC = "fact tuples/s per aggregate batch"
 UNIT = "tuples/s"
 
 
+def tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1800.0
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -58,23 +66,24 @@ def workload(n_fact, seed=0, which="retailer"):
     return rels, W.retailer_batch()
 
 
-def measured_traffic(workload_name, n_fact, root_pass):
-    """DRAM bytes per root-pass launch from the committed ncu summary of the same kernel, scaled
-    from the captured fact size to n_fact by the per-tuple column bytes (the per-segment parts
-    do not change with the fact size). None when no capture of this kernel and workload exists."""
-    path = os.path.join(ROOT, "profiles", "root_pass_retailer_40m.md")
-    if not root_pass or not root_pass.get("generated") or not os.path.exists(path):
-        return None, None
-    with open(path) as f:
-        for line in f:
-            if not line.startswith("traffic:"):
-                continue
-            kv = dict(x.split("=", 1) for x in line.split()[1:])
-            if kv.get("kernel") != "lmfao_gen_root_pass" or kv.get("workload") != workload_name:
-                return None, None
-            t = int(kv["read"]) + int(kv["write"]) + (n_fact - int(kv["tuples"])) * int(kv["bytes_per_tuple"])
-            return t, f"ncu capture at {kv['tuples']} fact tuples ({os.path.basename(path)}), scaled by tuples"
-    return None, None
+def measured_traffic(n_fact, root_pass):
+    """DRAM bytes per root-pass launch from the committed capture of the same generated kernel
+    (profiles/traffic.json, keyed by the hash of the kernel's source text), scaled from the
+    captured fact size to n_fact by the per-tuple column bytes (the per-segment parts do not
+    change with the fact size). (None, reason) when no capture of this exact kernel exists."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not root_pass or not root_pass.get("generated"):
+        return None, "root pass not generated"
+    try:
+        with open(path) as f:
+            caps = json.load(f)
+    except (OSError, ValueError):
+        return None, "no committed capture"
+    for c in caps:
+        if c.get("kernel") == "lmfao_gen_root_pass" and c.get("source_hash") == root_pass.get("source_hash"):
+            t = c["read"] + c["write"] + (n_fact - c["tuples"]) * c["bytes_per_tuple"]
+            return t, f"ncu capture of this kernel at {c['tuples']} fact tuples (profiles/traffic.json), scaled by tuples"
+    return None, "kernel changed since the last capture (no capture of this source hash)"
 
 
 def workload_config(args, n_fact, qs):
@@ -216,20 +225,35 @@ def bench_lmfao(args):
     roofline = {"bound": "hbm", "kernel": "fact_pass", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_kind,
                 "algorithmic_bytes": fbytes, "kernel_ms": fms, "traffic": None}
-    traffic, tsrc = measured_traffic(args.workload, n_fact, desc["physical"].get("root_pass"))
-    if traffic is not None:
-        roofline["traffic"] = traffic
-        roofline["traffic_source"] = tsrc
+    traffic, tsrc = measured_traffic(n_fact, desc["physical"].get("root_pass"))
+    roofline["traffic"] = traffic
+    roofline["traffic_source"] = tsrc
+    # the per-block contraction kernel of the combine, against HBM and against the tensor pipe
+    comb = None
+    czb, czf = desc["physical"].get("combine_z_bytes", 0), desc["physical"].get("combine_z_flops", 0)
+    if czb and kernel_ms.get("combine_z"):
+        t = kernel_ms["combine_z"] / 1e3
+        comb = {"kernel": "combine_z", "contraction": desc["physical"].get("contraction"),
+                "bound": "hbm", "algorithmic_bytes": czb, "achieved": czb / t / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": czb / t / 1e9 / peak, "flops": czf, "tflops": czf / t / 1e12,
+                "kernel_ms": kernel_ms["combine_z"], "chunk": desc["physical"].get("combine_chunk")}
+        if args.precision == "split_bf16":
+            tp = tensor_peak()
+            comb["tensor_frac"] = czf / t / 1e12 / tp if tp else None
+            comb["tensor_peak_tflops"] = tp
     # end to end through the C ABI: pinned host -> device copies, load, plan, run, fetch
     got = eng.fetch_all() if rank == 0 and args.parity else None
+    eng.close()
     e2e = None
+    batches = None
     if not args.skip_e2e:
         e2e = bench_e2e(args, rels, qs, torch, local)
-    eng.close()
+        batches = bench_batches(args, rels, qs, torch, local)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "split_bf16": "f32 (dense contraction as split bf16 x3)"}[args.precision],
         "data": f"synthetic (seeded, {args.workload}-shaped)",
         "config": {**workload_config(args, n_fact, qs), "precision": args.precision,
                    "l2": "inputs larger than L2 (no flush)",
@@ -240,6 +264,9 @@ def bench_lmfao(args):
         "vs_plain_fp64_gpu": (fp64_ms / ms_step) if fp64_ms else None,
         "plain_fp64_ms_per_step": fp64_ms,
         "plan_ms": info["plan_ms"],
+        "reorg_ms": info["reorg_ms"],
+        "batches_from_resident_data": batches,
+        "combine_roofline": comb,
         "kernel_ms": kernel_ms,
         "root_pass_shape": desc["physical"].get("root_pass"),
         "combine_shape": {k: desc["physical"].get(k) for k in
@@ -304,6 +331,33 @@ def bench_e2e(args, rels, qs, torch, local):
             "d2h_bytes_per_step": int(d2h), "seconds_per_step": s,
             "includes": "pinned H2D of all relations, lmfao_load_relation, lmfao_plan (trie reorganisation), "
                         "lmfao_run, lmfao_fetch of every query"}
+
+
+def bench_batches(args, rels, qs, torch, local):
+    """Plan + run + fetch of a batch from relations already resident in HBM: the first batch on
+    a new context (reorganises the root relation; the generated kernel is already compiled in
+    this process) and a second batch on the same context (reuses the segment order)."""
+    from paper_2008_08657_b300.lmfao import Engine
+    dev = [[torch.from_numpy(np.ascontiguousarray(c["data"])).cuda() for c in R["columns"]] for R in rels]
+    torch.cuda.synchronize()
+    eng = Engine(local)
+    for R, cols in zip(rels, dev):
+        eng.load_relation(dict(R, columns=[dict(c, data=d) for c, d in zip(R["columns"], cols)]), where="device")
+    out = {}
+    for name in ("first", "second"):
+        if name == "second":
+            eng.clear_batch()
+        eng.add_queries(qs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = eng.plan(precision=args.precision)
+        eng.run()
+        eng.fetch_all()
+        out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "reorg_ms": info["reorg_ms"],
+                     "reorg_reused": bool(info["reorg_reused"]), "plan_ms": info["plan_ms"]}
+    eng.close()
+    del dev
+    return out
 
 
 def cpu_baseline(args, sample_rows=300_000):
@@ -410,7 +464,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lmfao", choices=["lmfao", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "split_bf16"])
     ap.add_argument("--workload", default="retailer", choices=sorted(WORKLOADS))
     ap.add_argument("--fact-rows", type=int, default=None)
     ap.add_argument("--ref-rows", type=int, default=200_000)

@@ -152,6 +152,10 @@ typedef struct lmfao_plan_info {
   int32_t mode;              /* mode chosen                                              */
   double predicted_ms;       /* planner's time estimate (-1 if none)                     */
   double plan_ms;            /* host+device time spent planning (incl. reorganisation)   */
+  double reorg_ms;           /* of which: reorganising the root relation into segment order
+                                (the context keeps that order per root relation and segment
+                                key, so a later plan over the same relations reuses it)   */
+  int32_t reorg_reused;      /* 1: the segment order of an earlier plan was reused       */
 } lmfao_plan_info;
 
 /* ---- results ------------------------------------------------------------------------ */
@@ -206,9 +210,13 @@ LMFAO_API int lmfao_clear_batch(struct lmfao_ctx *ctx);
  * For a root relation of at least 2^20 tuples the root pass is generated for the batch
  * and compiled with NVRTC (Fig. 1's code generation; about 0.3 s per new shape, cached
  * for the life of the process; a shape outside the generators uses the built-in kernel).
+ * A group-by attribute of a non-root relation must be determined by the key of that
+ * relation's view toward the root; this is checked on the loaded data while planning. The
+ * heuristic planner then moves the root (largest relations first) and a forced root that
+ * fails gives LMFAO_ERR_UNSUPPORTED.
  * Environment: LMFAO_CODEGEN=0 never generates, =1 generates at any size;
  * LMFAO_NO_PROJECTION_COMBINE selects the entry-wise combine where the projection
- * combine would run. */
+ * combine would run; LMFAO_COMBINE=single keeps the single-kernel block combine. */
 LMFAO_API int lmfao_plan(struct lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *info);
 
 /* Candidate physical plans of the current batch (root relation, segment relation, root
@@ -268,8 +276,37 @@ LMFAO_API int lmfao_describe_plan(struct lmfao_ctx *ctx, char *buf, size_t len, 
  * written as y^2 or y * y); anything else gives LMFAO_ERR_ARG. For every threshold
  * k < B - 1 the left fragment is buckets 0..k and the right the rest; VARIANCE(T) =
  * SUM(y^2) - SUM(y)^2 / |T| (0 if T is empty). `out` (device, n x (B-1) x 2 doubles:
- * left, right) is written asynchronously on `stream`. */
+ * left, right) is written asynchronously on `stream`. Waits for the last run and returns
+ * the status lmfao_fetch would give for its device-side failures. */
 LMFAO_API int lmfao_cart_variances(struct lmfao_ctx *ctx, const int *qids, int n, double *out, void *stream);
+
+/* One node of a regression tree grown by lmfao_cart_tree (nodes in heap order: the children
+ * of node i are 2i + 1 (left, x <= threshold) and 2i + 2 (right, x > threshold)). */
+typedef struct lmfao_cart_node {
+  int32_t active;      /* 1: the node was evaluated (every ancestor split)                   */
+  int32_t feature;     /* index into features[] of the chosen split, -1: no valid split     */
+  float threshold;     /* the split: left x <= threshold, right x > threshold               */
+  double score;        /* VARIANCE(left) + VARIANCE(right) of the chosen split             */
+  int64_t count;       /* tuples of the join that reach the node                            */
+  double sum_y, sum_y2;  /* SUM(y), SUM(y^2) over those tuples                              */
+} lmfao_cart_node;
+
+/* Grow a regression tree (Section 3, decision trees) over the natural join of the loaded
+ * relations: levels 0 .. depth-1, every node of a level evaluated in one batch (one query
+ * per node and feature: COUNT, SUM(y), SUM(y^2) GROUP BY the feature's bucket, filtered by
+ * the node's path of split predicates), one plan and run per level (the reorganised root
+ * relation is reused across levels) and the best split of every node chosen on the device:
+ * the least VARIANCE(left) + VARIANCE(right) over the features' thresholds with both sides
+ * non-empty, ties to the lower feature index, then the lower threshold. `target` is a CONT
+ * attribute (y); `features` (host, nfeatures names) CONT attributes; `thresholds` (host)
+ * their ascending thresholds concatenated, nthresholds[f] of them for feature f (at most 31
+ * per feature); depth in [1, 5]. opts as for lmfao_plan (NULL: FP32, heuristic). nodes
+ * (host, 2^depth - 1 entries) receives the tree; level_ms (host, depth x 2 doubles or NULL)
+ * the host time of planning and of the run plus split selection per level. The context's
+ * batch is replaced (cleared on return); relations stay loaded. */
+LMFAO_API int lmfao_cart_tree(struct lmfao_ctx *ctx, const char *target, const char *const *features, int nfeatures,
+                              const float *thresholds, const int32_t *nthresholds, int depth,
+                              const lmfao_plan_opts *opts, lmfao_cart_node *nodes, double *level_ms);
 
 /* Allocation-free variant of lmfao_cart_variances (same arguments, same results), for
  * callers that cannot allocate device memory when they ask for split variances: a host

@@ -329,3 +329,82 @@ def evaluate_chunked(rels, queries, root=0, processes=1, chunk=CHUNK):
             shm.close()
             shm.unlink()
     return merge_results(queries, parts), time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------------------------------
+# Regression tree (Section 3, decision trees): the splits a CART learner chooses from the
+# VARIANCE aggregates of every node, level by level.
+# ---------------------------------------------------------------------------------------
+
+def _tree_level_queries(target, features, thresholds, paths):
+    qs = []
+    for path in paths:
+        for f in features:
+            qs.append({"aggs": [[], [(target, "id", 1)], [(target, "pow", 2)]],
+                       "groupby": [(f, "bucket", list(thresholds[f]))], "filters": list(path)})
+    return qs
+
+
+def best_split(results, nbuckets):
+    """The split of one node from its per-feature bucketed (COUNT, SUM(y), SUM(y^2)) results:
+    for feature f and threshold k (left = buckets 0..k, right = the rest), both sides
+    non-empty, score = VARIANCE(left) + VARIANCE(right) with VARIANCE(T) = SUM(y^2) -
+    SUM(y)^2 / |T|; the least score, ties to the lower feature, then the lower threshold.
+    Returns (feature, k, score) or None."""
+    best = None
+    for f, (r, nb) in enumerate(zip(results, nbuckets)):
+        n = np.zeros(nb)
+        s = np.zeros(nb)
+        s2 = np.zeros(nb)
+        if len(r["keys"]):
+            k = r["keys"][:, 0]
+            n[k] = r["counts"]
+            s[k] = r["sums"][:, 1]
+            s2[k] = r["sums"][:, 2]
+        tn, ts, ts2 = n.sum(), s.sum(), s2.sum()
+        cn = cs = cs2 = 0.0
+        for k in range(nb - 1):
+            cn += n[k]
+            cs += s[k]
+            cs2 += s2[k]
+            rn = tn - cn
+            if cn <= 0 or rn <= 0:
+                continue
+            sc = (cs2 - cs * cs / cn) + ((ts2 - cs2) - (ts - cs) ** 2 / rn)
+            if best is None or sc < best[2]:
+                best = (f, k, sc)
+    return best
+
+
+def cart_tree(rels, target, features, thresholds, depth, processes=1):
+    """Grow the tree of depth ``depth`` (levels 0 .. depth-1 choose splits) over the natural
+    join of ``rels`` with the batches of ``_tree_level_queries`` evaluated by the oracle
+    (whole-join evaluation, chunked over ``processes``). Nodes in heap order: dicts with
+    active, feature (-1: no valid split), threshold, score, count, sum_y, sum_y2."""
+    nn = (1 << depth) - 1
+    nodes = [{"active": 0, "feature": -1, "threshold": 0.0, "score": 0.0, "count": 0, "sum_y": 0.0, "sum_y2": 0.0}
+             for _ in range(nn)]
+    paths = [[] for _ in range(nn)]
+    nodes[0]["active"] = 1
+    nb = [len(thresholds[f]) + 1 for f in features]
+    for lev in range(depth):
+        act = [v for v in range((1 << lev) - 1, (1 << (lev + 1)) - 1) if nodes[v]["active"]]
+        if not act:
+            continue
+        qs = _tree_level_queries(target, features, thresholds, [paths[v] for v in act])
+        res, _ = evaluate_chunked(rels, qs, root=0, processes=processes)
+        for i, v in enumerate(act):
+            rs = res[i * len(features):(i + 1) * len(features)]
+            cnt = sum(int(x) for x in rs[0]["counts"])
+            nodes[v].update(count=cnt, sum_y=float(rs[0]["sums"][:, 1].sum()), sum_y2=float(rs[0]["sums"][:, 2].sum()))
+            b = best_split(rs, nb)
+            if b is None:
+                continue
+            f, k, sc = b
+            t = float(np.float32(thresholds[features[f]][k]))
+            nodes[v].update(feature=f, threshold=t, score=float(sc))
+            if 2 * v + 2 < nn:
+                for c, op in ((1, "le"), (2, "gt")):
+                    paths[2 * v + c] = paths[v] + [(features[f], op, t)]
+                    nodes[2 * v + c]["active"] = 1
+    return nodes

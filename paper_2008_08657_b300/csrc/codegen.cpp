@@ -17,6 +17,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <map>
 #include <mutex>
 #include <sstream>
@@ -409,7 +410,19 @@ bool eligible(const DFast &d, std::string &why) {
 namespace {
 
 // compile (or take from the cache) and check one generated source
+std::string fnv1a_hex(const std::string &text) {
+  unsigned long long h = 1469598103934665603ull;
+  for (unsigned char ch : text) {
+    h ^= ch;
+    h *= 1099511628211ull;
+  }
+  char buf[17];
+  snprintf(buf, sizeof buf, "%016llx", h);
+  return buf;
+}
+
 bool finish(GenRootPass &g, const std::string &src, int block, size_t smem) {
+  g.source_hash = fnv1a_hex(src);
   Compiled c;
   {
     std::lock_guard<std::mutex> lk(cache_mu);

@@ -21,6 +21,7 @@ struct GenRootPass {
   size_t smem = 0;
   bool family = false;       // generated from the general shape (codegen_family.cpp)
   std::string why;           // why the kernel was not generated (empty when it was)
+  std::string source_hash;   // FNV-1a (64-bit, hex) of the generated source: names the exact kernel
 };
 
 // Generate (or take from the cache) the kernel for the specialised root pass described by d:

@@ -3,6 +3,17 @@
 
 #include "plan.h"
 
+// The root relation reorganised into segment order for one segment key, kept across plans so
+// that a new batch over the same relations (every level of a decision tree, for instance) does
+// not sort the root relation again. Owned by the context.
+struct lmfao_reorg {
+  int root = -1;
+  std::vector<int> segcols;
+  std::vector<int64_t> hist;        // tuples per segment
+  unsigned int *dest = nullptr;     // device: row -> position in segment order
+  std::map<int, void *> cols;       // root column -> device copy in segment order (+16 bytes)
+};
+
 struct lmfao_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;  // internal stream for loading and planning
@@ -23,4 +34,5 @@ struct lmfao_ctx {
   std::vector<cudaEvent_t> events;
   std::vector<std::string> ev_names;
   std::vector<std::string> kernel_names;
+  std::vector<lmfao_reorg> reorg;   // reorganised root relations (see lmfao_reorg)
 };

@@ -1278,47 +1278,80 @@ void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   cudaStream_t s = ctx->stream;
   const Relation &F = ctx->rels[t.root];
   const int64_t n = F.nrows;
-  // reorganised copies of the root columns read per tuple
+  const auto t0 = std::chrono::steady_clock::now();
+  // reorganised copies of the root columns read per tuple, cached per (root, segment key)
   std::vector<int64_t> hist(P.nseg, 0);
   P.rowdev.clear();
+  P.reorg_cached = false;
   if (P.segrel >= 0 && n > 0) {
-    std::vector<DCol> kc;
-    std::vector<int64_t> radix(P.segcols.size());
-    int64_t acc = 1;
-    for (int i = (int)P.segcols.size() - 1; i >= 0; --i) { radix[i] = acc; acc *= P.segdom[i]; }
-    for (int c : P.segcols) kc.push_back(dcol(F.cols[c]));
-    int *segid = (int *)P.arena.alloc(n * 4);
-    unsigned int *h = (unsigned int *)P.arena.alloc(P.nseg * 4);
-    LMFAO_CUDA(cudaMemsetAsync(h, 0, P.nseg * 4, s));
-    if (kc.size() > 4) throw Error(LMFAO_ERR_UNSUPPORTED, "segment key with more than 4 attributes");
-    launch_segment_ids(kc.data(), (int)kc.size(), radix.data(), n, segid, s);
-    launch_histogram(segid, n, h, s);
-    std::vector<unsigned int> hh(P.nseg);
-    LMFAO_CUDA(cudaMemcpyAsync(hh.data(), h, P.nseg * 4, cudaMemcpyDeviceToHost, s));
-    LMFAO_CUDA(cudaStreamSynchronize(s));
-    std::vector<unsigned long long> begin(P.nseg);
-    unsigned long long run = 0;
-    for (int64_t i = 0; i < P.nseg; ++i) { begin[i] = run; run += hh[i]; hist[i] = hh[i]; }
-    unsigned long long *cursor = P.arena.upload(begin, s);
-    std::vector<DCol> in, out;
-    std::vector<int> esz;
-    for (int c : P.rowcols) {
-      const Column &col = F.cols[c];
-      int e = col.dtype == LMFAO_U8 ? 1 : 4;
-      void *p = P.arena.alloc(n * e + 16);  // padded: 4-tuple vector loads may read past the end
-      in.push_back(dcol(col));
-      out.push_back(DCol{p, col.dtype});
-      esz.push_back(e);
+    if (n >= (int64_t(1) << 32)) throw Error(LMFAO_ERR_UNSUPPORTED, "root relation of 2^32 tuples or more");
+    lmfao_reorg *E = nullptr;
+    for (auto &e : ctx->reorg)
+      if (e.root == t.root && e.segcols == P.segcols) E = &e;
+    std::vector<int> missing;
+    for (int c : P.rowcols)
+      if (!E || !E->cols.count(c)) missing.push_back(c);
+    auto out_cols = [&](std::vector<DCol> &in, std::vector<DCol> &out, std::vector<int> &esz, lmfao_reorg &R) {
+      for (int c : missing) {
+        const Column &col = F.cols[c];
+        const int e = col.dtype == LMFAO_U8 ? 1 : 4;
+        void *p = nullptr;
+        LMFAO_CUDA(cudaMalloc(&p, n * e + 16));  // padded: 4-tuple vector loads may read past the end
+        LMFAO_CUDA(cudaMemsetAsync(p, 0, n * e + 16, s));
+        R.cols[c] = p;
+        in.push_back(dcol(col));
+        out.push_back(DCol{p, col.dtype});
+        esz.push_back(e);
+      }
+    };
+    if (!E) {
+      std::vector<DCol> kc;
+      std::vector<int64_t> radix(P.segcols.size());
+      int64_t acc = 1;
+      for (int i = (int)P.segcols.size() - 1; i >= 0; --i) { radix[i] = acc; acc *= P.segdom[i]; }
+      for (int c : P.segcols) kc.push_back(dcol(F.cols[c]));
+      if (kc.size() > 4) throw Error(LMFAO_ERR_UNSUPPORTED, "segment key with more than 4 attributes");
+      ctx->reorg.emplace_back();
+      E = &ctx->reorg.back();
+      E->root = t.root;
+      E->segcols = P.segcols;
+      LMFAO_CUDA(cudaMalloc((void **)&E->dest, n * 4));
+      int *segid = (int *)P.arena.alloc(n * 4);
+      unsigned int *h = (unsigned int *)P.arena.alloc(P.nseg * 4);
+      LMFAO_CUDA(cudaMemsetAsync(h, 0, P.nseg * 4, s));
+      launch_segment_ids(kc.data(), (int)kc.size(), radix.data(), n, segid, s);
+      launch_histogram(segid, n, h, s);
+      std::vector<unsigned int> hh(P.nseg);
+      LMFAO_CUDA(cudaMemcpyAsync(hh.data(), h, P.nseg * 4, cudaMemcpyDeviceToHost, s));
+      LMFAO_CUDA(cudaStreamSynchronize(s));
+      std::vector<unsigned long long> begin(P.nseg);
+      unsigned long long run = 0;
+      E->hist.assign(P.nseg, 0);
+      for (int64_t i = 0; i < P.nseg; ++i) { begin[i] = run; run += hh[i]; E->hist[i] = hh[i]; }
+      unsigned long long *cursor = P.arena.upload(begin, s);
+      std::vector<DCol> in, out;
+      std::vector<int> esz;
+      out_cols(in, out, esz, *E);
+      // one pass assigns every row its position (kept for later columns) and moves the columns
+      launch_scatter_rows(segid, n, cursor, in.data(), out.data(), esz.data(), (int)in.size(), E->dest, s);
+      LMFAO_CUDA(cudaStreamSynchronize(s));
+      cudaFree(segid);
+      P.arena.ptrs.erase(std::find(P.arena.ptrs.begin(), P.arena.ptrs.end(), (void *)segid));
+    } else {
+      P.reorg_cached = missing.empty();
+      std::vector<DCol> in, out;
+      std::vector<int> esz;
+      out_cols(in, out, esz, *E);
+      launch_permute_rows(E->dest, n, in.data(), out.data(), esz.data(), (int)in.size(), s);
+      LMFAO_CUDA(cudaStreamSynchronize(s));
     }
-    if (!in.empty()) launch_scatter_rows(segid, n, cursor, in.data(), out.data(), esz.data(), (int)in.size(), s);
-    P.rowdev = out;
-    LMFAO_CUDA(cudaStreamSynchronize(s));
-    cudaFree(segid);
-    P.arena.ptrs.erase(std::find(P.arena.ptrs.begin(), P.arena.ptrs.end(), (void *)segid));
+    hist = E->hist;
+    for (int c : P.rowcols) P.rowdev.push_back(DCol{E->cols[c], F.cols[c].dtype});
   } else {
     hist[0] = n;
     for (int c : P.rowcols) P.rowdev.push_back(dcol(F.cols[c]));
   }
+  P.reorg_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   // work items: each segment in chunks of at most WORK_CHUNK tuples
   std::vector<DWork> work;
   long long r0 = 0;
@@ -1938,6 +1971,75 @@ bool setup_combine4(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   return true;
 }
 
+// Two-kernel block combine (combine5.cu) over the block tables of P.c3: per-block contraction
+// Z_p = B_p^T Y_p into a global scratch array (FP32/FP64 on the CUDA cores, or split BF16 on
+// the tensor cores when the plan asks for it and Y and the B terms fit one MMA tile), then
+// one pass over the entries. Returns false (with the reason in P.c5_why) when it does not
+// apply; the single-kernel block combine then runs.
+bool setup_combine5(lmfao_ctx *ctx, PhysPlan &P) {
+  const char *env = getenv("LMFAO_COMBINE");
+  if (env && std::string(env) == "single") {
+    P.c5_why = "LMFAO_COMBINE=single";
+    return false;
+  }
+  const DComb3 &d = P.c3;
+  DComb5 D{};
+  D.c = d;
+  const int ny = d.nyf + d.nyi;
+  const int64_t m = d.m;
+  const bool tc_fits = ny <= 128 && d.nb <= 256;
+  D.tc = P.split_bf16 && tc_fits ? 1 : 0;
+  if (P.split_bf16 && !tc_fits)
+    P.c5_why = "split BF16 needs at most 128 Y columns and 256 B terms (have " + std::to_string(ny) + ", " +
+               std::to_string(d.nb) + "): contraction in FP32";
+  D.npad = std::max(16, (d.nb + 15) / 16 * 16);
+  D.tmem_cols = 32;
+  while (D.tmem_cols < D.npad) D.tmem_cols *= 2;
+  const int ts = P.fp64 ? 8 : 4;
+  int kc0 = 64;
+  if (const char *k = getenv("LMFAO_COMBINE_CHUNK")) kc0 = std::max(16, atoi(k) / 16 * 16);
+  int kc = D.tc ? (int)std::min<int64_t>(kc0, (m + 15) / 16 * 16) : (int)std::min<int64_t>(kc0, m);
+  for (; kc >= (D.tc ? 16 : 1); kc = D.tc ? kc - 16 : kc / 2) {
+    D.kc = kc;
+    if (combine5_smem(D, P.fp64) <= 200 * 1024) break;
+  }
+  if (kc < (D.tc ? 16 : 1)) {
+    P.c5_why = "block tables do not fit shared memory";
+    return false;
+  }
+  // TMA bulk staging: every chunk's rows start on a 16-byte boundary and span a multiple of 16 bytes
+  const int64_t rb[5] = {(int64_t)d.n0f * ts, d.phi1f_seg * 4, (int64_t)d.n0i * 8, d.phi1i_seg * 4, 8};
+  const void *base[5] = {d.phi0f, d.phi1f, d.phi0i, d.phi1i, d.wseg};
+  D.bulk = 1;
+  for (int i = 0; i < 5; ++i) {
+    if (!rb[i]) continue;
+    if ((m * rb[i]) % 16 || ((int64_t)D.kc * rb[i]) % 16 || ((uintptr_t)base[i] % 16)) D.bulk = 0;
+  }
+  const int64_t nz = d.nblocks * (int64_t)d.nb * ny, nzi = d.nblocks * (int64_t)d.nbi * d.nyi;
+  const int64_t bytes = nz * ts + nzi * 8 + d.nblocks * (int64_t)d.na * (ts + 8) + d.nblocks * (int64_t)d.nog * 8 +
+                        d.nblocks * 4;
+  if (bytes > ((int64_t)1 << 30)) {
+    P.c5_why = "per-block scratch above 1 GiB";
+    return false;
+  }
+  D.z = P.arena.alloc(std::max<int64_t>(1, nz) * ts);
+  D.zi = (unsigned long long *)P.arena.alloc(std::max<int64_t>(1, nzi) * 8);
+  D.a = P.arena.alloc(std::max<int64_t>(1, d.nblocks * (int64_t)d.na) * ts);
+  D.ai = (unsigned long long *)P.arena.alloc(std::max<int64_t>(1, d.nblocks * (int64_t)d.na) * 8);
+  D.cells = (long long *)P.arena.alloc(std::max<int64_t>(1, d.nblocks * (int64_t)d.nog) * 8);
+  D.live = (int *)P.arena.alloc(std::max<int64_t>(1, d.nblocks) * 4);
+  D.err = P.err;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  D.grid = (int)std::min<int64_t>(d.nblocks, (int64_t)sms * 8);
+  const int64_t ethreads = (int64_t)(d.nent + 255) / 256 * 256;
+  D.eranges = (int)std::max<int64_t>(1, std::min<int64_t>(d.nblocks, ((int64_t)sms * 2048 + ethreads - 1) /
+                                                                        std::max<int64_t>(1, ethreads)));
+  (void)ctx;
+  P.c5 = D;
+  return true;
+}
+
 // Prefix-block combine (combine3.cu): eligible when the segment key has a proper prefix,
 // every outer cell is constant inside a block (A-level group references only) and the
 // block tables fit in shared memory. Returns false otherwise (the entry combine runs).
@@ -2144,6 +2246,7 @@ bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
     og_off.push_back((int)og_refs.size());
   }
   d.nbst = (int)bstage.size();
+  d.nbpart = (int)bpart.size();
   d.nb = (int)bdesc.size();
   d.nbi = nbi;
   d.nast = (int)astage.size();
@@ -2153,7 +2256,7 @@ bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   d.mirror_f = fcells;
   d.mirror_i = icells;
   d.nmirror = (int)mirrors.size();
-  if (combine3_smem(d, P.fp64) > 222 * 1024) return false;  // + static shared memory < 227 KB
+  const bool c3_fits = combine3_smem(d, P.fp64) <= 222 * 1024;  // + static shared memory < 227 KB
   d.bstage = P.arena.upload(bstage.empty() ? std::vector<int2>{make_int2(0, 0)} : bstage, s);
   d.bterm = P.arena.upload(bdesc.empty() ? std::vector<DPsi>{DPsi{}} : bdesc, s);
   d.bpart = P.arena.upload(bpart.empty() ? std::vector<int>{0} : bpart, s);
@@ -2168,6 +2271,8 @@ bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   d.fsum = P.fsum;
   d.icnt = P.icnt;
   P.c3 = d;
+  P.use_c5 = setup_combine5(ctx, P);
+  if (!P.use_c5 && !c3_fits) return false;
   P.use_c3 = true;
   P.c3_block = 512;
   P.c3_grid = (int)std::max<int64_t>(1, std::min<int64_t>(148, d.nblocks));
@@ -2400,7 +2505,11 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     mark("fact_pass");
   }
   if (!P.comb.empty()) {
-    if (P.use_c3) launch_combine3(P.c3, P.fp64, P.c3_grid, P.c3_block, s);
+    if (P.use_c5) {
+      launch_combine5_z(P.c5, P.fp64, s);
+      mark("combine_z");
+      launch_combine5_entries(P.c5, P.fp64, s);
+    } else if (P.use_c3) launch_combine3(P.c3, P.fp64, P.c3_grid, P.c3_block, s);
     else if (P.use_c4) {
       const DComb4 &c4 = P.c4;
       if (c4.need_d0) {
@@ -2440,6 +2549,26 @@ int64_t fact_pass_bytes(const lmfao_ctx *ctx, const PhysPlan &P) {
   return b;
 }
 
+// Bytes the per-block contraction kernel must move per launch: the per-segment sums and segment
+// weights it reads, the B-side view columns of every segment and the A-side ones of every
+// block (FP64 views), and the Z, A and cell arrays it writes.
+int64_t combine_z_bytes(const PhysPlan &P) {
+  if (!P.use_c5) return 0;
+  const DComb3 &d = P.c3;
+  const int64_t ts = P.fp64 ? 8 : 4, nseg = d.nblocks * d.m, ny = d.nyf + d.nyi;
+  int64_t b = nseg * ((int64_t)d.n0f * ts + d.phi1f_seg * 4 + (int64_t)d.n0i * 8 + d.phi1i_seg * 4 + 8);
+  b += nseg * (int64_t)d.nbst * 8 + d.nblocks * (int64_t)d.nast * 8;
+  b += d.nblocks * ((int64_t)d.nb * ny * ts + (int64_t)d.nbi * d.nyi * 8 + (int64_t)d.na * (ts + 8) + (int64_t)d.nog * 8);
+  return b;
+}
+// Multiply-adds x 2 of the contraction Z_p = B_p^T Y_p over all blocks (the method's work; the
+// split-BF16 form issues three such products on the tensor cores).
+int64_t combine_z_flops(const PhysPlan &P) {
+  if (!P.use_c5) return 0;
+  const DComb3 &d = P.c3;
+  return 2 * d.nblocks * d.m * (int64_t)d.nb * (d.nyf + d.nyi);
+}
+
 std::string json_escape(const std::string &x) {
   std::string o;
   for (char c : x) {
@@ -2472,10 +2601,8 @@ lmfao_plan_opts default_opts() {
 // Options this engine does not evaluate are refused rather than replaced by others.
 void check_plan_opts(const lmfao_ctx *ctx, const lmfao_plan_opts &o) {
   (void)ctx;
-  if (o.precision != LMFAO_FP64 && o.precision != LMFAO_FP32)
-    throw Error(o.precision == LMFAO_SPLIT_BF16 ? LMFAO_ERR_UNSUPPORTED : LMFAO_ERR_ARG,
-                o.precision == LMFAO_SPLIT_BF16 ? "precision LMFAO_SPLIT_BF16 is not available in this build"
-                                                : "unknown precision " + std::to_string(o.precision));
+  if (o.precision != LMFAO_FP64 && o.precision != LMFAO_FP32 && o.precision != LMFAO_SPLIT_BF16)
+    throw Error(LMFAO_ERR_ARG, "unknown precision " + std::to_string(o.precision));
   if (o.autotune) throw Error(LMFAO_ERR_UNSUPPORTED, "autotuning is not available in this build");
   if (o.planner < LMFAO_PLAN_HEURISTIC || o.planner > LMFAO_PLAN_FORCED)
     throw Error(LMFAO_ERR_ARG, "unknown planner " + std::to_string(o.planner));
@@ -2587,6 +2714,7 @@ void build_plan(lmfao_ctx *ctx, const lmfao_plan_opts &o, bool dry, std::vector<
   PhysPlan *P = new PhysPlan();
   ctx->plan = P;
   P->fp64 = o.precision == LMFAO_FP64;
+  P->split_bf16 = o.precision == LMFAO_SPLIT_BF16;
   P->no_c3 = o.combine == 1;
   P->mode = (o.mode == LMFAO_MODE_PER_TUPLE || o.mode == LMFAO_MODE_GENERIC) ? o.mode : LMFAO_MODE_FACTORISED;
   P->root = root;
@@ -2703,6 +2831,33 @@ double time_plan(lmfao_ctx *ctx, int warm, int reps) {
 // Whether the last evaluation of the current plan passed its device checks (group-by
 // attributes determined by the join keys of their relations, exact 32-bit view counts).
 // A plan whose checks fail on the loaded data cannot be chosen by a planner.
+// Runs the view kernels of the current plan once on the context's stream and returns the
+// device error flags they raise (1: a group-by attribute of a non-root relation is not
+// determined by the key of that relation's view toward the root; 2: a count above 2^32).
+int view_flags(lmfao_ctx *ctx) {
+  PhysPlan &P = *ctx->plan;
+  cudaStream_t s = ctx->stream;
+  LMFAO_CUDA(cudaMemsetAsync(P.err, 0, 4, s));
+  for (size_t i = 0; i < P.vk.size(); ++i) {
+    View &v = P.views[P.vk_rel[i]];
+    LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
+    if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+    launch_view_kernel(P.vk[i], s);
+    launch_view_finish(v.v64, v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint, v.nkeys, P.err, s);
+  }
+  LMFAO_CUDA(cudaGetLastError());
+  int e = 0;
+  LMFAO_CUDA(cudaStreamSynchronize(s));
+  LMFAO_CUDA(cudaMemcpy(&e, P.err, 4, cudaMemcpyDeviceToHost));
+  return e;
+}
+
+bool views_carry_codes(const PhysPlan &P) {
+  for (size_t i = 0; i < P.vk.size(); ++i)
+    if (!P.views[P.vk_rel[i]].codes.empty()) return true;
+  return false;
+}
+
 bool plan_checks_pass(lmfao_ctx *ctx) {
   int e = 0;
   LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -2864,6 +3019,10 @@ int lmfao_destroy(lmfao_ctx *ctx) {
   for (auto &R : ctx->rels)
     for (auto &c : R.cols)
       if (c.owned && c.dev) cudaFree(c.dev);
+  for (auto &E : ctx->reorg) {
+    if (E.dest) cudaFree(E.dest);
+    for (auto &kv : E.cols) cudaFree(kv.second);
+  }
   for (auto e : ctx->events) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -3084,6 +3243,37 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
       build_plan(ctx, cand_opts(o, cands[best]), false, nullptr);
     } else {
       build_plan(ctx, o, false, nullptr);
+      // A group-by attribute of a non-root relation must be determined by the key of that
+      // relation's view toward the root (checked on the loaded data by the view kernels). The
+      // heuristic planner then tries the other relations as root, largest first; a forced root
+      // that fails is an error of the plan.
+      if (ctx->device >= 0 && ctx->plan && views_carry_codes(*ctx->plan) && (view_flags(ctx) & 1)) {
+        const int bad_root = ctx->plan->root;
+        drop_plan(ctx);
+        const std::string msg = "a group-by attribute of a non-root relation is not determined by the key of "
+                                "that relation's view toward the root";
+        if (o.planner == LMFAO_PLAN_FORCED)
+          return fail(ctx, LMFAO_ERR_UNSUPPORTED, msg + " (root " + ctx->rels[bad_root].name + ")");
+        std::vector<int> order((size_t)ctx->rels.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return ctx->rels[a].nrows > ctx->rels[b].nrows; });
+        bool ok = false;
+        for (int r : order) {
+          if (r == bad_root) continue;
+          lmfao_plan_opts o2 = o;
+          o2.planner = LMFAO_PLAN_FORCED;
+          o2.root_rel = r;
+          o2.segment_rel = -2;
+          build_plan(ctx, o2, false, nullptr);
+          if (!views_carry_codes(*ctx->plan) || !(view_flags(ctx) & 1)) {
+            ok = true;
+            break;
+          }
+          drop_plan(ctx);
+        }
+        if (!ok) return fail(ctx, LMFAO_ERR_UNSUPPORTED, msg + " for any root relation");
+      }
     }
     PhysPlan *P = ctx->plan;
     if (P) P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -3094,7 +3284,7 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
       info->n_segments = P ? P->nseg : 0;
       info->n_views = (int)ctx->logical.views.size();
       info->n_groups = (int)ctx->logical.groups.size();
-      int combine_kernels = P && !P->comb.empty() ? 1 : 0;
+      int combine_kernels = P && !P->comb.empty() ? (P->use_c5 ? 2 : 1) : 0;
       if (P && !P->comb.empty() && !P->use_c3 && P->use_c4) {  // projection combine: several kernels
         const DComb4 &c4 = P->c4;
         combine_kernels = 1 + ((c4.need_d1 || c4.nent3) ? 1 : 0) + (c4.nent3 ? 1 : 0) + (c4.nent012 ? 1 : 0);
@@ -3104,6 +3294,8 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
       info->mode = P ? P->mode : 0;
       info->predicted_ms = predicted;
       info->plan_ms = P ? P->plan_ms : 0;
+      info->reorg_ms = P ? P->reorg_ms : 0;
+      info->reorg_reused = P && P->reorg_cached ? 1 : 0;
     }
     return LMFAO_OK;
   });
@@ -3157,6 +3349,7 @@ static void check_device_flags(lmfao_ctx *ctx) {
     throw Error(LMFAO_ERR_UNSUPPORTED,
                 "a group-by attribute of a non-root relation is not determined by that relation's join key");
   if (e & 2) throw Error(LMFAO_ERR_UNSUPPORTED, "an exact count in a view exceeds 2^32");
+  if (e & 8) throw Error(LMFAO_ERR_TIMEOUT, "a bounded wait of the block combine ran out (results incomplete)");
 }
 
 int lmfao_fetch(lmfao_ctx *ctx, int query_id, lmfao_result *out) {
@@ -3299,18 +3492,28 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
     for (size_t i = 0; i < P.outer.size(); ++i) o << (i ? "," : "") << nm(P.outer[i]);
     o << "],\"inner\":[";
     for (size_t i = 0; i < P.inner.size(); ++i) o << (i ? "," : "") << nm(P.inner[i]);
-    o << "],\"precision\":\"" << (P.fp64 ? "fp64" : "fp32") << "\",\"mode\":\""
+    o << "],\"precision\":\"" << (P.fp64 ? "fp64" : P.split_bf16 ? "split_bf16" : "fp32") << "\",\"mode\":\""
       << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : P.fast.on ? "factorised" : "generic")
       << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false")
       << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false")
       << ",\"block_combine\":" << (P.use_c3 ? "true" : "false") << ",\"prefix_digits\":" << P.prefix_len
+      << ",\"block_combine_two_kernels\":" << (P.use_c5 ? "true" : "false") << ",\"contraction\":\""
+      << (!P.use_c5 ? (P.use_c3 ? "cuda cores, single kernel" : "none")
+                    : P.c5.tc ? "tensor cores (tcgen05, split BF16)" : (P.fp64 ? "cuda cores FP64" : "cuda cores FP32"))
+      << "\",\"combine_chunk\":" << P.c5.kc << ",\"combine_bulk_copies\":" << (P.c5.bulk ? "true" : "false")
+      << ",\"combine_blocks\":" << P.c3.nblocks << ",\"combine_entries\":" << P.c3.nent
+      << ",\"block_terms\":[" << P.c3.na << "," << P.c3.nb << "," << P.c3.nbi << "]"
+      << ",\"y_columns\":[" << P.c3.nyf << "," << P.c3.nyi << "]"
+      << ",\"combine_note\":\"" << json_escape(P.c5_why) << "\""
+      << ",\"combine_z_bytes\":" << combine_z_bytes(P) << ",\"combine_z_flops\":" << combine_z_flops(P)
       << ",\"projection_combine\":" << (!P.use_c3 && P.use_c4 ? "true" : "false")
       << ",\"projection_entries\":[" << P.c4.nent012 << "," << P.c4.nent3 << "," << P.c4.njobs << "]"
       << ",\"filter_family\":" << P.fast.fam_k << ",\"cta_items\":" << P.fast.b4.size()
       << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
-      << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows;
+      << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows
+      << ",\"reorganisation_ms\":" << P.reorg_ms << ",\"reorganisation_reused\":" << (P.reorg_cached ? "true" : "false");
     if (P.fast.on) {
       const DFast &d = P.fd;
       o << ",\"root_pass\":{\"monomials\":" << d.nm << ",\"inner_columns\":" << d.nw << ",\"value_columns\":" << d.nx
@@ -3321,7 +3524,8 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
         << ",\"smem_bytes\":" << fast_smem(d, P.fp64, P.fast_block) << ",\"block\":" << P.fast_block
         << ",\"grid\":" << P.fast_grid << ",\"vector_loads\":" << d.vec
         << ",\"generated\":" << (P.gen.fn ? "true" : "false") << ",\"generated_block\":" << P.gen.block
-        << ",\"generated_smem\":" << P.gen.smem << ",\"not_generated_because\":\"" << json_escape(P.gen.why)
+        << ",\"generated_smem\":" << P.gen.smem << ",\"source_hash\":\"" << (P.gen.fn ? P.gen.source_hash : "")
+        << "\",\"not_generated_because\":\"" << json_escape(P.gen.why)
         << "\"}";
     }
     o
@@ -3350,10 +3554,116 @@ int lmfao_cart_variances(lmfao_ctx *ctx, const int *qids, int n, double *out, vo
     const int nb = cart_descriptors(ctx, qids, n, qd.data());
     if (!n || nb < 2) return LMFAO_OK;
     PhysPlan &P = *ctx->plan;
+    check_device_flags(ctx);  // the run's own failures (counts above 2^32, a wait that ran out)
     int64_t *dq = P.arena.upload(qd, ctx->stream);
     LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
     launch_cart_variances(P.icnt, P.fsum, dq, n, nb, out, (cudaStream_t)stream);
     LMFAO_CUDA(cudaGetLastError());
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_cart_tree(lmfao_ctx *ctx, const char *target, const char *const *features, int nfeatures,
+                    const float *thresholds, const int32_t *nthresholds, int depth, const lmfao_plan_opts *opts,
+                    lmfao_cart_node *nodes, double *level_ms) {
+  return guarded(ctx, [&]() -> int {
+    if (ctx->device < 0) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "host-only context");
+    if (!target || !features || nfeatures <= 0 || !thresholds || !nthresholds || !nodes || depth < 1 || depth > 5)
+      return fail(ctx, LMFAO_ERR_ARG, "bad tree arguments");
+    std::vector<std::vector<float>> thr(nfeatures);
+    int64_t off = 0;
+    for (int f = 0; f < nfeatures; ++f) {
+      if (!features[f] || nthresholds[f] < 1 || nthresholds[f] > 31) return fail(ctx, LMFAO_ERR_ARG, "bad feature thresholds");
+      thr[f].assign(thresholds + off, thresholds + off + nthresholds[f]);
+      off += nthresholds[f];
+      for (size_t k = 1; k < thr[f].size(); ++k)
+        if (!(thr[f][k - 1] < thr[f][k])) return fail(ctx, LMFAO_ERR_ARG, "thresholds must be strictly ascending");
+    }
+    const int nnodes_all = (1 << depth) - 1;
+    for (int i = 0; i < nnodes_all; ++i) nodes[i] = lmfao_cart_node{0, -1, 0.f, 0.0, 0, 0.0, 0.0};
+    std::vector<std::vector<PredIn>> path(nnodes_all);
+    nodes[0].active = 1;
+    for (int lev = 0; lev < depth; ++lev) {
+      const auto t0 = std::chrono::steady_clock::now();
+      std::vector<int> act;
+      for (int v = (1 << lev) - 1; v < (1 << (lev + 1)) - 1; ++v)
+        if (nodes[v].active) act.push_back(v);
+      if (act.empty()) {
+        if (level_ms) level_ms[2 * lev] = level_ms[2 * lev + 1] = 0;
+        continue;
+      }
+      drop_plan(ctx);
+      ctx->queries.clear();
+      for (int v : act)
+        for (int f = 0; f < nfeatures; ++f) {
+          QueryIn q;
+          q.aggs = {{}, {FactorIn{target, LMFAO_FN_ID, 1}}, {FactorIn{target, LMFAO_FN_POW, 2}}};
+          q.gb = {GroupIn{features[f], LMFAO_GB_BUCKET, thr[f]}};
+          q.filters = path[v];
+          ctx->queries.push_back(q);
+        }
+      int rc = lmfao_plan(ctx, opts, nullptr);
+      if (rc != LMFAO_OK) return rc;
+      const auto t1 = std::chrono::steady_clock::now();
+      PhysPlan &P = *ctx->plan;
+      enqueue_run(ctx, P, ctx->tree, ctx->stream);
+      ctx->run_stream = ctx->stream;
+      ctx->ran = true;
+      const int nq = (int)ctx->queries.size();
+      std::vector<int> ids(nq);
+      std::iota(ids.begin(), ids.end(), 0);
+      std::vector<int64_t> qd((size_t)nq * kCartDescWords);
+      for (int i = 0; i < nq; ++i) {
+        const QueryOut &qo = P.qout[i];
+        int64_t *d = qd.data() + (size_t)i * kCartDescWords;
+        d[0] = qo.io;
+        d[1] = qo.fo;
+        d[2] = qo.cells;
+        d[3] = qo.naggs;
+        d[4] = 1;
+        d[5] = 2;
+      }
+      std::vector<int> qbeg(act.size() + 1);
+      for (size_t i = 0; i <= act.size(); ++i) qbeg[i] = (int)i * nfeatures;
+      int64_t *dq = P.arena.upload(qd, ctx->stream);
+      int *dqb = P.arena.upload(qbeg, ctx->stream);
+      int2 *dbest = (int2 *)P.arena.alloc(act.size() * sizeof(int2));
+      double *dscore = (double *)P.arena.alloc(act.size() * 8);
+      double *dstats = (double *)P.arena.alloc(act.size() * 3 * 8);
+      launch_cart_split(P.icnt, P.fsum, dq, dqb, (int)act.size(), dbest, dscore, dstats, ctx->stream);
+      LMFAO_CUDA(cudaGetLastError());
+      check_device_flags(ctx);
+      std::vector<int2> best(act.size());
+      std::vector<double> score(act.size()), stats(3 * act.size());
+      LMFAO_CUDA(cudaMemcpy(best.data(), dbest, best.size() * sizeof(int2), cudaMemcpyDeviceToHost));
+      LMFAO_CUDA(cudaMemcpy(score.data(), dscore, score.size() * 8, cudaMemcpyDeviceToHost));
+      LMFAO_CUDA(cudaMemcpy(stats.data(), dstats, stats.size() * 8, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < act.size(); ++i) {
+        const int v = act[i];
+        lmfao_cart_node &nd = nodes[v];
+        nd.count = (int64_t)stats[3 * i];
+        nd.sum_y = stats[3 * i + 1];
+        nd.sum_y2 = stats[3 * i + 2];
+        if (best[i].x < 0) continue;
+        nd.feature = best[i].x;
+        nd.threshold = thr[nd.feature][best[i].y];
+        nd.score = score[i];
+        if (2 * v + 2 < nnodes_all) {
+          for (int c = 0; c < 2; ++c) {
+            path[2 * v + 1 + c] = path[v];
+            path[2 * v + 1 + c].push_back(PredIn{features[nd.feature], c ? LMFAO_GT : LMFAO_LE, nd.threshold});
+            nodes[2 * v + 1 + c].active = 1;
+          }
+        }
+      }
+      const auto t2 = std::chrono::steady_clock::now();
+      if (level_ms) {
+        level_ms[2 * lev] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        level_ms[2 * lev + 1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+      }
+    }
+    drop_plan(ctx);
+    ctx->queries.clear();
     return LMFAO_OK;
   });
 }

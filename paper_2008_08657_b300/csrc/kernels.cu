@@ -390,10 +390,24 @@ struct DScatterCols {
   int ncols;
 };
 
-__global__ void scatter_rows_kernel(const int *segid, int64_t n, unsigned long long *cursor, DScatterCols c) {
+__global__ void scatter_rows_kernel(const int *segid, int64_t n, unsigned long long *cursor, DScatterCols c,
+                                    unsigned int *dest) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     unsigned long long pos = atomicAdd(cursor + segid[r], 1ull);
+    if (dest) dest[r] = (unsigned int)pos;
+    for (int j = 0; j < c.ncols; ++j) {
+      if (c.esz[j] == 4) reinterpret_cast<int *>(c.out[j])[pos] = reinterpret_cast<const int *>(c.in[j])[r];
+      else reinterpret_cast<unsigned char *>(c.out[j])[pos] = reinterpret_cast<const unsigned char *>(c.in[j])[r];
+    }
+  }
+}
+
+// out[dest[r]] = in[r]: a column moved into the segment order recorded by scatter_rows_kernel
+__global__ void permute_rows_kernel(const unsigned int *dest, int64_t n, DScatterCols c) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const unsigned int pos = dest[r];
     for (int j = 0; j < c.ncols; ++j) {
       if (c.esz[j] == 4) reinterpret_cast<int *>(c.out[j])[pos] = reinterpret_cast<const int *>(c.in[j])[r];
       else reinterpret_cast<unsigned char *>(c.out[j])[pos] = reinterpret_cast<const unsigned char *>(c.in[j])[r];
@@ -461,6 +475,71 @@ __global__ void cart_kernel(const unsigned long long *icnt, const double *fsum, 
     double rn = totn - cn, rs = tots - cs, rs2 = tots2 - cs2;
     out[((int64_t)q * (nb_max - 1) + b) * 2 + 0] = cn > 0 ? cs2 - cs * cs / cn : 0.0;
     out[((int64_t)q * (nb_max - 1) + b) * 2 + 1] = rn > 0 ? rs2 - rs * rs / rn : 0.0;
+  }
+}
+
+// Best CART split per node (Section 3, decision trees): the queries of node v are
+// qdesc[qbeg[v] .. qbeg[v+1]) (one per feature, in feature order), each a bucketed
+// (COUNT, SUM(y), SUM(y^2)) query. A split "bucket <= k" of a query is valid when both
+// sides hold tuples; its score is VARIANCE(left) + VARIANCE(right) in FP64. The least
+// score wins, ties going to the earlier query, then the lower threshold. One CTA per node.
+__global__ void __launch_bounds__(256) cart_split_kernel(const unsigned long long *icnt, const double *fsum,
+                                                         const int64_t *qdesc, const int *qbeg, int2 *best,
+                                                         double *score, double *stats) {
+  const int v = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q0 = qbeg[v], q1 = qbeg[v + 1];
+  double bs = 0.0;
+  int bq = -1, bk = -1;
+  // lanes over thresholds of one query per warp (at most 32 buckets per query here; more are
+  // handled by striding k)
+  for (int q = q0 + warp; q < q1; q += blockDim.x >> 5) {
+    const int64_t *qd = qdesc + (int64_t)q * 6;
+    const int64_t ib = qd[0], fb = qd[1];
+    const int nb = (int)qd[2], na = (int)qd[3], a1 = (int)qd[4], a2 = (int)qd[5];
+    double tn = 0, ts = 0, ts2 = 0;
+    for (int b = 0; b < nb; ++b) {
+      tn += (double)icnt[ib + (int64_t)b * (1 + na)];
+      ts += fsum[fb + (int64_t)b * na + a1];
+      ts2 += fsum[fb + (int64_t)b * na + a2];
+    }
+    if (q == q0 && lane == 0 && stats) {
+      stats[3 * v + 0] = tn;
+      stats[3 * v + 1] = ts;
+      stats[3 * v + 2] = ts2;
+    }
+    for (int k = lane; k + 1 < nb; k += 32) {
+      double cn = 0, cs = 0, cs2 = 0;
+      for (int b = 0; b <= k; ++b) {
+        cn += (double)icnt[ib + (int64_t)b * (1 + na)];
+        cs += fsum[fb + (int64_t)b * na + a1];
+        cs2 += fsum[fb + (int64_t)b * na + a2];
+      }
+      const double rn = tn - cn;
+      if (cn <= 0 || rn <= 0) continue;
+      const double sc = (cs2 - cs * cs / cn) + ((ts2 - cs2) - (ts - cs) * (ts - cs) / rn);
+      if (bq < 0 || sc < bs || (sc == bs && (q < bq || (q == bq && k < bk)))) { bs = sc; bq = q; bk = k; }
+    }
+  }
+  // CTA argmin with the same order
+  __shared__ double ss[256];
+  __shared__ int sq[256], sk[256];
+  ss[tid] = bs;
+  sq[tid] = bq;
+  sk[tid] = bk;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+      const double os = ss[tid + w];
+      const int oq = sq[tid + w], ok = sk[tid + w];
+      const bool take = oq >= 0 && (sq[tid] < 0 || os < ss[tid] ||
+                                    (os == ss[tid] && (oq < sq[tid] || (oq == sq[tid] && ok < sk[tid]))));
+      if (take) { ss[tid] = os; sq[tid] = oq; sk[tid] = ok; }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    best[v] = make_int2(sq[0] < 0 ? -1 : sq[0] - q0, sk[0]);
+    score[v] = sq[0] < 0 ? 0.0 : ss[0];
   }
 }
 
@@ -537,11 +616,20 @@ void launch_histogram(const int *segid, int64_t n, unsigned int *hist, cudaStrea
 }
 
 void launch_scatter_rows(const int *segid, int64_t n, unsigned long long *cursor, const DCol *in, DCol *out,
-                         const int *elem_size, int ncols, cudaStream_t s) {
+                         const int *elem_size, int ncols, unsigned int *dest, cudaStream_t s) {
   DScatterCols c{};
   c.ncols = ncols;
   for (int j = 0; j < ncols; ++j) { c.in[j] = in[j].p; c.out[j] = const_cast<void *>(out[j].p); c.esz[j] = elem_size[j]; }
-  scatter_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(segid, n, cursor, c);
+  scatter_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(segid, n, cursor, c, dest);
+}
+
+void launch_permute_rows(const unsigned int *dest, int64_t n, const DCol *in, DCol *out, const int *elem_size,
+                         int ncols, cudaStream_t s) {
+  if (n == 0 || ncols == 0) return;
+  DScatterCols c{};
+  c.ncols = ncols;
+  for (int j = 0; j < ncols; ++j) { c.in[j] = in[j].p; c.out[j] = const_cast<void *>(out[j].p); c.esz[j] = elem_size[j]; }
+  permute_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(dest, n, c);
 }
 
 void launch_range_check(const void *p, int dtype, int64_t n, int64_t domain, int *bad, cudaStream_t s) {
@@ -568,6 +656,12 @@ void launch_cart_variances(const unsigned long long *icnt, const double *fsum, c
                            int nb_max, double *out, cudaStream_t s) {
   if (n == 0) return;
   cart_kernel<<<(n + 127) / 128, 128, 0, s>>>(icnt, fsum, qdesc, n, nb_max, out);
+}
+
+void launch_cart_split(const unsigned long long *icnt, const double *fsum, const int64_t *qdesc, const int *qbeg,
+                       int nnodes, int2 *best, double *score, double *stats, cudaStream_t s) {
+  if (nnodes == 0) return;
+  cart_split_kernel<<<nnodes, 256, 0, s>>>(icnt, fsum, qdesc, qbeg, best, score, stats);
 }
 
 void launch_results(const unsigned long long *icnt, const double *fsum, int64_t cells, int naggs, const int *integral,

@@ -219,13 +219,17 @@ void launch_segment_ids(const DCol *cols, int ncols, const int64_t *radix, int64
                         cudaStream_t s);
 void launch_histogram(const int *segid, int64_t n, unsigned int *hist, cudaStream_t s);
 void launch_scatter_rows(const int *segid, int64_t n, unsigned long long *cursor, const DCol *in,
-                         DCol *out, const int *elem_size, int ncols, cudaStream_t s);
+                         DCol *out, const int *elem_size, int ncols, unsigned int *dest, cudaStream_t s);
+void launch_permute_rows(const unsigned int *dest, int64_t n, const DCol *in, DCol *out, const int *elem_size,
+                         int ncols, cudaStream_t s);
 void launch_range_check(const void *p, int dtype, int64_t n, int64_t domain, int *bad, cudaStream_t s);
 void launch_key_multiplicity(const DCol *cols, int ncols, const int64_t *stride, int64_t n,
                              unsigned int *hist, cudaStream_t s);
 void launch_max_u32(const unsigned int *h, int64_t n, unsigned int *out, cudaStream_t s);
 void launch_cart_variances(const unsigned long long *icnt, const double *fsum, const int64_t *qdesc,
                            int n, int nb_max, double *out, cudaStream_t s);
+void launch_cart_split(const unsigned long long *icnt, const double *fsum, const int64_t *qdesc, const int *qbeg,
+                       int nnodes, int2 *best, double *score, double *stats, cudaStream_t s);
 void launch_results(const unsigned long long *icnt, const double *fsum, int64_t cells, int naggs,
                     const int *integral, int64_t *counts, double *sums, cudaStream_t s);
 
@@ -252,6 +256,7 @@ struct DComb3 {
   int nouter;
   DOuter outer[MAXOUT];
   int nbst, nb, nbi;        // staged B columns, B terms, integral B terms (first nbi terms)
+  int nbpart;               // entries of bpart
   const int2 *bstage;       // (outer view, column)
   const DPsi *bterm;        // parts index bpart[]
   const int *bpart;         // -> staged B column
@@ -279,5 +284,30 @@ struct DComb3 {
 };
 size_t combine3_smem(const DComb3 &d, bool fp64);
 void launch_combine3(const DComb3 &d, bool fp64, int grid, int block, cudaStream_t s);
+
+// Two-kernel prefix-block combine (combine5.cu): block_z_kernel computes per block p the
+// contraction Z_p = B_p^T Y_p (FP32 or FP64 on the CUDA cores, or split-BF16 on the tensor
+// cores), the integral part exactly, the A terms a_alpha(p) and the outer cells, into global
+// scratch arrays; block_entries_kernel then forms SUM_p a_alpha(p) Z_p[beta][c] per entry.
+struct DComb5 {
+  DComb3 c;                  // segments, outer views, A/B terms, Y columns, entries, outputs
+  int kc;                    // segments per chunk (a multiple of 16 on the tensor-core path)
+  int npad;                  // tensor-core path: N of the MMA (B terms rounded up to 16)
+  int tmem_cols;             // tensor-core path: tensor-memory columns allocated per CTA
+  int tc;                    // 1: contraction on the tensor cores (split BF16)
+  int bulk;                  // 1: per-segment sums staged with TMA bulk copies (16-byte aligned)
+  int grid;                  // CTAs of block_z_kernel
+  int eranges;               // block ranges of block_entries_kernel (grid.y)
+  void *z;                   // nblocks x nb x ny (FP32 or FP64)
+  unsigned long long *zi;    // nblocks x nbi x nyi
+  void *a;                   // nblocks x na
+  unsigned long long *ai;    // nblocks x na (integral A terms)
+  long long *cells;          // nblocks x nog (-1: a code of the cell is missing)
+  int *live;                 // nblocks: some segment of the block has all its outer partners
+  int *err;                  // error flags (8: a bounded wait of block_z_kernel ran out)
+};
+size_t combine5_smem(const DComb5 &d, bool fp64);
+void launch_combine5_z(const DComb5 &d, bool fp64, cudaStream_t s);
+void launch_combine5_entries(const DComb5 &d, bool fp64, cudaStream_t s);
 
 }  // namespace lmfao

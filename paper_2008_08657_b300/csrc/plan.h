@@ -58,6 +58,7 @@ struct DeviceArena {  // allocations owned by a plan
 
 struct PhysPlan {
   bool fp64 = false;
+  bool split_bf16 = false;         // dense block contraction as split BF16 on the tensor cores
   int mode = LMFAO_MODE_FACTORISED;
   int root = -1, segrel = -1;
   std::vector<int> segcols;        // root columns forming the segment key
@@ -154,11 +155,16 @@ struct PhysPlan {
   bool use_c4 = false;
   DComb3 c3{};
   bool use_c3 = false, no_c3 = false;
+  DComb5 c5{};                     // two-kernel block combine (combine5.cu)
+  bool use_c5 = false;
+  std::string c5_why;              // why the two-kernel block combine does not run (if not)
   int c3_grid = 0, c3_block = 512;
   DSegWeight sw{};
   int fp_grid = 0, fp_block = 256;
   std::vector<std::string> kernel_names;
   double plan_ms = 0;
+  double reorg_ms = 0;             // host wall time of reorganising the root relation in this plan
+  bool reorg_cached = false;       // the segment order came from an earlier plan
 };
 
 }  // namespace lmfao

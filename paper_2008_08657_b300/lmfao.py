@@ -36,6 +36,7 @@ ENTRY_POINTS = [
     "lmfao_describe_plan", "lmfao_cart_variances", "lmfao_kernel_times", "lmfao_kernel_name",
     "lmfao_set_profiling", "lmfao_cart_variances_noalloc", "lmfao_mlp_param_count", "lmfao_mlp_forward",
     "lmfao_mlp_loss", "lmfao_mlp_backward", "lmfao_mlp_adam", "lmfao_plan_candidates", "lmfao_result_state",
+    "lmfao_cart_tree",
 ]
 COST_MODEL_PATH = os.path.join(_HERE, "cost_model.txt")
 
@@ -72,7 +73,13 @@ class PlanOpts(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("root_rel", C.c_int32), ("segment_rel", C.c_int32), ("n_segments", C.c_int64),
                 ("n_views", C.c_int32), ("n_groups", C.c_int32), ("n_kernels", C.c_int32),
-                ("mode", C.c_int32), ("predicted_ms", C.c_double), ("plan_ms", C.c_double)]
+                ("mode", C.c_int32), ("predicted_ms", C.c_double), ("plan_ms", C.c_double),
+                ("reorg_ms", C.c_double), ("reorg_reused", C.c_int32)]
+
+
+class CartNode(C.Structure):
+    _fields_ = [("active", C.c_int32), ("feature", C.c_int32), ("threshold", C.c_float), ("score", C.c_double),
+                ("count", C.c_int64), ("sum_y", C.c_double), ("sum_y2", C.c_double)]
 
 
 class Result(C.Structure):
@@ -126,6 +133,9 @@ def library():
             "lmfao_mlp_loss": (C.c_int, [P, P, C.c_int, P, P, P]),
             "lmfao_mlp_backward": (C.c_int, [P, C.c_int, C.c_int, P, P, P, P, P, P]),
             "lmfao_mlp_adam": (C.c_int, [P, P, P, P, C.c_int64, C.c_int, C.c_float, P]),
+            "lmfao_cart_tree": (C.c_int, [P, C.c_char_p, C.POINTER(C.c_char_p), C.c_int, C.POINTER(C.c_float),
+                                          C.POINTER(C.c_int32), C.c_int, C.POINTER(PlanOpts), C.POINTER(CartNode),
+                                          C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -386,6 +396,29 @@ class Engine:
         arr = (C.c_int * len(qids))(*[int(q) for q in qids])
         self._check(self.lib.lmfao_cart_variances(self.ctx, arr, len(qids), C.c_void_p(out.data_ptr()),
                                                   _stream_handle(stream)))
+
+    def cart_tree(self, target, features, thresholds, depth, precision="fp32"):
+        """Grow a regression tree (lmfao_cart_tree). ``thresholds``: dict or list of ascending
+        thresholds per feature. Returns (nodes in heap order as dicts, per-level [plan_ms, run_ms])."""
+        thr = [np.asarray(thresholds[f] if isinstance(thresholds, dict) else thresholds[i], dtype=np.float32)
+               for i, f in enumerate(features)]
+        names = (C.c_char_p * len(features))(*[f.encode() for f in features])
+        flat = np.ascontiguousarray(np.concatenate(thr).astype(np.float32))
+        counts = (C.c_int32 * len(features))(*[len(t) for t in thr])
+        o = PlanOpts()
+        o.precision = PRECISION[precision]
+        o.planner = PLANNER["heuristic"]
+        o.root_rel = -1
+        o.segment_rel = -2
+        nn = (1 << depth) - 1
+        nodes = (CartNode * nn)()
+        ms = (C.c_double * (2 * depth))()
+        self._check(self.lib.lmfao_cart_tree(self.ctx, target.encode(), names, len(features),
+                                             flat.ctypes.data_as(C.POINTER(C.c_float)), counts, depth, C.byref(o),
+                                             nodes, ms))
+        self.queries = []
+        out = [{f: getattr(nodes[i], f) for f, _ in CartNode._fields_} for i in range(nn)]
+        return out, [[ms[2 * i], ms[2 * i + 1]] for i in range(depth)]
 
     def cart_variances_noalloc(self, qids, out, stream=None):
         """Same as ``cart_variances`` without any device allocation (fixed descriptor

@@ -25,13 +25,21 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
 
 
-def test_traffic_from_the_committed_capture_scales_with_tuples():
+def test_traffic_is_taken_only_from_a_capture_of_the_same_kernel(tmp_path, monkeypatch):
+    """roofline.traffic comes from a committed ncu capture of the exact generated kernel (the
+    hash of its source text), scaled by tuples; any other kernel gets no traffic figure."""
     import bench
-    t40, src = bench.measured_traffic("retailer", 40_000_000, {"generated": True})
-    t84, _ = bench.measured_traffic("retailer", 84_000_000, {"generated": True})
-    assert src and t40 > 40_000_000 * 8 and t84 - t40 == 44_000_000 * 8
-    assert bench.measured_traffic("retailer", 84_000_000, {"generated": False}) == (None, None)
-    assert bench.measured_traffic("favorita", 84_000_000, {"generated": True}) == (None, None)
+    os.makedirs(tmp_path / "profiles")
+    rec = [{"kernel": "lmfao_gen_root_pass", "source_hash": "abc", "tuples": 40_000_000, "read": 366_000_000,
+            "write": 34_000_000, "bytes_per_tuple": 8}]
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    t40, src = bench.measured_traffic(40_000_000, {"generated": True, "source_hash": "abc"})
+    t84, _ = bench.measured_traffic(84_000_000, {"generated": True, "source_hash": "abc"})
+    assert t40 == 400_000_000 and t84 - t40 == 44_000_000 * 8 and "scaled" in src
+    t, why = bench.measured_traffic(84_000_000, {"generated": True, "source_hash": "other"})
+    assert t is None and "changed" in why
+    assert bench.measured_traffic(84_000_000, {"generated": False})[0] is None
 
 
 def test_parity_report_flags_errors_per_family():

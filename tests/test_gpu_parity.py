@@ -27,14 +27,16 @@ def run_engine(rels, qs, **plan):
     return out, info
 
 
-@pytest.mark.parametrize("seed", range(16))
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+# (seed, forced segment relation): R4 exists only in the five-relation variant (odd seeds)
+TINY_SEG_CASES = [(seed, seg) for seed in range(16) for seg in (None, "R1", "R2", "R4")
+                  if seg != "R4" or seed % 2 == 1]
+
+
+@pytest.mark.parametrize("seed,segment", TINY_SEG_CASES)
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "split_bf16"])
 @pytest.mark.parametrize("mode", ["factorised", "generic", "per_tuple"])
-@pytest.mark.parametrize("segment", [None, "R1", "R2", "R4"])
 def test_tiny_schemas_match_oracle(seed, precision, mode, segment):
     shared3 = seed % 2 == 1
-    if segment == "R4" and not shared3:
-        pytest.skip("R4 exists only in the five-relation variant")
     rels = W.tiny_schema(seed, shared3=shared3, fd=True)
     qs = W.tiny_queries(seed, rels, nq=6, group_attrs=TINY_GROUPS, bucket_attrs=TINY_BUCKETS)
     ref = O.evaluate(rels, qs)
@@ -46,16 +48,13 @@ def test_tiny_schemas_match_oracle(seed, precision, mode, segment):
         compare(q, g, r, where=f"seed {seed} query {i}")
 
 
-@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("seed,segment", [(a, b) for a, b in TINY_SEG_CASES if b is not None])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("segment", ["R1", "R2", "R4"])
 def test_tiny_schemas_generated_root_pass(seed, precision, segment, monkeypatch):
     """Tiny schemas (duplicate and dangling keys, group-bys, buckets, filters) with the root
     pass generated at plan time at any size; shapes outside the generator keep the template."""
     monkeypatch.setenv("LMFAO_CODEGEN", "1")
     shared3 = seed % 2 == 1
-    if segment == "R4" and not shared3:
-        pytest.skip("R4 exists only in the five-relation variant")
     rels = W.tiny_schema(seed, shared3=shared3, fd=True)
     qs = W.tiny_queries(seed, rels, nq=6, group_attrs=TINY_GROUPS, bucket_attrs=TINY_BUCKETS)
     ref = O.evaluate(rels, qs)
@@ -219,11 +218,34 @@ def test_group_attribute_not_determined_by_key_is_reported():
     for R in rels:
         e.load_relation(R)
     e.add_query(q)
-    e.plan(root="R0")
-    e.run()
+    with pytest.raises(LmfaoError) as ei:  # detected on the loaded data when the plan is built
+        e.plan(root="R0")
+    assert ei.value.code == ERR_UNSUPPORTED and "not determined" in str(ei.value)
+    e.close()
+
+
+def test_heuristic_planner_avoids_a_root_that_leaves_a_group_by_undetermined():
+    """With 50k fact tuples the largest relation is Weather; rooted there, Item's bucketed
+    attribute would reach the root through Inventory's view keyed by (locn, date), which does
+    not determine it. The heuristic planner moves the root and the results equal the oracle;
+    forcing the Weather root is refused when planning."""
+    rels = W.retailer_schema(n_fact=50_000, seed=2)
+    item = next(R for R in rels if R["name"] == "Item")
+    thr = [float(v) for v in np.quantile(next(c["data"] for c in item["columns"] if c["attr"] == "i1"),
+                                         [0.25, 0.5, 0.75])]
+    qs = [{"aggs": [[], [("y", "id", 1)], [("y", "pow", 2)]], "groupby": [("i1", "bucket", thr)], "filters": []}]
+    ref = O.evaluate(rels, qs)
+    e = Engine(0)
+    for R in rels:
+        e.load_relation(R)
+    e.add_queries(qs)
     with pytest.raises(LmfaoError) as ei:
-        e.fetch(0)
+        e.plan(root="Weather")
     assert ei.value.code == ERR_UNSUPPORTED
+    e.plan()
+    assert e.describe()["physical"]["root"] != "Weather"
+    e.run()
+    compare(qs[0], e.fetch(0), ref[0])
     e.close()
 
 
@@ -375,3 +397,35 @@ def test_favorita_projection_and_entry_combine(precision, projection, monkeypatc
     assert phys["projection_combine"] == projection
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"{precision} projection={projection} query {i}")
+
+
+@pytest.mark.parametrize("precision,impl", [("fp32", "two"), ("fp64", "two"), ("split_bf16", "two"),
+                                            ("fp32", "single"), ("fp64", "single")])
+def test_block_combine_kernels_match_the_oracle(precision, impl, monkeypatch):
+    """The block combine as two kernels (per-block contraction into scratch, then the entries;
+    FP32 and FP64 on the CUDA cores, split BF16 on the tensor cores with TMA-staged sums) and
+    as the single-kernel form, on the Retailer shape with ragged segments: blocks of 124
+    segments run as chunks of 64 and 60 (the last padded to the MMA's K)."""
+    monkeypatch.setenv("LMFAO_COMBINE", impl)
+    rels, qs, ref = _shape_case("retailer")
+    e = Engine(0)
+    try:
+        for R in rels:
+            e.load_relation(R)
+        e.add_queries(qs)
+        e.plan(precision=precision)
+        phys = e.describe()["physical"]
+        # in FP64 the single-kernel block tables exceed shared memory: the entry combine runs
+        assert phys["block_combine"] == (impl == "two" or precision != "fp64"), phys
+        assert phys["block_combine_two_kernels"] == (impl == "two"), phys["combine_note"]
+        if impl == "two":
+            assert phys["combine_bulk_copies"], phys
+            want = {"fp32": "cuda cores FP32", "fp64": "cuda cores FP64",
+                    "split_bf16": "tensor cores (tcgen05, split BF16)"}[precision]
+            assert phys["contraction"] == want, phys
+        e.run()
+        got = e.fetch_all()
+    finally:
+        e.close()
+    for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r, where=f"query {i}")
