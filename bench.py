@@ -177,7 +177,7 @@ def bench_lmfao(args):
     for R in rels:
         eng.load_relation(R)
     eng.add_queries(qs)
-    info = eng.plan(precision=args.precision)
+    info = eng.plan(precision=args.precision, autotune=args.autotune)
     desc = eng.describe()
     stream = torch.cuda.Stream()
     # kernel-level timing of the dominant kernel (CUDA events inside lmfao_run, same stream)
@@ -267,6 +267,7 @@ def bench_lmfao(args):
         "reorg_ms": info["reorg_ms"],
         "batches_from_resident_data": batches,
         "combine_roofline": comb,
+        "tiles": desc["physical"].get("tiles"),
         "kernel_ms": kernel_ms,
         "root_pass_shape": desc["physical"].get("root_pass"),
         "combine_shape": {k: desc["physical"].get(k) for k in
@@ -472,6 +473,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="plan with the default tiles instead of timing candidates")
     ap.add_argument("--no-parity", dest="parity", action="store_false",
                     help="skip the comparison of every aggregate with the oracle over the whole workload")
     args = ap.parse_args()

@@ -131,8 +131,11 @@ typedef struct lmfao_plan_opts {
   int32_t segment_rel;      /* FORCED: child of the root whose join key orders the root
                                relation into segments (-1: none, -2: default)            */
   int32_t mode;             /* LMFAO_MODE_*: factorised views or per-tuple evaluation   */
-  int32_t autotune;         /* nonzero: time launch shapes once and keep the fastest
-                               (LMFAO_ERR_UNSUPPORTED where this build has no tuner)     */
+  int32_t autotune;         /* nonzero: time a small set of launch shapes (root-pass work-
+                               item length, combine chunk) on the data while planning and
+                               keep the fastest; winners are cached in the file
+                               LMFAO_TUNE_CACHE (default ~/.cache/lmfao/tiles.txt) by plan
+                               shape and device, so the same shape is timed once        */
   const int32_t *join_parent; /* host, nullable: parent relation id per relation (-1 for
                                the tree root) to impose a join tree instead of GYO       */
   const int32_t *query_root;  /* host, nullable: logical root relation per query (-1:

@@ -234,6 +234,46 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "    wi = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  Work wk = {0, 0, 0};\n  unsigned long long ws = 0ull;\n";
   o << "  if (wi < nwork) { wk = work[wi]; ws = wseg[wk.seg]; }\n";
+  if (d.lanes) {
+    // one tuple per lane and step: tuple r0 + lane + 32 i; the next step's key and values are
+    // loaded while the current tuple is processed (coalesced 4-byte loads, no ragged edges)
+    auto lane_load = [&](const std::string &r, const std::string &ind) {
+      if (s.ni) o << ind << "kn = kc[" << r << "];\n";
+      for (int i = 0; i < s.nx; ++i) o << ind << "xn" << i << " = (T)xc" << i << "[" << r << "];\n";
+    };
+    if (s.ni) o << "  int kn = 0;\n";
+    for (int i = 0; i < s.nx; ++i) o << "  T xn" << i << " = (T)0;\n";
+    o << "  long long r = wk.r0 + lane;\n";
+    o << "  if (r < wk.r0 + wk.len) {\n";
+    lane_load("r", "    ");
+    o << "  }\n";
+    o << "  while (wi < nwork) {\n";
+    o << "    unsigned int tnext = 0u;\n";
+    o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // read after the tuples of this item\n";
+    o << "    const T wsT = (T)ws;\n";
+    o << "    const unsigned int wsu = (unsigned int)ws;\n";
+    o << "    T acc[" << V << "];\n";
+    o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
+    o << "    if (ws != 0ull) {  // else no outer partner for the whole segment\n";
+    o << "      const long long rend = wk.r0 + wk.len;\n";
+    o << "      for (; r < rend; r += 32) {\n";
+    if (s.ni) o << "        const int kk = kn;\n";
+    for (int i = 0; i < s.nx; ++i) o << "        const T xk" << i << " = xn" << i << ";\n";
+    o << "        if (r + 32 < rend) {\n";
+    lane_load("r + 32", "          ");
+    o << "        }\n";
+    o << "        tuple(" << (s.ni ? "kk" : "0");
+    for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? "xk" + std::to_string(i) : std::string("(T)0"));
+    o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
+    o << "      }\n    }\n";
+    o << "    const long long wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
+    o << "    Work wkn = {0, 0, 0};\n    unsigned long long wsn = 0ull;\n";
+    o << "    if (wn < nwork) { wkn = work[wn]; wsn = wseg[wkn.seg]; }\n";
+    o << "    r = wkn.r0 + lane;\n";
+    o << "    if (r < wkn.r0 + wkn.len) {\n";
+    lane_load("r", "      ");
+    o << "    }\n";
+  } else {
   o << "  long long qa = (wk.r0 + 3) >> 2, qe = (wk.r0 + wk.len) >> 2;\n";
   o << "  if (qe < qa) qe = qa;\n";
   if (s.ni) o << "  int4 kn = make_int4(0, 0, 0, 0);\n";
@@ -284,6 +324,7 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "    if (q < qen) {\n";
   quad_load("q", "      ");
   o << "    }\n";
+  }
   o << "    if (ws != 0ull) {\n";
   // per-segment sums: reduce-scatter over the warp
   o << "    T r_[" << PV << "];\n";
@@ -321,7 +362,8 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     o << "    __syncwarp();\n";
   }
   o << "    }\n";
-  o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
+  if (d.lanes) o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n";
+  else o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
   o << "  }\n";
   // root-to-inner partials: CTA-private -> global
   o << "  __syncthreads();\n";

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cstdlib>
 #include <chrono>
+#include <fstream>
+#include <sys/stat.h>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -1274,6 +1276,22 @@ namespace {
 
 constexpr int64_t WORK_CHUNK = 4096;  // tuples per work item (segments longer than this split)
 
+// Work items of the root pass: each segment in pieces of at most P.work_chunk tuples.
+void build_work(lmfao_ctx *ctx, PhysPlan &P) {
+  std::vector<DWork> work;
+  long long r0 = 0;
+  const int64_t wc = std::max(1, P.work_chunk);
+  for (int64_t sidx = 0; sidx < P.nseg; ++sidx) {
+    int64_t len = P.seg_hist[sidx];
+    for (int64_t o = 0; o < len; o += wc)
+      work.push_back(DWork{r0 + o, (int)sidx, (int)std::min<int64_t>(wc, len - o)});
+    r0 += len;
+  }
+  P.nwork = (int64_t)work.size();
+  P.work = P.arena.upload(work.empty() ? std::vector<DWork>{DWork{0, 0, 0}} : work, ctx->stream);
+  if (work.empty()) P.nwork = 0;
+}
+
 void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
   cudaStream_t s = ctx->stream;
   const Relation &F = ctx->rels[t.root];
@@ -1352,17 +1370,9 @@ void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
     for (int c : P.rowcols) P.rowdev.push_back(dcol(F.cols[c]));
   }
   P.reorg_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  // work items: each segment in chunks of at most WORK_CHUNK tuples
-  std::vector<DWork> work;
-  long long r0 = 0;
-  for (int64_t sidx = 0; sidx < P.nseg; ++sidx) {
-    int64_t len = hist[sidx];
-    for (int64_t o = 0; o < len; o += WORK_CHUNK)
-      work.push_back(DWork{r0 + o, (int)sidx, (int)std::min<int64_t>(WORK_CHUNK, len - o)});
-    r0 += len;
-  }
-  P.nwork = (int64_t)work.size();
-  P.work = P.arena.upload(work, s);
+  P.seg_hist = hist;
+  P.work_chunk = (int)WORK_CHUNK;
+  build_work(ctx, P);
 }
 
 // Device tables of the specialised root pass and of the B3 finalisation.
@@ -1599,6 +1609,8 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   // disables it, =1 forces it at any size
   P.gen = GenRootPass{};
   {
+    const char *lanes = std::getenv("LMFAO_ROOT_LANES");
+    d.lanes = lanes ? (std::atoi(lanes) != 0) : 0;
     const char *env = std::getenv("LMFAO_CODEGEN");
     const int mode = env ? std::atoi(env) : -1;
     if (mode == 1 || (mode != 0 && ctx->rels[P.root].nrows >= (int64_t(1) << 20))) {
@@ -2603,7 +2615,6 @@ void check_plan_opts(const lmfao_ctx *ctx, const lmfao_plan_opts &o) {
   (void)ctx;
   if (o.precision != LMFAO_FP64 && o.precision != LMFAO_FP32 && o.precision != LMFAO_SPLIT_BF16)
     throw Error(LMFAO_ERR_ARG, "unknown precision " + std::to_string(o.precision));
-  if (o.autotune) throw Error(LMFAO_ERR_UNSUPPORTED, "autotuning is not available in this build");
   if (o.planner < LMFAO_PLAN_HEURISTIC || o.planner > LMFAO_PLAN_FORCED)
     throw Error(LMFAO_ERR_ARG, "unknown planner " + std::to_string(o.planner));
 }
@@ -2826,6 +2837,151 @@ double time_plan(lmfao_ctx *ctx, int warm, int reps) {
   cudaEventDestroy(b);
   std::sort(ms.begin(), ms.end());
   return ms[ms.size() / 2];
+}
+
+// ------------------------------------------------------------------ tile autotuner
+// Launch shapes that change speed but not results: the root pass's work-item length (tuples
+// per work item taken from the ticket) and the per-block combine's chunk of segments. The
+// tuner times whole runs of the plan on its data for a small candidate set (coordinate search:
+// work-item length first, then the chunk), keeps the fastest and records it in a cache file
+// (LMFAO_TUNE_CACHE, default ~/.cache/lmfao/tiles.txt) under a key of the plan's shape and the
+// device, so a later plan of the same shape takes the tiles without timing.
+
+void set_work_chunk(lmfao_ctx *ctx, PhysPlan &P, int chunk) {
+  if (P.seg_hist.empty()) return;
+  P.work_chunk = chunk;
+  build_work(ctx, P);
+  P.fd.nwork = P.nwork;
+  P.fd.work = P.work;
+  P.fp.nwork = P.nwork;
+  P.fp.work = P.work;
+  if (P.gen.fn) {
+    int per_sm = 1, nsm = 148;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.gen.fn, P.gen.block, P.gen.smem);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    cudaGetLastError();
+    P.fast_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(1, per_sm), P.nwork));
+  }
+}
+
+// Lane layout of the generated lean root pass (one tuple per lane, or a 4-tuple quad per lane);
+// regenerates (or takes from the process cache) the kernel. False when not applicable.
+bool set_root_lanes(lmfao_ctx *ctx, PhysPlan &P, int lanes) {
+  if (!P.gen.fn || P.gen.family || !P.fd.lean) return false;
+  DFast d = P.fd;
+  d.lanes = lanes;
+  GenRootPass g = gen_root_pass(d, P.fp64, ctx->device, P.thr);
+  if (!g.fn) return false;
+  P.fd.lanes = lanes;
+  P.gen = g;
+  int per_sm = 1, nsm = 148;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.gen.fn, P.gen.block, P.gen.smem);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  cudaGetLastError();
+  P.fast_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(1, per_sm), P.nwork));
+  return true;
+}
+
+// A chunk of segments for the two-kernel block combine: a multiple of 16 on the tensor-core
+// path; rejected when its tables do not fit shared memory or break the bulk-copy alignment.
+bool set_combine_chunk(PhysPlan &P, int kc) {
+  if (!P.use_c5) return false;
+  DComb5 D = P.c5;
+  const int64_t m = D.c.m;
+  if (D.tc) kc = (int)std::min<int64_t>(kc, (m + 15) / 16 * 16);
+  else kc = (int)std::min<int64_t>(kc, m);
+  if (kc < 1 || (D.tc && kc % 16)) return false;
+  D.kc = kc;
+  if (combine5_smem(D, P.fp64) > 200 * 1024) return false;
+  if (D.bulk) {
+    const int64_t ts = P.fp64 ? 8 : 4;
+    const int64_t rb[5] = {(int64_t)D.c.n0f * ts, D.c.phi1f_seg * 4, (int64_t)D.c.n0i * 8, D.c.phi1i_seg * 4, 8};
+    for (int i = 0; i < 5; ++i)
+      if (rb[i] && ((int64_t)kc * rb[i]) % 16) return false;
+  }
+  P.c5 = D;
+  return true;
+}
+
+std::string tune_key(const lmfao_ctx *ctx, const PhysPlan &P) {
+  std::ostringstream k;
+  cudaDeviceProp pr{};
+  cudaGetDeviceProperties(&pr, ctx->device);
+  std::string name = pr.name;
+  for (char &c : name)
+    if (c == ' ') c = '_';
+  k << name << "/" << pr.multiProcessorCount << "/" << (P.fp64 ? "fp64" : P.split_bf16 ? "bf16x3" : "fp32") << "/"
+    << ctx->rels[P.root].nrows << "/" << P.nseg << "/" << P.gen.source_hash << "/" << P.use_c5 << "/" << P.c3.nb
+    << "x" << P.c3.nyf + P.c3.nyi << "x" << P.c3.m << "x" << P.c3.nblocks << "/" << P.c3.nent;
+  return k.str();
+}
+
+std::string tune_cache_path() {
+  if (const char *p = std::getenv("LMFAO_TUNE_CACHE")) return p;
+  const char *home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/lmfao/tiles.txt";
+}
+
+void autotune(lmfao_ctx *ctx, PhysPlan &P) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const std::string key = tune_key(ctx, P), path = tune_cache_path();
+  P.tuned = true;
+  {
+    std::ifstream in(path);
+    std::string k;
+    int wc = 0, kc = 0, ln = -1;
+    double ms = 0;
+    while (in >> k >> wc >> kc >> ln >> ms)
+      if (k == key) {
+        if (ln >= 0 && ln != P.fd.lanes) set_root_lanes(ctx, P, ln);
+        if (wc > 0) set_work_chunk(ctx, P, wc);
+        if (kc > 0) set_combine_chunk(P, kc);
+        P.tune_cached = true;
+      }
+    if (P.tune_cached) {
+      P.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      return;
+    }
+  }
+  double best = time_plan(ctx, 1, 3);
+  P.tune_candidates = 1;
+  int best_ln = P.fd.lanes;
+  if (set_root_lanes(ctx, P, 1 - best_ln)) {
+    const double ms = time_plan(ctx, 1, 3);
+    ++P.tune_candidates;
+    if (ms < best) { best = ms; best_ln = 1 - best_ln; }
+    else set_root_lanes(ctx, P, best_ln);
+  }
+  int best_wc = P.work_chunk;
+  if (!P.seg_hist.empty()) {
+    for (int wc : {1024, 2048, 8192, 16384}) {
+      set_work_chunk(ctx, P, wc);
+      const double ms = time_plan(ctx, 1, 3);
+      ++P.tune_candidates;
+      if (ms < best) { best = ms; best_wc = wc; }
+    }
+    set_work_chunk(ctx, P, best_wc);
+  }
+  int best_kc = P.use_c5 ? P.c5.kc : 0;
+  if (P.use_c5) {
+    for (int kc : {16, 32, 64, 128}) {
+      if (kc == best_kc || !set_combine_chunk(P, kc)) continue;
+      const double ms = time_plan(ctx, 1, 3);
+      ++P.tune_candidates;
+      if (ms < best) { best = ms; best_kc = kc; }
+    }
+    set_combine_chunk(P, best_kc);
+  }
+  // append the winner to the cache file (one line per key; the last line of a key wins)
+  const std::string dir = path.substr(0, path.find_last_of('/'));
+  if (!dir.empty()) {
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  }
+  std::ofstream out(path, std::ios::app);
+  if (out) out << key << " " << best_wc << " " << best_kc << " " << (P.gen.fn && !P.gen.family ? best_ln : -1) << " "
+                << best << "\n";
+  P.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 // Whether the last evaluation of the current plan passed its device checks (group-by
@@ -3276,6 +3432,7 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
       }
     }
     PhysPlan *P = ctx->plan;
+    if (P && o.autotune && ctx->device >= 0) autotune(ctx, *P);
     if (P) P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
       std::memset(info, 0, sizeof(*info));
@@ -3513,6 +3670,11 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()
       << ",\"outer_terms\":" << P.psis.size() << ",\"row_terms\":" << P.rts.size() << ",\"work_items\":" << P.nwork
       << ",\"fact_pass_bytes\":" << fact_pass_bytes(ctx, P) << ",\"root_rows\":" << ctx->rels[P.root].nrows
+      << ",\"tiles\":{\"work_chunk\":" << P.work_chunk << ",\"combine_chunk\":" << (P.use_c5 ? P.c5.kc : 0)
+      << ",\"root_pass_lanes\":" << (P.fd.lanes ? "\"tuple per lane\"" : "\"quad per lane\"")
+      << ",\"root_pass_grid\":" << P.fast_grid << ",\"root_pass_block\":" << (P.gen.fn ? P.gen.block : P.fast_block)
+      << ",\"autotuned\":" << (P.tuned ? "true" : "false") << ",\"from_cache\":" << (P.tune_cached ? "true" : "false")
+      << ",\"candidates\":" << P.tune_candidates << ",\"tune_ms\":" << P.tune_ms << "}"
       << ",\"reorganisation_ms\":" << P.reorg_ms << ",\"reorganisation_reused\":" << (P.reorg_cached ? "true" : "false");
     if (P.fast.on) {
       const DFast &d = P.fd;

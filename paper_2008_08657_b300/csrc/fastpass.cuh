@@ -86,6 +86,8 @@ struct DFast {
   // (1, x_i, x_i x_j), no indicators, B1 columns are inner COUNTs only
   int lean;
   int vec;                // root columns padded by 16 bytes: 4-tuple vector loads
+  int lanes;              // generated pass: one tuple per lane and step (coalesced 4-byte loads)
+                          // instead of a 4-tuple quad per lane (16-byte loads, ragged head/tail)
   int b1code[FMAXB1];     // inner view code (position in codes) of each B1 set
   double *p3f;            // [nkeys][n3]
   unsigned long long *p3i;

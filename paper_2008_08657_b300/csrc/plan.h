@@ -164,6 +164,11 @@ struct PhysPlan {
   std::vector<std::string> kernel_names;
   double plan_ms = 0;
   double reorg_ms = 0;             // host wall time of reorganising the root relation in this plan
+  std::vector<int64_t> seg_hist;   // tuples per segment of the root relation
+  int work_chunk = 4096;           // tuples per work item of the root pass (a tile the tuner picks)
+  bool tuned = false, tune_cached = false;  // tiles chosen by the autotuner (from its cache file)
+  int tune_candidates = 0;         // launch shapes timed by the autotuner
+  double tune_ms = 0;              // host time spent autotuning
   bool reorg_cached = false;       // the segment order came from an earlier plan
 };
 

@@ -55,6 +55,8 @@ int main() {
       d.n3 = 2; d.j3[0] = 0; d.int3[0] = 1; d.p3col[0] = 0; d.j3[1] = 1; d.p3col[1] = 0; d.n3f = 1; d.n3i = 1;
       d.n0i = 1;
       check(("lean_retailer" + sfx).c_str(), gen_root_pass_source(d, fp64, block));
+      d.lanes = 1;
+      check(("lean_retailer_lanes" + sfx).c_str(), gen_root_pass_source(d, fp64, block));
     }
     {  // Favorita-like lean pass: a float and a uint8 value column, three histogram sets
       DFast d = lean_base();

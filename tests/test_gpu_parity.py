@@ -429,3 +429,35 @@ def test_block_combine_kernels_match_the_oracle(precision, impl, monkeypatch):
         e.close()
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"query {i}")
+
+
+@pytest.mark.parametrize("which", ["retailer", "dt"])
+def test_autotuned_plans_match_the_oracle_and_reuse_their_tiles(which, tmp_path, monkeypatch):
+    """Autotuning times a few work-item lengths and combine chunks on the data while planning;
+    the tuned plan gives the oracle's results, and a second plan of the same shape takes its
+    tiles from the cache file without timing."""
+    monkeypatch.setenv("LMFAO_TUNE_CACHE", str(tmp_path / "tiles.txt"))
+    monkeypatch.setenv("LMFAO_CODEGEN", "1")
+    if which == "retailer":
+        rels, qs, ref = _shape_case("retailer")
+    else:
+        rels = W.retailer_schema(n_fact=300_000, seed=8)
+        qs = W.dt_level_batch(rels, seed=8)[0]
+        ref = O.evaluate(rels, qs)
+    for attempt in range(2):
+        e = Engine(0)
+        try:
+            for R in rels:
+                e.load_relation(R)
+            e.add_queries(qs)
+            e.plan(autotune=True)
+            tiles = e.describe()["physical"]["tiles"]
+            e.run()
+            got = e.fetch_all()
+        finally:
+            e.close()
+        assert tiles["autotuned"] and tiles["from_cache"] == (attempt == 1), tiles
+        if attempt == 0:
+            assert tiles["candidates"] >= 5, tiles
+        for i, (q, g, r) in enumerate(zip(qs, got, ref)):
+            compare(q, g, r, where=f"attempt {attempt} query {i}")
