@@ -104,7 +104,7 @@ bool family_eligible(const DFast &d, std::string &why, const std::vector<DGroupR
     for (int i = 0; i < d.b1[s].nref; ++i)
       if (!ref_ok(d.b1[s].ref[i])) { why = "histogram group code"; return false; }
   for (const DGroupRef &q : grefs4)
-    if (q.src != 2 || !ref_ok(q)) { why = "CTA-private item group code"; return false; }
+    if ((q.src != 2 && q.src != 3) || !ref_ok(q)) { why = "CTA-private item group code"; return false; }
   return true;
 }
 
@@ -261,7 +261,8 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   for (int s = 0; s < d.nb1; ++s)
     for (int i = 0; i < d.b1[s].nref; ++i)
       if (d.b1[s].ref[i].src == 2) declare_rowcode(d.b1[s].ref[i]);
-  for (const DGroupRef &q : grefs4) declare_rowcode(q);
+  for (const DGroupRef &q : grefs4)
+    if (q.src == 2) declare_rowcode(q);
   auto rowcode = [&](const DGroupRef &q) -> std::string {
     return rcode.at(std::make_pair(xidx(q.a), std::make_pair(q.thr0, q.nthr)));
   };
@@ -313,7 +314,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     o << "        if (val != (T)0) {\n          long long cell = 0;\n          bool ok = true;\n";
     for (int gi = d.b4_g0[i]; gi < d.b4_g0[i] + d.b4_ng[i]; ++gi) {
       const DGroupRef &q = grefs4[gi];
-      o << "          { const int c = " << rowcode(q) << "; if (c < 0) ok = false; cell += (long long)c * " << q.stride
+      o << "          { const int c = " << code_of(q) << "; if (c < 0) ok = false; cell += (long long)c * " << q.stride
         << "; }\n";
     }
     o << "          if (ok) ";

@@ -795,12 +795,19 @@ struct Planner {
   // Routing of the specialised root pass (at most one inner child): B0 as the outer product
   // of monomials and inner view columns, B1 per-segment group histograms, B3 partial view
   // from the root to the inner relation. Returns false when the batch needs the generic pass.
+  // Records why the specialised root pass does not take the batch (reported by the plan's
+  // description) and declines.
+  bool decline(const char *why) {
+    P.fast_why += std::string(P.fast_why.empty() ? "" : "; ") + (use_family ? "as a filter family: " : "") + why;
+    return false;
+  }
+
   bool route_fast(const std::vector<ItemD> &items) {
-    if (P.inner.size() > 1) return false;
+    if (P.inner.size() > 1) return decline("P.inner.size() > 1");
     if (P.inner.size() == 1) {
       const View &v = P.views[P.inner[0]];
-      if (v.keycols.size() > 2) return false;
-      if (v.count_bound * 4096.0 >= 16777216.0) return false;  // exact integral sums in FP32
+      if (v.keycols.size() > 2) return decline("v.keycols.size() > 2");
+      if (v.count_bound * 4096.0 >= 16777216.0) return decline("v.count_bound * 4096.0 >= 16777216.0");  // exact integral sums in FP32
     }
     auto &F = P.fast;
     F = PhysPlan::Fast{};
@@ -821,6 +828,14 @@ struct Planner {
     F.b3leaf = 1;
     bool b3_plain = false, b3_leafed = false;
     const int K = use_family ? (int)fam.filters.size() : 0;
+    // Items of a filter family grouped by inner codes go to the leaf-split view from the root
+    // to the inner relation (inner keys x leaves x columns; its float part in global memory
+    // when it does not fit a CTA), or with LMFAO_LEAF_ITEMS=cta to per-CTA (leaf, code) cells:
+    // one shared atomic per item and tuple instead of per column, which measured slower on
+    // the decision-tree level (5.5 ms against 3.3 ms at 84M tuples).
+    bool leaf_items_cta = false;
+    if (K > 1 && P.inner.size() == 1)
+      if (const char *e = std::getenv("LMFAO_LEAF_ITEMS")) leaf_items_cta = std::string(e) == "cta";
     for (const ItemD &it : items) {
       int j = mono_of(it.rowf);
       int vcol = it.ipart.empty() ? 0 : it.ipart[0].second;
@@ -830,13 +845,13 @@ struct Planner {
         all_row = all_row && g.src == 2;
       }
       if (it.leaf >= 0) {
-        if (!it.ig.empty() && all_view && !it.outer_dep && !it.ipart.empty()) {
+        if (!it.ig.empty() && all_view && !it.outer_dep && !it.ipart.empty() && !leaf_items_cta) {
           b3_leafed = true;
           pend.push_back({it, j, vcol, 3, -1});
-        } else if (!it.ig.empty() && all_row && !it.outer_dep) {
+        } else if (!it.ig.empty() && (all_row || (all_view && leaf_items_cta)) && !it.outer_dep) {
           pend.push_back({it, j, wcol_of(vcol), 4, -1});
         } else {
-          if (it.ig.size() > 1) return false;
+          if (it.ig.size() > 1) return decline("it.ig.size() > 1");
           // per-segment sums grouped by the tuple's filter index (and at most one inner code)
           DGroupRef lr{};
           lr.src = 4;
@@ -851,9 +866,9 @@ struct Planner {
             dom.push_back(dd);
             G *= dd;
           }
-          if (G > 4096) return false;
+          if (G > 4096) return decline("G > 4096");
           int set = find_or_add_b1(key, dom, G);
-          if (set < 0) return false;
+          if (set < 0) return decline("set < 0");
           ItemD it2 = it;
           it2.ig = key;
           it2.ig[0].stride = 0;  // the filter index selects; it is not an output group
@@ -873,7 +888,7 @@ struct Planner {
         pend.push_back({it, j, wcol_of(vcol), 0, -1});
         continue;
       }
-      if (it.ig.size() > 2) return false;
+      if (it.ig.size() > 2) return decline("it.ig.size() > 2");
       // B1 set keyed by its group references (without the query strides)
       std::vector<DGroupRef> key = it.ig;
       int64_t G = 1;
@@ -884,12 +899,12 @@ struct Planner {
         dom.push_back(d);
         G *= d;
       }
-      if (G > 4096) return false;
+      if (G > 4096) return decline("G > 4096");
       int set = find_or_add_b1(key, dom, G);
-      if (set < 0) return false;
+      if (set < 0) return decline("set < 0");
       pend.push_back({it, j, wcol_of(vcol), 1, set});
     }
-    if (b3_plain && b3_leafed) return false;
+    if (b3_plain && b3_leafed) return decline("b3_plain && b3_leafed");
     if (b3_leafed) F.b3leaf = K;
     // Lean variant: root-level monomials of degree <= 2 over at most 3 value columns and no
     // indicators. The monomial list becomes the full basis (1, x_i, x_i x_j) in the order
@@ -941,8 +956,8 @@ struct Planner {
         F.lean_cols = xcols;
       }
     }
-    if (F.monos.size() > FMAXM || F.wcols.size() > FMAXW) return false;
-    if (!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return false;
+    if (F.monos.size() > FMAXM || F.wcols.size() > FMAXW) return decline("F.monos.size() > FMAXM || F.wcols.size() > FMAXW");
+    if (!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return decline("!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())");
     int nfac = 0;
     std::set<int> xcols;
     for (auto &m : F.monos)
@@ -950,8 +965,8 @@ struct Planner {
         if (P.facs[f].ind) ++nfac;
         else xcols.insert(P.facs[f].col);
       }
-    if (nfac > FMAXF || (int)xcols.size() > FMAXX) return false;
-    if (P.inner.size() == 1 && P.views[P.inner[0]].nkeys * (int64_t)F.wcols.size() >= (int64_t(1) << 31)) return false;
+    if (nfac > FMAXF || (int)xcols.size() > FMAXX) return decline("nfac > FMAXF || (int)xcols.size() > FMAXX");
+    if (P.inner.size() == 1 && P.views[P.inner[0]].nkeys * (int64_t)F.wcols.size() >= (int64_t(1) << 31)) return decline("P.inner.size() == 1 && P.views[P.inner[0]].nkeys * (int64_t)F.wcols.size() >= (int64_t(1) ");
     const int nw = (int)F.wcols.size();
     for (auto &pd : pend) {
       const ItemD &it = pd.it;
@@ -966,7 +981,7 @@ struct Planner {
           for (size_t i = 0; i < F.int0.size(); ++i)
             if (F.int0[i].first == pd.j && F.int0[i].second == pd.w) pos = (int)i;
           if (pos < 0) {
-            if ((int)F.int0.size() >= NI0_MAX) return false;
+            if ((int)F.int0.size() >= NI0_MAX) return decline("(int)F.int0.size() >= NI0_MAX");
             F.int0.push_back({pd.j, pd.w});
             pos = (int)F.int0.size() - 1;
           }
@@ -992,7 +1007,7 @@ struct Planner {
         int pos = -1;
         for (size_t i = 0; i < cols.size(); ++i) if (cols[i].first == pd.j && cols[i].second == pd.w) pos = (int)i;
         if (pos < 0) {
-          if ((int)cols.size() >= FMAXC) return false;
+          if ((int)cols.size() >= FMAXC) return decline("(int)cols.size() >= FMAXC");
           cols.push_back({pd.j, pd.w});
           pos = (int)cols.size() - 1;
         }
@@ -1022,17 +1037,17 @@ struct Planner {
         b.out = it.out;
         b.cellmul = it.cellmul;
         F.b4.push_back(b);
-        if ((int)F.b4.size() > FMAXB4) return false;
+        if ((int)F.b4.size() > FMAXB4) return decline("(int)F.b4.size() > FMAXB4");
       } else {
         // the partial w_s * u_j is an exact integer when the monomial has only indicator
         // factors (or none): one integral column then serves integral and float items
         bool mono_int = true;
         for (int f : F.monos[pd.j]) mono_int = mono_int && P.facs[f].ind;
-        if (it.integral && !mono_int) return false;
+        if (it.integral && !mono_int) return decline("it.integral && !mono_int");
         int pos = -1;
         for (size_t i = 0; i < F.p3.size(); ++i) if (F.p3[i].first == pd.j && F.p3[i].second == mono_int) pos = (int)i;
         if (pos < 0) {
-          if ((int)F.p3.size() >= FMAXC) return false;
+          if ((int)F.p3.size() >= FMAXC) return decline("(int)F.p3.size() >= FMAXC");
           F.p3.push_back({pd.j, mono_int});
           pos = (int)F.p3.size() - 1;
         }
@@ -1080,7 +1095,7 @@ struct Planner {
           F.lean = false;
       for (auto &c : F.p3)
         if (c.second && c.first != 0) F.lean = false;
-      if (!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return false;
+      if (!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())) return decline("!F.lean && !fast_shape_ok((int)F.monos.size(), (int)F.wcols.size())");
     }
     F.on = true;
     return true;
@@ -1575,7 +1590,10 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
       d.b4_sel[i] = b.sel;
       d.b4_g0[i] = (int)g4.size();
       d.b4_ng[i] = (int)b.refs.size();
-      g4.insert(g4.end(), b.refs.begin(), b.refs.end());
+      for (DGroupRef g : b.refs) {
+        if (g.src == 3) g.b = code_pos(g.b);  // inner view code staged with the inner table
+        g4.push_back(g);
+      }
       d.b4_so[i] = it->second + (int)(b.out - gbase);
       d.b4_cellmul[i] = b.cellmul;
     }
@@ -3651,7 +3669,8 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
     for (size_t i = 0; i < P.inner.size(); ++i) o << (i ? "," : "") << nm(P.inner[i]);
     o << "],\"precision\":\"" << (P.fp64 ? "fp64" : P.split_bf16 ? "split_bf16" : "fp32") << "\",\"mode\":\""
       << (P.mode == LMFAO_MODE_PER_TUPLE ? "per_tuple" : P.fast.on ? "factorised" : "generic")
-      << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false")
+      << "\",\"specialised_pass\":" << (P.fast.on ? "true" : "false") << ",\"specialised_pass_declined\":\""
+      << json_escape(P.fast.on ? "" : P.fast_why) << "\""
       << ",\"lean_pass\":" << (P.fast.on && P.fast.lean ? "true" : "false")
       << ",\"block_combine\":" << (P.use_c3 ? "true" : "false") << ",\"prefix_digits\":" << P.prefix_len
       << ",\"block_combine_two_kernels\":" << (P.use_c5 ? "true" : "false") << ",\"contraction\":\""

@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512, 1) fast_pass_kerne
           bool okc = true;
           for (int g = d.b4_g0[i]; g < d.b4_g0[i] + d.b4_ng[i]; ++g) {
             const DGroupRef q = d.grefs4[g];
-            int code = row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
+            int code = (q.src == 3) ? codes[(int64_t)k * ncode + q.b]
+                                    : row_code(d.col[q.a], r, q.kind, d.thr + q.thr0, q.nthr);
             if (code < 0) okc = false;
             cell += (int64_t)code * q.stride;
           }

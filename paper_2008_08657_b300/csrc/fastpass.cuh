@@ -23,7 +23,7 @@ constexpr int FMAXC = 8;    // columns per B1 set / B3 columns
 constexpr int FMAXX = 6;    // root columns read per tuple (fact values and group columns)
 constexpr int FMAXFAM = 16; // filters of a filter family (disjoint conjunctions, e.g. tree leaves)
 constexpr int FMAXBIT = 32; // distinct predicates of a filter family
-constexpr int FMAXB4 = 64;  // items accumulated per CTA without segments
+constexpr int FMAXB4 = 256; // items accumulated per CTA without segments
 
 struct DFastB1 {
   int G;                 // cells of the group set

@@ -158,6 +158,7 @@ struct PhysPlan {
   DComb5 c5{};                     // two-kernel block combine (combine5.cu)
   bool use_c5 = false;
   std::string c5_why;              // why the two-kernel block combine does not run (if not)
+  std::string fast_why;            // why the specialised root pass declined the batch (if it did)
   int c3_grid = 0, c3_block = 512;
   DSegWeight sw{};
   int fp_grid = 0, fp_block = 256;
