@@ -143,6 +143,9 @@ typedef struct lmfao_plan_opts {
   const char *cost_model;   /* path of a learned cost model file (LEARNED), or NULL      */
   int32_t combine;          /* 0: automatic; 1: entry-wise combine; 2: prefix-block combine
                                when the plan allows it (results are the same)             */
+  int32_t learned_topk;     /* LEARNED: 0 or 1 takes the candidate of least predicted time;
+                               k > 1 times the k best-predicted candidates (among those
+                               whose checks pass) on the device and keeps the fastest     */
 } lmfao_plan_opts;
 
 typedef struct lmfao_plan_info {
@@ -310,6 +313,37 @@ typedef struct lmfao_cart_node {
 LMFAO_API int lmfao_cart_tree(struct lmfao_ctx *ctx, const char *target, const char *const *features, int nfeatures,
                               const float *thresholds, const int32_t *nthresholds, int depth,
                               const lmfao_plan_opts *opts, lmfao_cart_node *nodes, double *level_ms);
+
+/* Ridge linear regression over the join (Section 3, linear regression) from the aggregates
+ * of query `query_id` of the last run: the model theta_0 + sum_f theta_f x_f for the target y,
+ * minimising J(theta) = 1/(2|D|) SUM_D (theta^T x - y)^2 + lambda/2 |theta|^2 with x = (1,
+ * x_1 .. x_d). J and its gradient need only Sigma = SUM x x^T, SUM x y and SUM y^2, which the
+ * query must hold (ungrouped, unfiltered; COUNT, SUM(x_f), SUM(y), SUM(x_f x_g), SUM(x_f y),
+ * SUM(y^2) in any order, as the ridge batch of Section 3 does): a missing one gives
+ * LMFAO_ERR_ARG naming it. method LMFAO_RIDGE_CLOSED_FORM solves (Sigma_xx/|D| + lambda I)
+ * theta = Sigma_xy/|D| by Cholesky; LMFAO_RIDGE_BGD runs `iters` batch gradient steps of size
+ * `step` from theta = 0. Computed in FP64 on the device. theta (host, nfeatures + 1: intercept
+ * first), *loss = J(theta) and *grad_norm = |grad J(theta)| (either may be NULL). At most 126
+ * features. */
+enum { LMFAO_RIDGE_CLOSED_FORM = 0, LMFAO_RIDGE_BGD = 1 };
+LMFAO_API int lmfao_ridge_fit(struct lmfao_ctx *ctx, int query_id, const char *target, const char *const *features,
+                              int nfeatures, double lambda, int method, int iters, double step, double *theta,
+                              double *loss, double *grad_norm);
+
+/* COUNT GROUP BY gb over the natural join of the loaded relations, with the groups kept in
+ * hash tables in device memory: the group-bys of Rk-means (Section 3), SUM(1) GROUP BY X_j
+ * over the values of one attribute (step 1) and SUM(1) GROUP BY C_1, ..., C_n over the cells
+ * of a grid of cluster intervals (step 3), whose key spaces are too large for the dense
+ * result cells of a batch. Each group attribute is VALUE (a KEY or CAT attribute by its value;
+ * a CONT attribute by its FP32 value, reported as its 32-bit pattern; a U8 one by its value)
+ * or BUCKET (a CONT attribute by the number of thresholds strictly below it). The product of
+ * the attributes' domains (2^32 for an FP32 value) must stay below 2^62 (else
+ * LMFAO_ERR_UNSUPPORTED), and attributes of non-root relations must be determined by the join
+ * key toward the root. keys (device, cap x ngb int32 codes) and counts (device, cap int64)
+ * receive min(groups, cap) groups in no particular order; *ngroups (host) the number of
+ * groups. Independent of the batch and plan; synchronous on the context's stream. */
+LMFAO_API int lmfao_group_count(struct lmfao_ctx *ctx, const lmfao_groupby *gb, int ngb, int64_t cap, int32_t *keys,
+                                int64_t *counts, int64_t *ngroups);
 
 /* Allocation-free variant of lmfao_cart_variances (same arguments, same results), for
  * callers that cannot allocate device memory when they ask for split variances: a host

@@ -148,6 +148,9 @@ def _group_code(J, g):
         # bucket(x) = number of thresholds strictly below x (x == t lies in the <= side)
         t = np.asarray(thr, dtype=np.float32)
         return np.searchsorted(t, v.astype(np.float32), side="left").astype(np.int64)
+    if kind == "float":
+        # an FP32 value itself, as its 32-bit pattern (one group per distinct stored value)
+        return v.astype(np.float32).view(np.uint32).astype(np.int64)
     raise ValueError(f"unknown group-by kind {kind}")
 
 
@@ -408,3 +411,53 @@ def cart_tree(rels, target, features, thresholds, depth, processes=1):
                     paths[2 * v + c] = paths[v] + [(features[f], op, t)]
                     nodes[2 * v + c]["active"] = 1
     return nodes
+
+
+# ---------------------------------------------------------------------------------------
+# Ridge regression from the aggregates (Section 3, linear regression)
+# ---------------------------------------------------------------------------------------
+
+def ridge_system(result, query, target, features):
+    """(A, b, syy) of the ridge objective J(theta) = 1/(2|D|) SUM_D (theta^T x - y)^2 +
+    lambda/2 |theta|^2 without lambda: A = SUM x x^T / |D|, b = SUM x y / |D|, syy = SUM y^2 /
+    |D| with x = (1, features), read from the ungrouped query's aggregates by their factors."""
+    def key(agg):
+        k = {}
+        for a, fn, p in agg:
+            k[a] = k.get(a, 0) + (int(p) if fn == "pow" else 1)
+        return tuple(sorted(k.items()))
+    pos = {key(a): j for j, a in enumerate(query["aggs"])}
+    n = float(result["counts"][0])
+    z = [None] + list(features) + [target]
+    w = len(z)
+    M = np.zeros((w, w))
+    for i in range(w):
+        for j in range(w):
+            if i == 0 and j == 0:
+                M[i, j] = n
+                continue
+            k = {}
+            for a in (z[i], z[j]):
+                if a is not None:
+                    k[a] = k.get(a, 0) + 1
+            M[i, j] = result["sums"][0, pos[tuple(sorted(k.items()))]]
+    M /= n
+    m = w - 1
+    return M[:m, :m], M[:m, m], M[m, m]
+
+
+def ridge_closed_form(A, b, lam):
+    """theta with grad J = (A + lam I) theta - b = 0."""
+    return np.linalg.solve(A + lam * np.eye(len(b)), b)
+
+
+def ridge_bgd(A, b, lam, iters, step):
+    """Batch gradient descent on J from theta = 0: theta <- theta - step * grad J(theta)."""
+    th = np.zeros(len(b))
+    for _ in range(iters):
+        th = th - step * ((A + lam * np.eye(len(b))) @ th - b)
+    return th
+
+
+def ridge_objective(A, b, syy, lam, th):
+    return 0.5 * (th @ A @ th - 2 * th @ b + syy) + 0.5 * lam * th @ th

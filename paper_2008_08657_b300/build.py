@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblmfao.so")
 SOURCES = ["kernels.cu", "fastpass.cu", "combine.cu", "combine3.cu", "mlp.cu", "engine.cpp", "noalloc.cu",
-           "codegen.cpp", "codegen_family.cpp", "combine4.cu", "combine5.cu"]
+           "codegen.cpp", "codegen_family.cpp", "combine4.cu", "combine5.cu", "sparse.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(NVCC)), "lib64")  # NVRTC (plan-time code generation)
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

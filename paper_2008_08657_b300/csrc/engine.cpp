@@ -3404,12 +3404,19 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
         std::vector<int> order(cands.size());
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] < y[b]; });
+        // the model ranks; the first learned_topk candidates that pass their checks are timed
+        // (one of them only: no timing) and the fastest is kept
+        const int topk = std::max(1, o.learned_topk);
+        double bt = 1e300;
+        int measured = 0;
         for (int c : order) {
           build_plan(ctx, cand_opts(o, cands[c]), false, nullptr);
-          enqueue_run(ctx, *ctx->plan, ctx->tree, ctx->stream);
+          const double ms = topk > 1 ? time_plan(ctx, 1, 3) : (enqueue_run(ctx, *ctx->plan, ctx->tree, ctx->stream), 0.0);
           const bool ok = plan_checks_pass(ctx);
           drop_plan(ctx);
-          if (ok) { best = c; break; }
+          if (!ok) continue;
+          if (ms < bt) { bt = ms; best = c; }
+          if (++measured >= topk) break;
         }
         if (best < 0) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "no candidate plan passes its checks on this data");
         predicted = std::exp((double)y[best]);
@@ -3845,6 +3852,207 @@ int lmfao_cart_tree(lmfao_ctx *ctx, const char *target, const char *const *featu
     }
     drop_plan(ctx);
     ctx->queries.clear();
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_ridge_fit(lmfao_ctx *ctx, int query_id, const char *target, const char *const *features, int nfeatures,
+                    double lambda, int method, int iters, double step, double *theta, double *loss,
+                    double *grad_norm) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->ran || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
+    if (query_id < 0 || query_id >= (int)ctx->queries.size() || !target || !theta || nfeatures < 0 ||
+        (nfeatures && !features) || nfeatures > 126 || lambda < 0 || (method != LMFAO_RIDGE_CLOSED_FORM &&
+        method != LMFAO_RIDGE_BGD) || (method == LMFAO_RIDGE_BGD && (iters < 0 || !(step > 0))))
+      return fail(ctx, LMFAO_ERR_ARG, "bad ridge arguments");
+    const QueryIn &Q = ctx->queries[query_id];
+    if (!Q.gb.empty() || !Q.filters.empty())
+      return fail(ctx, LMFAO_ERR_ARG, "the ridge query must be ungrouped and unfiltered");
+    // canonical form of a product: attribute -> power
+    auto key_of = [](const std::vector<FactorIn> &fs) {
+      std::map<std::string, int> k;
+      for (const FactorIn &f : fs) k[f.attr] += f.fn == LMFAO_FN_POW ? f.param : 1;
+      return k;
+    };
+    std::map<std::map<std::string, int>, int> agg;
+    for (int a = 0; a < (int)Q.aggs.size(); ++a) agg.emplace(key_of(Q.aggs[a]), a);
+    std::vector<std::string> z{""};  // z_0 = 1 (the intercept)
+    for (int f = 0; f < nfeatures; ++f) {
+      if (!features[f]) return fail(ctx, LMFAO_ERR_ARG, "null feature name");
+      z.push_back(features[f]);
+    }
+    z.push_back(target);
+    const int d = nfeatures, w = d + 2;
+    std::vector<int> zmap((size_t)w * w, -1);
+    const QueryOut &qo = ctx->plan->qout[query_id];
+    for (int i = 0; i < w; ++i)
+      for (int j = 0; j < w; ++j) {
+        if (i == 0 && j == 0) continue;  // the COUNT of the (single) group
+        std::map<std::string, int> k;
+        if (i) k[z[i]] += 1;
+        if (j) k[z[j]] += 1;
+        auto it = agg.find(k);
+        if (it == agg.end() || qo.integral[it->second]) {
+          std::string name;
+          for (auto &kv : k) name += (name.empty() ? "" : " * ") + kv.first + (kv.second > 1 ? "^2" : "");
+          return fail(ctx, LMFAO_ERR_ARG, "the ridge query has no SUM(" + name + ")");
+        }
+        zmap[(size_t)i * w + j] = it->second;
+      }
+    check_device_flags(ctx);
+    PhysPlan &P = *ctx->plan;
+    int *dz = P.arena.upload(zmap, ctx->stream);
+    double *dout = (double *)P.arena.alloc((size_t)(d + 3) * 8);
+    launch_ridge(P.icnt, P.fsum, qo.io, qo.fo, dz, d, lambda, method, iters, step, dout, ctx->stream);
+    LMFAO_CUDA(cudaGetLastError());
+    std::vector<double> out(d + 3);
+    LMFAO_CUDA(cudaMemcpyAsync(out.data(), dout, out.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i <= d; ++i) theta[i] = out[i];
+    if (loss) *loss = out[d + 1];
+    if (grad_norm) *grad_norm = out[d + 2];
+    return LMFAO_OK;
+  });
+}
+
+int lmfao_group_count(lmfao_ctx *ctx, const lmfao_groupby *gb, int ngb, int64_t cap, int32_t *keys, int64_t *counts,
+                      int64_t *ngroups) {
+  return guarded(ctx, [&]() -> int {
+    if (ctx->device < 0) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "host-only context");
+    if (ctx->rels.empty()) return fail(ctx, LMFAO_ERR_ARG, "no relations loaded");
+    if (!gb || ngb < 1 || ngb > GC_MAXATTR || cap < 0 || (cap > 0 && (!keys || !counts)) || !ngroups)
+      return fail(ctx, LMFAO_ERR_ARG, "bad group-count arguments");
+    cudaStream_t s = ctx->stream;
+    lmfao_plan_opts o = default_opts();
+    const std::vector<int> par = parent_links(ctx, o);
+    const JoinTree t = build_tree(ctx, par, largest_relation(ctx));
+    // group attributes: home relation, code kind and domain
+    struct Attr { int rel, col, kind, nthr; int64_t dom, radix; float *thr; };
+    std::vector<Attr> at(ngb);
+    std::vector<void *> tmp;
+    auto dalloc = [&](size_t bytes) {
+      void *p = nullptr;
+      LMFAO_CUDA(cudaMalloc(&p, std::max<size_t>(bytes, 16)));
+      tmp.push_back(p);
+      return p;
+    };
+    struct Free {  // temporaries of this call
+      std::vector<void *> &v;
+      ~Free() {
+        for (void *p : v) cudaFree(p);
+      }
+    } free_tmp{tmp};
+    for (int i = 0; i < ngb; ++i) {
+      if (!gb[i].attr) return fail(ctx, LMFAO_ERR_ARG, "null group attribute");
+      Attr &a = at[i];
+      a.rel = home_of(ctx, t, gb[i].attr);
+      a.col = ctx->rels[a.rel].col(gb[i].attr);
+      const Column &c = ctx->rels[a.rel].cols[a.col];
+      a.thr = nullptr;
+      a.nthr = 0;
+      if (gb[i].kind == LMFAO_GB_VALUE) {
+        if (c.role != LMFAO_CONT) { a.kind = 0; a.dom = c.domain; }
+        else if (c.dtype == LMFAO_U8) { a.kind = 0; a.dom = 256; }
+        else { a.kind = 2; a.dom = int64_t(1) << 32; }  // the FP32 value itself (its bit pattern)
+      } else if (gb[i].kind == LMFAO_GB_BUCKET) {
+        if (gb[i].nthresholds < 0 || (gb[i].nthresholds && !gb[i].thresholds)) return fail(ctx, LMFAO_ERR_ARG, "bad thresholds");
+        for (int k = 1; k < gb[i].nthresholds; ++k)
+          if (!(gb[i].thresholds[k - 1] < gb[i].thresholds[k])) return fail(ctx, LMFAO_ERR_ARG, "thresholds must be strictly ascending");
+        a.kind = 1;
+        a.nthr = gb[i].nthresholds;
+        a.dom = a.nthr + 1;
+        a.thr = (float *)dalloc((size_t)a.nthr * 4);
+        if (a.nthr) LMFAO_CUDA(cudaMemcpyAsync(a.thr, gb[i].thresholds, (size_t)a.nthr * 4, cudaMemcpyHostToDevice, s));
+      } else return fail(ctx, LMFAO_ERR_ARG, "unknown group-by kind");
+    }
+    double total = 1;
+    for (int i = ngb - 1; i >= 0; --i) {
+      at[i].radix = (int64_t)total;
+      total *= (double)at[i].dom;
+    }
+    if (total > 4.6e18) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "the group key does not fit 62 bits");
+    auto fill_cols = [&](DGcRel &d, int r) {
+      const Relation &R = ctx->rels[r];
+      if ((int)R.cols.size() > GC_MAXCOL) throw Error(LMFAO_ERR_UNSUPPORTED, "relation with more than 32 columns");
+      d.nrows = R.nrows;
+      for (size_t c = 0; c < R.cols.size(); ++c) d.col[c] = dcol(R.cols[c]);
+      d.nattr = 0;
+      for (const Attr &a : at)
+        if (a.rel == r) d.attr[d.nattr++] = DGcAttr{a.kind, a.col, a.nthr, a.thr, a.radix};
+    };
+    // the join key of relation r toward relation p: columns of `side` and mixed-radix strides
+    auto join_key = [&](int r, int p, int side, int *kcol, int64_t *kstride) {
+      const std::vector<std::string> sh = shared_attrs(ctx, r, p);
+      if (sh.empty() || (int)sh.size() > MAXK) throw Error(LMFAO_ERR_UNSUPPORTED, "join key of 0 or more than 4 attributes");
+      int64_t nk = 1;
+      for (int i = (int)sh.size() - 1; i >= 0; --i) {
+        const Column &c = ctx->rels[r].cols[ctx->rels[r].col(sh[i])];
+        if (c.role == LMFAO_CONT) throw Error(LMFAO_ERR_UNSUPPORTED, "join on a value attribute");
+        kcol[i] = ctx->rels[side].col(sh[i]);
+        kstride[i] = nk;
+        nk *= c.domain;
+        if (nk > (int64_t(1) << 28)) throw Error(LMFAO_ERR_UNSUPPORTED, "join key domain above 2^28");
+      }
+      return std::make_pair((int)sh.size(), nk);
+    };
+    std::vector<unsigned long long *> vcnt(ctx->rels.size(), nullptr);
+    std::vector<long long *> vcode(ctx->rels.size(), nullptr);
+    int *err = (int *)dalloc(4);
+    LMFAO_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    auto add_children = [&](DGcRel &d, int r) {
+      d.nchild = 0;
+      for (int c : t.children[r]) {
+        if (d.nchild >= MAXCH) throw Error(LMFAO_ERR_UNSUPPORTED, "more than 8 children");
+        DGcChild &ch = d.child[d.nchild++];
+        ch.nk = join_key(c, r, r, ch.kcol, ch.kstride).first;
+        ch.cnt = vcnt[c];
+        ch.code = vcode[c];
+      }
+    };
+    for (int r : t.post) {
+      DGcRel d{};
+      fill_cols(d, r);
+      const auto k = join_key(r, t.parent[r], r, d.kcol, d.kstride);
+      d.nk = k.first;
+      add_children(d, r);
+      vcnt[r] = (unsigned long long *)dalloc((size_t)k.second * 8);
+      vcode[r] = (long long *)dalloc((size_t)k.second * 8);
+      LMFAO_CUDA(cudaMemsetAsync(vcnt[r], 0, (size_t)k.second * 8, s));
+      LMFAO_CUDA(cudaMemsetAsync(vcode[r], 0xff, (size_t)k.second * 8, s));
+      d.cnt = vcnt[r];
+      d.code = vcode[r];
+      launch_gc_view(d, err, s);
+    }
+    // the global table: twice the largest possible number of groups, rounded up to 2^k
+    const double most = std::min<double>(total, (double)std::max<int64_t>(1, ctx->rels[t.root].nrows));
+    int64_t slots = 1024;
+    while ((double)slots < 2 * most && slots < (int64_t(1) << 28)) slots *= 2;
+    unsigned long long *gk = (unsigned long long *)dalloc((size_t)slots * 8);
+    unsigned long long *gc = (unsigned long long *)dalloc((size_t)slots * 8);
+    LMFAO_CUDA(cudaMemsetAsync(gk, 0xff, (size_t)slots * 8, s));
+    LMFAO_CUDA(cudaMemsetAsync(gc, 0, (size_t)slots * 8, s));
+    DGcRel d{};
+    fill_cols(d, t.root);
+    add_children(d, t.root);
+    launch_gc_root(d, gk, gc, (unsigned long long)(slots - 1), err, s);
+    DGcOut out{};
+    out.ngb = ngb;
+    for (int i = 0; i < ngb; ++i) out.radix[i] = at[i].radix;
+    out.cap = cap;
+    out.keys = keys;
+    out.counts = counts;
+    unsigned long long *nout = (unsigned long long *)dalloc(8);
+    LMFAO_CUDA(cudaMemsetAsync(nout, 0, 8, s));
+    launch_gc_compact(gk, gc, slots, out, nout, s);
+    LMFAO_CUDA(cudaGetLastError());
+    int e = 0;
+    unsigned long long n = 0;
+    LMFAO_CUDA(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
+    LMFAO_CUDA(cudaMemcpyAsync(&n, nout, 8, cudaMemcpyDeviceToHost, s));
+    LMFAO_CUDA(cudaStreamSynchronize(s));
+    if (e & 1) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "a group attribute of a non-root relation is not determined by its join key");
+    if (e & 4) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "more groups than the hash table holds");
+    *ngroups = (int64_t)n;
     return LMFAO_OK;
   });
 }

@@ -543,6 +543,97 @@ __global__ void __launch_bounds__(256) cart_split_kernel(const unsigned long lon
   }
 }
 
+// Ridge regression from the aggregates of one query (Section 3, linear regression): z = (1,
+// x_1 .. x_d, y); zmap[i * (d + 2) + j] is the aggregate of SUM(z_i z_j) (-1: the COUNT).
+// A = SUM(x x^T) / n + lambda I, b = SUM(x y) / n (x = z_0 .. z_d); the closed form solves
+// A theta = b by Cholesky; batch gradient descent takes `iters` steps theta -= step * (A theta - b)
+// from theta = 0. out: theta (d + 1), then J(theta), then |A theta - b|. One CTA, FP64.
+__global__ void __launch_bounds__(256) ridge_kernel(const unsigned long long *icnt, const double *fsum,
+                                                    int64_t io, int64_t fo, const int *zmap, int d, double lambda,
+                                                    int method, int iters, double step, double *out) {
+  extern __shared__ double rs[];
+  const int m = d + 1, w = d + 2, tid = threadIdx.x, bs = blockDim.x;
+  double *A = rs;            // m x m
+  double *L = A + m * m;     // m x m (Cholesky factor)
+  double *b = L + m * m;     // m
+  double *th = b + m;        // m
+  double *g = th + m;        // m
+  double *syy = g + m;       // 1
+  const double n = (double)icnt[io];
+  for (int idx = tid; idx < w * w; idx += bs) {
+    const int i = idx / w, j = idx - i * w;
+    const int a = zmap[idx];
+    const double v = a < 0 ? n : fsum[fo + a];
+    if (i < m && j < m) A[i * m + j] = v / n + (i == j ? lambda : 0.0);
+    else if (i < m && j == m) b[i] = v / n;
+    else if (i == m && j == m) syy[0] = v / n;
+  }
+  for (int i = tid; i < m; i += bs) th[i] = 0.0;
+  __syncthreads();
+  if (method == 0) {
+    // Cholesky A = L L^T, column by column
+    for (int i = tid; i < m * m; i += bs) L[i] = 0.0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+      if (tid == 0) {
+        double s = A[k * m + k];
+        for (int p = 0; p < k; ++p) s -= L[k * m + p] * L[k * m + p];
+        L[k * m + k] = sqrt(s > 0 ? s : 0.0);
+      }
+      __syncthreads();
+      for (int i = k + 1 + tid; i < m; i += bs) {
+        double s = A[i * m + k];
+        for (int p = 0; p < k; ++p) s -= L[i * m + p] * L[k * m + p];
+        L[i * m + k] = L[k * m + k] > 0 ? s / L[k * m + k] : 0.0;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {  // L u = b, then L^T theta = u
+      for (int i = 0; i < m; ++i) {
+        double s = b[i];
+        for (int p = 0; p < i; ++p) s -= L[i * m + p] * g[p];
+        g[i] = L[i * m + i] > 0 ? s / L[i * m + i] : 0.0;
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int p = i + 1; p < m; ++p) s -= L[p * m + i] * th[p];
+        th[i] = L[i * m + i] > 0 ? s / L[i * m + i] : 0.0;
+      }
+    }
+    __syncthreads();
+  } else {
+    for (int it = 0; it < iters; ++it) {
+      for (int i = tid; i < m; i += bs) {
+        double s = -b[i];
+        for (int j = 0; j < m; ++j) s += A[i * m + j] * th[j];
+        g[i] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += bs) th[i] -= step * g[i];
+      __syncthreads();
+    }
+  }
+  // gradient and objective at theta: J = (theta^T (A - lambda I) theta - 2 theta^T b + syy) / 2
+  //                                      + lambda / 2 |theta|^2 = (theta^T A theta - 2 theta^T b + syy) / 2
+  for (int i = tid; i < m; i += bs) {
+    double s = -b[i];
+    for (int j = 0; j < m; ++j) s += A[i * m + j] * th[j];
+    g[i] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double q = 0, tb = 0, gn = 0;
+    for (int i = 0; i < m; ++i) {
+      q += th[i] * (g[i] + b[i]);
+      tb += th[i] * b[i];
+      gn += g[i] * g[i];
+    }
+    for (int i = 0; i < m; ++i) out[i] = th[i];
+    out[m] = 0.5 * (q - 2.0 * tb + syy[0]);
+    out[m + 1] = sqrt(gn);
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 static int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
@@ -662,6 +753,14 @@ void launch_cart_split(const unsigned long long *icnt, const double *fsum, const
                        int nnodes, int2 *best, double *score, double *stats, cudaStream_t s) {
   if (nnodes == 0) return;
   cart_split_kernel<<<nnodes, 256, 0, s>>>(icnt, fsum, qdesc, qbeg, best, score, stats);
+}
+
+void launch_ridge(const unsigned long long *icnt, const double *fsum, int64_t io, int64_t fo, const int *zmap, int d,
+                  double lambda, int method, int iters, double step, double *out, cudaStream_t s) {
+  const int m = d + 1;
+  const size_t smem = (size_t)(2 * m * m + 3 * m + 1) * sizeof(double);
+  cudaFuncSetAttribute(ridge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ridge_kernel<<<1, 256, smem, s>>>(icnt, fsum, io, fo, zmap, d, lambda, method, iters, step, out);
 }
 
 void launch_results(const unsigned long long *icnt, const double *fsum, int64_t cells, int naggs, const int *integral,

@@ -230,6 +230,8 @@ void launch_cart_variances(const unsigned long long *icnt, const double *fsum, c
                            int n, int nb_max, double *out, cudaStream_t s);
 void launch_cart_split(const unsigned long long *icnt, const double *fsum, const int64_t *qdesc, const int *qbeg,
                        int nnodes, int2 *best, double *score, double *stats, cudaStream_t s);
+void launch_ridge(const unsigned long long *icnt, const double *fsum, int64_t io, int64_t fo, const int *zmap, int d,
+                  double lambda, int method, int iters, double step, double *out, cudaStream_t s);
 void launch_results(const unsigned long long *icnt, const double *fsum, int64_t cells, int naggs,
                     const int *integral, int64_t *counts, double *sums, cudaStream_t s);
 
@@ -309,5 +311,47 @@ struct DComb5 {
 size_t combine5_smem(const DComb5 &d, bool fp64);
 void launch_combine5_z(const DComb5 &d, bool fp64, cudaStream_t s);
 void launch_combine5_entries(const DComb5 &d, bool fp64, cudaStream_t s);
+
+// COUNT GROUP BY with hash-table results (sparse.cu).
+constexpr int GC_MAXATTR = 16;   // group attributes
+constexpr int GC_MAXCOL = 32;    // columns of a relation visible to the kernels
+struct DGcAttr {                 // a group attribute homed at the relation being scanned
+  int kind;                      // 0: key / categorical value, 1: bucket, 2: FP32 bit pattern
+  int col, nthr;
+  const float *thr;
+  int64_t radix;                 // weight of its code in the group key
+};
+struct DGcChild {                // the partial view of a child relation
+  int nk;
+  int kcol[MAXK];
+  int64_t kstride[MAXK];
+  const unsigned long long *cnt; // multiplicity per join key
+  const long long *code;         // group-key part per join key (-1: no row)
+};
+struct DGcRel {
+  int64_t nrows;
+  DCol col[GC_MAXCOL];
+  int nk;                        // the join key toward the parent (non-root relations)
+  int kcol[MAXK];
+  int64_t kstride[MAXK];
+  int nchild;
+  DGcChild child[MAXCH];
+  int nattr;
+  DGcAttr attr[GC_MAXATTR];
+  unsigned long long *cnt;       // output partial view (non-root relations)
+  long long *code;
+};
+struct DGcOut {
+  int ngb;
+  int64_t radix[GC_MAXATTR];
+  int64_t cap;
+  int32_t *keys;                 // cap x ngb group codes
+  int64_t *counts;               // cap
+};
+void launch_gc_view(const DGcRel &d, int *err, cudaStream_t s);
+void launch_gc_root(const DGcRel &d, unsigned long long *gkeys, unsigned long long *gcnts, unsigned long long gmask,
+                    int *err, cudaStream_t s);
+void launch_gc_compact(const unsigned long long *gkeys, const unsigned long long *gcnts, int64_t slots, const DGcOut &o,
+                       unsigned long long *nout, cudaStream_t s);
 
 }  // namespace lmfao

@@ -36,7 +36,7 @@ ENTRY_POINTS = [
     "lmfao_describe_plan", "lmfao_cart_variances", "lmfao_kernel_times", "lmfao_kernel_name",
     "lmfao_set_profiling", "lmfao_cart_variances_noalloc", "lmfao_mlp_param_count", "lmfao_mlp_forward",
     "lmfao_mlp_loss", "lmfao_mlp_backward", "lmfao_mlp_adam", "lmfao_plan_candidates", "lmfao_result_state",
-    "lmfao_cart_tree",
+    "lmfao_cart_tree", "lmfao_ridge_fit", "lmfao_group_count",
 ]
 COST_MODEL_PATH = os.path.join(_HERE, "cost_model.txt")
 
@@ -67,7 +67,7 @@ class PlanOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("planner", C.c_int32), ("root_rel", C.c_int32),
                 ("segment_rel", C.c_int32), ("mode", C.c_int32), ("autotune", C.c_int32),
                 ("join_parent", C.POINTER(C.c_int32)), ("query_root", C.POINTER(C.c_int32)),
-                ("cost_model", C.c_char_p), ("combine", C.c_int32)]
+                ("cost_model", C.c_char_p), ("combine", C.c_int32), ("learned_topk", C.c_int32)]
 
 
 class PlanInfo(C.Structure):
@@ -133,6 +133,10 @@ def library():
             "lmfao_mlp_loss": (C.c_int, [P, P, C.c_int, P, P, P]),
             "lmfao_mlp_backward": (C.c_int, [P, C.c_int, C.c_int, P, P, P, P, P, P]),
             "lmfao_mlp_adam": (C.c_int, [P, P, P, P, C.c_int64, C.c_int, C.c_float, P]),
+            "lmfao_group_count": (C.c_int, [P, C.POINTER(GroupBy), C.c_int, C.c_int64, P, P, C.POINTER(C.c_int64)]),
+            "lmfao_ridge_fit": (C.c_int, [P, C.c_int, C.c_char_p, C.POINTER(C.c_char_p), C.c_int, C.c_double, C.c_int,
+                                          C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]),
             "lmfao_cart_tree": (C.c_int, [P, C.c_char_p, C.POINTER(C.c_char_p), C.c_int, C.POINTER(C.c_float),
                                           C.POINTER(C.c_int32), C.c_int, C.POINTER(PlanOpts), C.POINTER(CartNode),
                                           C.POINTER(C.c_double)]),
@@ -280,8 +284,9 @@ class Engine:
 
     # ------------------------------------------------------------------ plan / run / fetch
     def plan(self, precision="fp32", planner="heuristic", root=None, segment="default", mode="auto",
-             join_parent=None, query_roots=None, autotune=False, cost_model=None, combine="auto"):
+             join_parent=None, query_roots=None, autotune=False, cost_model=None, combine="auto", learned_topk=1):
         o = PlanOpts()
+        o.learned_topk = int(learned_topk)
         o.precision = PRECISION[precision]
         forced = root is not None or segment != "default" or planner == "forced"
         o.planner = PLANNER["forced" if forced and planner == "heuristic" else planner]
@@ -396,6 +401,42 @@ class Engine:
         arr = (C.c_int * len(qids))(*[int(q) for q in qids])
         self._check(self.lib.lmfao_cart_variances(self.ctx, arr, len(qids), C.c_void_p(out.data_ptr()),
                                                   _stream_handle(stream)))
+
+    def group_count(self, groupby, cap):
+        """COUNT GROUP BY ``groupby`` (list of (attr, "value"|"bucket", thresholds)) with hash-table
+        results (lmfao_group_count). Returns (codes: n x ngb int64, counts: n int64, groups) with
+        n = min(groups, cap); FP32 values come back as their 32-bit patterns (non-negative)."""
+        import torch
+        keep = []
+        gbs = (GroupBy * len(groupby))()
+        for i, (attr, kind, thr) in enumerate(groupby):
+            b = attr.encode()
+            keep.append(b)
+            if kind == "bucket":
+                t = np.ascontiguousarray(np.asarray(thr, dtype=np.float32))
+                keep.append(t)
+                gbs[i] = GroupBy(b, GB_BUCKET, len(t), t.ctypes.data_as(C.POINTER(C.c_float)))
+            else:
+                gbs[i] = GroupBy(b, GB_VALUE, 0, None)
+        keys = torch.empty((max(1, cap), len(groupby)), dtype=torch.int32, device="cuda")
+        counts = torch.empty(max(1, cap), dtype=torch.int64, device="cuda")
+        n = C.c_int64()
+        self._check(self.lib.lmfao_group_count(self.ctx, gbs, len(groupby), int(cap), C.c_void_p(keys.data_ptr()),
+                                               C.c_void_p(counts.data_ptr()), C.byref(n)))
+        m = min(n.value, cap)
+        k = keys[:m].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+        return k, counts[:m].cpu().numpy(), n.value
+
+    def ridge_fit(self, qid, target, features, lam, method="closed_form", iters=0, step=0.0):
+        """Ridge regression from query ``qid``'s aggregates (lmfao_ridge_fit). Returns
+        (theta with the intercept first, J(theta), |grad J(theta)|)."""
+        names = (C.c_char_p * max(1, len(features)))(*[f.encode() for f in features])
+        th = (C.c_double * (len(features) + 1))()
+        loss, gn = C.c_double(), C.c_double()
+        self._check(self.lib.lmfao_ridge_fit(self.ctx, int(qid), target.encode(), names, len(features), float(lam),
+                                             {"closed_form": 0, "bgd": 1}[method], int(iters), float(step), th,
+                                             C.byref(loss), C.byref(gn)))
+        return np.array(th[:]), loss.value, gn.value
 
     def cart_tree(self, target, features, thresholds, depth, precision="fp32"):
         """Grow a regression tree (lmfao_cart_tree). ``thresholds``: dict or list of ascending

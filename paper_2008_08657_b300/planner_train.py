@@ -189,34 +189,27 @@ def regrets(data, models, mean, std):
     return np.array(rl), np.array(rh)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--schemas", type=int, default=300)
-    ap.add_argument("--train", type=int, default=200)
-    ap.add_argument("--fact-min", type=float, default=1e5)
-    ap.add_argument("--fact-max", type=float, default=5e6)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--out", default="planner_out")
-    args = ap.parse_args()
-    os.makedirs(args.out, exist_ok=True)
-    t0 = time.time()
-    data = collect(range(args.schemas), (args.fact_min, args.fact_max), log=print)
-    t1 = time.time()
-    np.savez_compressed(os.path.join(args.out, "planner_data.npz"),
-                        **{f"{k}_{i}": v for i, d in enumerate(data) for k, v in d.items()
-                           if isinstance(v, np.ndarray)},
-                        t_heur=np.array([d["t_heur"] for d in data]),
-                        seeds=np.array([d["seed"] for d in data]))
-    tr, te = data[:args.train], data[args.train:]
-    models, mean, std, info = train(tr, max_steps=args.steps)
-    save_model(os.path.join(args.out, "cost_model.txt"), models, mean, std)
+def topk_regrets(data, models, mean, std, k):
+    """Per schema: regret of timing the k best-predicted candidates (that pass their checks)
+    and keeping the fastest, the LEARNED planner with learned_topk = k."""
+    r = []
+    for d in data:
+        t = d["times"]
+        ok = np.isfinite(t)
+        if not ok.any():
+            continue
+        pred = predict(models, d["feats"], mean, std)
+        pred[~ok] = np.inf
+        picks = [int(c) for c in np.argsort(pred, kind="stable")[:k] if ok[c]]
+        r.append(min(t[c] for c in picks) / t[ok].min() - 1.0)
+    return np.array(r)
+
+
+def summarise(tr, te, models, mean, std, extra):
     rl, rh = regrets(te, models, mean, std)
     rl_tr, rh_tr = regrets(tr, models, mean, std)
-    res = {
-        "schemas": args.schemas, "train": len(tr), "test": len(te),
-        "fact_rows_range": [args.fact_min, args.fact_max],
-        "candidates_per_schema": float(np.mean([len(d["cands"]) for d in data])),
-        "collect_seconds": t1 - t0, "training": info, "ensemble": len(models),
+    res = dict(extra)
+    res.update({
         "test_regret_learned_mean": float(rl.mean()), "test_regret_learned_median": float(np.median(rl)),
         "test_regret_learned_p90": float(np.quantile(rl, 0.9)),
         "test_regret_heuristic_mean": float(rh[np.isfinite(rh)].mean()),
@@ -227,9 +220,78 @@ def main():
         "test_within_10pct_heuristic": float(np.mean(rh <= 0.10)),
         "train_regret_learned_mean": float(rl_tr.mean()),
         "train_regret_heuristic_mean": float(rh_tr[np.isfinite(rh_tr)].mean()),
-    }
+        "test_regret_learned_topk": {},
+    })
+    for k in (2, 3, 4, 5):
+        rk = topk_regrets(te, models, mean, std, k)
+        res["test_regret_learned_topk"][str(k)] = {
+            "mean": float(rk.mean()), "median": float(np.median(rk)), "p90": float(np.quantile(rk, 0.9)),
+            "within_10pct": float(np.mean(rk <= 0.10)),
+            "candidates_timed_fraction": float(np.mean([min(k, np.isfinite(d["times"]).sum()) / len(d["times"])
+                                                        for d in te]))}
+    return res
+
+
+def load_data(path):
+    z = np.load(path)
+    out = []
+    for i, seed in enumerate(z["seeds"]):
+        out.append({"seed": int(seed), "cands": z[f"cands_{i}"], "feats": z[f"feats_{i}"], "times": z[f"times_{i}"],
+                    "t_heur": float(z["t_heur"][i])})
+    return out
+
+
+def install(out):
+    """Copy the trained model and its results into the package (the installed cost model)."""
+    import shutil
+    here = os.path.dirname(os.path.abspath(__file__))
+    shutil.copy(os.path.join(out, "cost_model.txt"), COST_MODEL_PATH)
+    shutil.copy(os.path.join(out, "planner_results.json"), os.path.join(here, "planner_results.json"))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--schemas", type=int, default=300)
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--fact-min", type=float, default=1e5)
+    ap.add_argument("--fact-max", type=float, default=5e6)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--out", default="planner_out")
+    ap.add_argument("--evaluate", action="store_true",
+                    help="recompute the results of the data and model already in --out (no measurement)")
+    ap.add_argument("--install", action="store_true",
+                    help="copy the model and its results into the package as the installed cost model")
+    args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    if args.evaluate:
+        data = load_data(os.path.join(args.out, "planner_data.npz"))
+        models, mean, std = load_model(os.path.join(args.out, "cost_model.txt"))
+        with open(os.path.join(args.out, "planner_results.json")) as f:
+            old = json.load(f)
+        keep = {k: old[k] for k in ("schemas", "train", "test", "fact_rows_range", "candidates_per_schema",
+                                    "collect_seconds", "training", "ensemble") if k in old}
+        res = summarise(data[:args.train], data[args.train:], models, mean, std, keep)
+    else:
+        t0 = time.time()
+        data = collect(range(args.schemas), (args.fact_min, args.fact_max), log=print)
+        t1 = time.time()
+        np.savez_compressed(os.path.join(args.out, "planner_data.npz"),
+                            **{f"{k}_{i}": v for i, d in enumerate(data) for k, v in d.items()
+                               if isinstance(v, np.ndarray)},
+                            t_heur=np.array([d["t_heur"] for d in data]),
+                            seeds=np.array([d["seed"] for d in data]))
+        tr, te = data[:args.train], data[args.train:]
+        models, mean, std, info = train(tr, max_steps=args.steps)
+        save_model(os.path.join(args.out, "cost_model.txt"), models, mean, std)
+        res = summarise(tr, te, models, mean, std, {
+            "schemas": args.schemas, "train": len(tr), "test": len(te),
+            "fact_rows_range": [args.fact_min, args.fact_max],
+            "candidates_per_schema": float(np.mean([len(d["cands"]) for d in data])),
+            "collect_seconds": t1 - t0, "training": info, "ensemble": len(models)})
     with open(os.path.join(args.out, "planner_results.json"), "w") as f:
         json.dump(res, f, indent=1)
+    if args.install:
+        install(args.out)
     print(json.dumps(res))
 
 

@@ -322,3 +322,18 @@ def test_chunked_evaluation_equals_the_whole_join(processes):
             np.testing.assert_array_equal(a["keys"], b["keys"])
             np.testing.assert_array_equal(a["counts"], b["counts"])
             np.testing.assert_allclose(a["sums"], b["sums"], rtol=1e-12, atol=1e-12)
+
+
+def test_group_by_fp32_value_counts_each_stored_value():
+    """Rk-means step 1 groups by the values of a continuous attribute: one group per distinct
+    stored FP32 value (its bit pattern), counted over the brute-force join."""
+    rels = W.tiny_schema(7, max_rows=10, empty_ok=False)
+    q = {"aggs": [[]], "groupby": [("x1", "float", None), ("k1", "value", None)], "filters": []}
+    res = O.evaluate(rels, [q])[0]
+    want = {}
+    for r in materialise(rels):
+        bits = int(np.array([r["x1"]], dtype=np.float32).view(np.uint32)[0])
+        key = (bits, int(r["k1"]))
+        want[key] = want.get(key, 0) + 1
+    got = {(int(k[0]), int(k[1])): int(c) for k, c in zip(res["keys"], res["counts"])}
+    assert got == want and len(got) > 1
