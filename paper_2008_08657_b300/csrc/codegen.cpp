@@ -11,7 +11,9 @@
 //     (monomial, view column), one shared atomic per histogram set and per root-to-inner
 //     column, with every index a constant;
 //   * a work item's full 4-tuple quads are read with 16-byte loads and no range checks; the
-//     at most 6 tuples of its ragged head and tail are taken by single lanes.
+//     at most 6 tuples of its ragged head and tail are taken by single lanes;
+//   * work-item tickets are taken one item ahead, so the next item's record is requested when
+//     the current item starts and its weight and first quad while the segment sums are reduced.
 #include "codegen.h"
 
 #include <nvrtc.h>
@@ -237,19 +239,33 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   if (d.lanes) {
     // one tuple per lane and step: tuple r0 + lane + 32 i; the next step's key and values are
     // loaded while the current tuple is processed (coalesced 4-byte loads, no ragged edges)
-    auto lane_load = [&](const std::string &r, const std::string &ind) {
-      if (s.ni) o << ind << "kn = kc[" << r << "];\n";
-      for (int i = 0; i < s.nx; ++i) o << ind << "xn" << i << " = (T)xc" << i << "[" << r << "];\n";
+    // a ring of D steps in flight per lane: slot j holds tuple r + 32 j
+    const int D = 4;
+    auto lane_load_slot = [&](int j, const std::string &r, const std::string &ind) {
+      if (s.ni) o << ind << "kn" << j << " = kc[" << r << "];\n";
+      for (int i = 0; i < s.nx; ++i) o << ind << "xn" << i << "_" << j << " = (T)xc" << i << "[" << r << "];\n";
     };
-    if (s.ni) o << "  int kn = 0;\n";
-    for (int i = 0; i < s.nx; ++i) o << "  T xn" << i << " = (T)0;\n";
+    auto lane_fill = [&](const std::string &base, const std::string &end, const std::string &ind) {
+      for (int j = 0; j < D; ++j) {
+        o << ind << "if (" << base << " + " << 32 * j << " < " << end << ") {\n";
+        lane_load_slot(j, base + " + " + std::to_string(32 * j), ind + "  ");
+        o << ind << "}\n";
+      }
+    };
+    for (int j = 0; j < D; ++j) {
+      if (s.ni) o << "  int kn" << j << " = 0;\n";
+      for (int i = 0; i < s.nx; ++i) o << "  T xn" << i << "_" << j << " = (T)0;\n";
+    }
     o << "  long long r = wk.r0 + lane;\n";
-    o << "  if (r < wk.r0 + wk.len) {\n";
-    lane_load("r", "    ");
-    o << "  }\n";
+    lane_fill("r", "wk.r0 + wk.len", "  ");
+    o << "  long long wn;\n";
+    o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
+    o << "    wn = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
     o << "  while (wi < nwork) {\n";
     o << "    unsigned int tnext = 0u;\n";
-    o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // read after the tuples of this item\n";
+    o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // the item after the next one\n";
+    o << "    Work wkn = {0, 0, 0};\n";
+    o << "    if (wn < nwork) wkn = work[wn];  // used after the tuples of this item\n";
     o << "    const T wsT = (T)ws;\n";
     o << "    const unsigned int wsu = (unsigned int)ws;\n";
     o << "    T acc[" << V << "];\n";
@@ -257,22 +273,23 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     o << "    if (ws != 0ull) {  // else no outer partner for the whole segment\n";
     o << "      const long long rend = wk.r0 + wk.len;\n";
     o << "      for (; r < rend; r += 32) {\n";
-    if (s.ni) o << "        const int kk = kn;\n";
-    for (int i = 0; i < s.nx; ++i) o << "        const T xk" << i << " = xn" << i << ";\n";
-    o << "        if (r + 32 < rend) {\n";
-    lane_load("r + 32", "          ");
+    if (s.ni) o << "        const int kk = kn0;\n";
+    for (int i = 0; i < s.nx; ++i) o << "        const T xk" << i << " = xn" << i << "_0;\n";
+    for (int j = 0; j + 1 < D; ++j) {  // the ring moves one step
+      if (s.ni) o << "        kn" << j << " = kn" << j + 1 << ";\n";
+      for (int i = 0; i < s.nx; ++i) o << "        xn" << i << "_" << j << " = xn" << i << "_" << j + 1 << ";\n";
+    }
+    o << "        if (r + " << 32 * D << " < rend) {\n";
+    lane_load_slot(D - 1, "r + " + std::to_string(32 * D), "          ");
     o << "        }\n";
     o << "        tuple(" << (s.ni ? "kk" : "0");
     for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? "xk" + std::to_string(i) : std::string("(T)0"));
     o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
     o << "      }\n    }\n";
-    o << "    const long long wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
-    o << "    Work wkn = {0, 0, 0};\n    unsigned long long wsn = 0ull;\n";
-    o << "    if (wn < nwork) { wkn = work[wn]; wsn = wseg[wkn.seg]; }\n";
+    o << "    unsigned long long wsn = 0ull;\n";
+    o << "    if (wn < nwork) wsn = wseg[wkn.seg];\n";
     o << "    r = wkn.r0 + lane;\n";
-    o << "    if (r < wkn.r0 + wkn.len) {\n";
-    lane_load("r", "      ");
-    o << "    }\n";
+    lane_fill("r", "wkn.r0 + wkn.len", "    ");
   } else {
   o << "  long long qa = (wk.r0 + 3) >> 2, qe = (wk.r0 + wk.len) >> 2;\n";
   o << "  if (qe < qa) qe = qa;\n";
@@ -282,9 +299,15 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "  if (q < qe) {\n";
   quad_load("q", "    ");
   o << "  }\n";
+  // tickets are taken one item ahead: the next item's record is requested when this item starts
+  o << "  long long wn;\n";
+  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
+  o << "    wn = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  while (wi < nwork) {\n";
   o << "    unsigned int tnext = 0u;\n";
-  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // read after the tuples of this item\n";
+  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // the item after the next one\n";
+  o << "    Work wkn = {0, 0, 0};\n";
+  o << "    if (wn < nwork) wkn = work[wn];  // used after the tuples of this item\n";
   o << "    const T wsT = (T)ws;\n";
   o << "    const unsigned int wsu = (unsigned int)ws;\n";
   o << "    T acc[" << V << "];\n";
@@ -314,10 +337,9 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
   }
   o << "      }\n    }\n";
-  // the next item: its loads overlap with the segment sums of this one
-  o << "    const long long wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
-  o << "    Work wkn = {0, 0, 0};\n    unsigned long long wsn = 0ull;\n";
-  o << "    if (wn < nwork) { wkn = work[wn]; wsn = wseg[wkn.seg]; }\n";
+  // the next item: its weight and first quad overlap with the segment sums of this one
+  o << "    unsigned long long wsn = 0ull;\n";
+  o << "    if (wn < nwork) wsn = wseg[wkn.seg];\n";
   o << "    long long qan = (wkn.r0 + 3) >> 2, qen = (wkn.r0 + wkn.len) >> 2;\n";
   o << "    if (qen < qan) qen = qan;\n";
   o << "    q = qan + lane;\n";
@@ -364,6 +386,7 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "    }\n";
   if (d.lanes) o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n";
   else o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
+  o << "    wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
   o << "  }\n";
   // root-to-inner partials: CTA-private -> global
   o << "  __syncthreads();\n";

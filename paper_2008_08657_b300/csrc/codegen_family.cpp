@@ -372,9 +372,15 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "  long long q = qa + lane;\n  if (q < qe) {\n";
   quad_load("q", "    ");
   o << "  }\n";
+  // tickets are taken one item ahead: the next item's record is requested when this item starts
+  o << "  long long wn;\n";
+  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
+  o << "    wn = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  while (wi < nwork) {\n";
   o << "    unsigned int tnext = 0u;\n";
-  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // read after the tuples of this item\n";
+  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // the item after the next one\n";
+  o << "    Work wkn = {0, 0, 0};\n";
+  o << "    if (wn < nwork) wkn = work[wn];  // used after the tuples of this item\n";
   o << "    const T wsT = (T)ws;\n";
   o << "    T acc[" << V << "];\n";
   o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
@@ -417,9 +423,8 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     o << ", obits, acc, wsT, ws);\n";
   }
   o << "      }\n    }\n";
-  o << "    const long long wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
-  o << "    Work wkn = {0, 0, 0};\n    unsigned long long wsn = 0ull;\n";
-  o << "    if (wn < nwork) { wkn = work[wn]; wsn = wseg[wkn.seg]; }\n";
+  o << "    unsigned long long wsn = 0ull;\n";
+  o << "    if (wn < nwork) wsn = wseg[wkn.seg];\n";
   o << "    long long qan = (wkn.r0 + 3) >> 2, qen = (wkn.r0 + wkn.len) >> 2;\n";
   o << "    if (qen < qan) qen = qan;\n";
   o << "    q = qan + lane;\n    if (q < qen) {\n";
@@ -467,7 +472,8 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     o << "      __syncwarp();\n";
   }
   o << "    }\n";
-  o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n  }\n";
+  o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
+  o << "    wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n  }\n";
   // end of the CTA: shared partials and CTA-private items to the outputs
   o << "  __syncthreads();\n";
   if (d.smem_p)
