@@ -162,6 +162,9 @@ typedef struct lmfao_plan_info {
                                 (the context keeps that order per root relation and segment
                                 key, so a later plan over the same relations reuses it)   */
   int32_t reorg_reused;      /* 1: the segment order of an earlier plan was reused       */
+  int32_t n_roots;           /* physical plans (roots) of the batch: 1, or more when no single
+                                root determines every query's group-by attributes; root_rel,
+                                segment_rel, n_segments and mode then describe the first */
 } lmfao_plan_info;
 
 /* ---- results ------------------------------------------------------------------------ */

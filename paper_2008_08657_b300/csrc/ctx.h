@@ -14,6 +14,14 @@ struct lmfao_reorg {
   std::map<int, void *> cols;       // root column -> device copy in segment order (+16 bytes)
 };
 
+// One physical plan of a batch whose queries need different roots: the plan, its join tree and
+// the batch's query ids it evaluates (its local query i is batch query qids[i]).
+struct lmfao_subplan {
+  lmfao::PhysPlan *plan = nullptr;
+  lmfao::JoinTree tree;
+  std::vector<int> qids;
+};
+
 struct lmfao_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;  // internal stream for loading and planning
@@ -35,4 +43,7 @@ struct lmfao_ctx {
   std::vector<std::string> ev_names;
   std::vector<std::string> kernel_names;
   std::vector<lmfao_reorg> reorg;   // reorganised root relations (see lmfao_reorg)
+  // A batch planned with several physical roots (plan == nullptr then): one plan per root.
+  std::vector<lmfao_subplan> subs;
+  std::vector<std::pair<int, int>> qroute;  // batch query -> (index in subs, local query id)
 };

@@ -73,14 +73,30 @@ int guarded(lmfao_ctx *ctx, F &&f) {
 }
 
 void drop_plan(lmfao_ctx *ctx) {
-  if (ctx->plan && ctx->device >= 0) {
+  if ((ctx->plan || !ctx->subs.empty()) && ctx->device >= 0) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->run_stream) cudaStreamSynchronize(ctx->run_stream);
+  }
+  if (ctx->plan && ctx->device >= 0) {
     ctx->plan->arena.release();
     delete ctx->plan;
     ctx->plan = nullptr;
   }
+  for (auto &sp : ctx->subs) {
+    sp.plan->arena.release();
+    delete sp.plan;
+  }
+  ctx->subs.clear();
+  ctx->qroute.clear();
   ctx->planned = ctx->ran = false;
+}
+
+// The physical plan that evaluates batch query q and q's index in it (a batch with several
+// roots has one plan per root); nullptr when there is no plan.
+std::pair<PhysPlan *, int> plan_of(lmfao_ctx *ctx, int q) {
+  if (ctx->plan) return {ctx->plan, q};
+  if (q < 0 || q >= (int)ctx->qroute.size()) return {nullptr, -1};
+  return {ctx->subs[ctx->qroute[q].first].plan, ctx->qroute[q].second};
 }
 
 // ------------------------------------------------------------------ join tree (GYO)
@@ -3115,13 +3131,19 @@ static int single_attr_power(const std::vector<FactorIn> &fs, std::string *attr)
   return fs.empty() ? 0 : pw;
 }
 
-int cart_descriptors(const lmfao_ctx *ctx, const int *qids, int n, int64_t *desc) {
-  if (!ctx->ran || !ctx->plan) throw Error(LMFAO_ERR_NOT_PLANNED, "no run yet");
-  const PhysPlan &P = *ctx->plan;
+int cart_descriptors(lmfao_ctx *ctx, const int *qids, int n, int64_t *desc, PhysPlan **plan) {
+  if (!ctx->ran || (!ctx->plan && ctx->subs.empty())) throw Error(LMFAO_ERR_NOT_PLANNED, "no run yet");
+  PhysPlan *PP = nullptr;
   int nb = 0;
   for (int i = 0; i < n; ++i) {
-    const int q = qids[i];
-    if (q < 0 || q >= (int)ctx->queries.size()) throw Error(LMFAO_ERR_ARG, "bad query id " + std::to_string(q));
+    const int q0 = qids[i];
+    if (q0 < 0 || q0 >= (int)ctx->queries.size()) throw Error(LMFAO_ERR_ARG, "bad query id " + std::to_string(q0));
+    const auto pq = plan_of(ctx, q0);
+    if (PP && pq.first != PP)
+      throw Error(LMFAO_ERR_UNSUPPORTED, "the queries are evaluated by plans with different roots");
+    PP = pq.first;
+    const PhysPlan &P = *PP;
+    const int q = q0;
     const QueryIn &Q = ctx->queries[q];
     const char *shape = "CART variances need one BUCKET group-by and aggregates COUNT, SUM(y), SUM(y^2) of one "
                         "attribute y (in any order)";
@@ -3137,7 +3159,7 @@ int cart_descriptors(const lmfao_ctx *ctx, const int *qids, int n, int64_t *desc
       else if (pw == 2 && i2 < 0) { i2 = a; y = attr; }
       else throw Error(LMFAO_ERR_ARG, std::string(shape) + " (query " + std::to_string(q) + ")");
     }
-    const QueryOut &qo = P.qout[q];
+    const QueryOut &qo = P.qout[pq.second];
     if (qo.integral[i1] || qo.integral[i2])
       throw Error(LMFAO_ERR_ARG, std::string(shape) + ": y must be a value attribute (query " + std::to_string(q) + ")");
     const int b = (int)Q.gb[0].thr.size() + 1;
@@ -3154,6 +3176,7 @@ int cart_descriptors(const lmfao_ctx *ctx, const int *qids, int n, int64_t *desc
       d[5] = i2;
     }
   }
+  if (plan) *plan = PP ? PP : ctx->plan;
   return nb;
 }
 
@@ -3453,11 +3476,68 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
           }
           drop_plan(ctx);
         }
-        if (!ok) return fail(ctx, LMFAO_ERR_UNSUPPORTED, msg + " for any root relation");
+        if (!ok) {
+          // Per-query roots (Section 2: each query has its own root): every query takes the
+          // largest relation whose views determine its group-by attributes, and the queries that
+          // share a root form one physical plan; lmfao_run runs them all.
+          const std::vector<QueryIn> all = ctx->queries;
+          std::vector<int32_t> qroot(all.size(), -1);
+          for (size_t q = 0; q < all.size(); ++q) {
+            ctx->queries = {all[q]};
+            for (int r : order) {
+              lmfao_plan_opts o2 = o;
+              o2.planner = LMFAO_PLAN_FORCED;
+              o2.root_rel = r;
+              o2.segment_rel = -2;
+              build_plan(ctx, o2, false, nullptr);
+              const bool good = !views_carry_codes(*ctx->plan) || !(view_flags(ctx) & 1);
+              drop_plan(ctx);
+              if (good) {
+                qroot[q] = r;
+                break;
+              }
+            }
+            if (qroot[q] < 0) {
+              ctx->queries = all;
+              return fail(ctx, LMFAO_ERR_UNSUPPORTED, msg + " for any root relation (query " + std::to_string(q) + ")");
+            }
+          }
+          std::map<int, std::vector<int>> by_root;
+          for (size_t q = 0; q < all.size(); ++q) by_root[qroot[q]].push_back((int)q);
+          std::vector<lmfao_subplan> subs;
+          std::vector<std::pair<int, int>> route(all.size());
+          for (auto &kv : by_root) {
+            ctx->queries.clear();
+            for (int q : kv.second) {
+              route[q] = {(int)subs.size(), (int)ctx->queries.size()};
+              ctx->queries.push_back(all[q]);
+            }
+            lmfao_plan_opts o2 = o;
+            o2.planner = LMFAO_PLAN_FORCED;
+            o2.root_rel = kv.first;
+            o2.segment_rel = -2;
+            try {
+              build_plan(ctx, o2, false, nullptr);
+            } catch (...) {
+              for (auto &sp : subs) { sp.plan->arena.release(); delete sp.plan; }
+              ctx->queries = all;
+              throw;
+            }
+            subs.push_back(lmfao_subplan{ctx->plan, ctx->tree, kv.second});
+            ctx->plan = nullptr;
+          }
+          ctx->queries = all;
+          // the logical plan of the whole batch: one join tree, the per-query roots
+          ctx->tree = build_tree(ctx, parent_links(ctx, o), largest_relation(ctx));
+          ctx->logical = build_logical(ctx, ctx->tree, qroot.data());
+          ctx->subs = std::move(subs);
+          ctx->qroute = std::move(route);
+          ctx->planned = true;
+        }
       }
     }
-    PhysPlan *P = ctx->plan;
-    if (P && o.autotune && ctx->device >= 0) autotune(ctx, *P);
+    PhysPlan *P = ctx->plan ? ctx->plan : (ctx->subs.empty() ? nullptr : ctx->subs[0].plan);
+    if (P && o.autotune && ctx->device >= 0 && ctx->plan) autotune(ctx, *P);
     if (P) P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
       std::memset(info, 0, sizeof(*info));
@@ -3473,6 +3553,11 @@ int lmfao_plan(lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *inf
         for (int c = 1; c <= 3; ++c) combine_kernels += (c4.tab[c].nt + c4.tab[c].ng) ? 1 : 0;
       }
       info->n_kernels = P ? (int)P->vk.size() * 2 + 2 + combine_kernels + (P->fast.on ? 2 : 0) : 0;
+      for (size_t i = 1; i < ctx->subs.size(); ++i) {  // the other plans of a batch with several roots
+        const PhysPlan *Q = ctx->subs[i].plan;
+        info->n_kernels += (int)Q->vk.size() * 2 + 2 + (Q->comb.empty() ? 0 : (Q->use_c5 ? 2 : 1)) + (Q->fast.on ? 2 : 0);
+      }
+      info->n_roots = ctx->subs.empty() ? 1 : (int)ctx->subs.size();
       info->mode = P ? P->mode : 0;
       info->predicted_ms = predicted;
       info->plan_ms = P ? P->plan_ms : 0;
@@ -3514,9 +3599,11 @@ int lmfao_plan_candidates(lmfao_ctx *ctx, const lmfao_plan_opts *opts, int32_t *
 
 int lmfao_run(lmfao_ctx *ctx, void *stream) {
   return guarded(ctx, [&]() -> int {
-    if (!ctx->planned || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "lmfao_run before lmfao_plan (or on a host-only context)");
+    if (!ctx->planned || (!ctx->plan && ctx->subs.empty()))
+      return fail(ctx, LMFAO_ERR_NOT_PLANNED, "lmfao_run before lmfao_plan (or on a host-only context)");
     cudaStream_t s = (cudaStream_t)stream;
-    enqueue_run(ctx, *ctx->plan, ctx->tree, s);
+    if (ctx->plan) enqueue_run(ctx, *ctx->plan, ctx->tree, s);
+    for (auto &sp : ctx->subs) enqueue_run(ctx, *sp.plan, sp.tree, s);
     ctx->run_stream = s;
     ctx->ran = true;
     return LMFAO_OK;
@@ -3526,7 +3613,14 @@ int lmfao_run(lmfao_ctx *ctx, void *stream) {
 static void check_device_flags(lmfao_ctx *ctx) {
   int e = 0;
   LMFAO_CUDA(cudaStreamSynchronize(ctx->run_stream));
-  LMFAO_CUDA(cudaMemcpy(&e, ctx->plan->err, 4, cudaMemcpyDeviceToHost));
+  std::vector<PhysPlan *> plans;
+  if (ctx->plan) plans.push_back(ctx->plan);
+  for (auto &sp : ctx->subs) plans.push_back(sp.plan);
+  for (PhysPlan *P : plans) {
+    int ep = 0;
+    LMFAO_CUDA(cudaMemcpy(&ep, P->err, 4, cudaMemcpyDeviceToHost));
+    e |= ep;
+  }
   if (e & 1)
     throw Error(LMFAO_ERR_UNSUPPORTED,
                 "a group-by attribute of a non-root relation is not determined by that relation's join key");
@@ -3536,11 +3630,12 @@ static void check_device_flags(lmfao_ctx *ctx) {
 
 int lmfao_fetch(lmfao_ctx *ctx, int query_id, lmfao_result *out) {
   return guarded(ctx, [&]() -> int {
-    if (!ctx->ran || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "lmfao_fetch before lmfao_run");
+    if (!ctx->ran || (!ctx->plan && ctx->subs.empty())) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "lmfao_fetch before lmfao_run");
     if (query_id < 0 || query_id >= (int)ctx->queries.size() || !out) return fail(ctx, LMFAO_ERR_ARG, "bad query id");
     check_device_flags(ctx);
-    PhysPlan &P = *ctx->plan;
-    const QueryOut &q = P.qout[query_id];
+    const auto pq = plan_of(ctx, query_id);
+    PhysPlan &P = *pq.first;
+    const QueryOut &q = P.qout[pq.second];
     std::vector<unsigned long long> ic(q.cells * (1 + q.naggs));
     std::vector<double> fs(q.cells * q.naggs);
     LMFAO_CUDA(cudaMemcpy(ic.data(), P.icnt + q.io, ic.size() * 8, cudaMemcpyDeviceToHost));
@@ -3574,23 +3669,22 @@ int lmfao_fetch(lmfao_ctx *ctx, int query_id, lmfao_result *out) {
 
 int lmfao_result_device(lmfao_ctx *ctx, int query_id, int64_t *counts, double *sums, int64_t *ncells, void *stream) {
   return guarded(ctx, [&]() -> int {
-    if (!ctx->planned || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
+    if (!ctx->planned || (!ctx->plan && ctx->subs.empty())) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
     if (query_id < 0 || query_id >= (int)ctx->queries.size()) return fail(ctx, LMFAO_ERR_ARG, "bad query id");
-    PhysPlan &P = *ctx->plan;
-    const QueryOut &q = P.qout[query_id];
+    const auto pq = plan_of(ctx, query_id);
+    PhysPlan &P = *pq.first;
+    const QueryOut &q = P.qout[pq.second];
     if (ncells) *ncells = q.cells;
     if (!counts && !sums) return LMFAO_OK;
     if (!ctx->ran) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
     cudaStream_t s = (cudaStream_t)stream;
-    // integral flags of the query, uploaded once per plan
-    static thread_local std::map<std::pair<const void *, int>, int *> flags;
-    auto key = std::make_pair((const void *)&P, query_id);
+    // integral flags of the query, uploaded once per plan (kept by the plan)
     int *fl;
-    auto it = flags.find(key);
-    if (it == flags.end()) {
+    auto it = P.result_flags.find(pq.second);
+    if (it == P.result_flags.end()) {
       fl = P.arena.upload(q.integral.empty() ? std::vector<int>{0} : q.integral, ctx->stream);
       LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
-      flags[key] = fl;
+      P.result_flags[pq.second] = fl;
     } else fl = it->second;
     launch_results(P.icnt + q.io, P.fsum + q.fo, q.cells, q.naggs, fl, counts, sums, s);
     LMFAO_CUDA(cudaGetLastError());
@@ -3600,6 +3694,8 @@ int lmfao_result_device(lmfao_ctx *ctx, int query_id, int64_t *counts, double *s
 
 int lmfao_result_state(lmfao_ctx *ctx, int64_t **counts, int64_t *ncounts, double **sums, int64_t *nsums) {
   return guarded(ctx, [&]() -> int {
+    if (!ctx->subs.empty())
+      return fail(ctx, LMFAO_ERR_UNSUPPORTED, "the batch is planned with several roots: one result state per plan");
     if (!ctx->planned || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no plan");
     PhysPlan &P = *ctx->plan;
     if (counts) *counts = reinterpret_cast<int64_t *>(P.icnt);
@@ -3656,7 +3752,15 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       for (int d : lg.deps) o << (i++ ? "," : "") << d;
       o << "]}";
     }
-    if (!ctx->plan) {
+    const PhysPlan *PP = ctx->plan ? ctx->plan : (ctx->subs.empty() ? nullptr : ctx->subs[0].plan);
+    o << "],\"physical_roots\":[";
+    if (ctx->plan) o << "{\"root\":" << nm(ctx->plan->root) << ",\"queries\":\"all\"}";
+    for (size_t i = 0; i < ctx->subs.size(); ++i) {
+      o << (i ? "," : "") << "{\"root\":" << nm(ctx->subs[i].plan->root) << ",\"queries\":[";
+      for (size_t k = 0; k < ctx->subs[i].qids.size(); ++k) o << (k ? "," : "") << ctx->subs[i].qids[k];
+      o << "]}";
+    }
+    if (!PP) {
       o << "],\"physical\":null}";
       std::string str = o.str();
       if (needed) *needed = str.size() + 1;
@@ -3667,7 +3771,7 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       }
       return LMFAO_OK;
     }
-    const PhysPlan &P = *ctx->plan;
+    const PhysPlan &P = *PP;
     o << "],\"physical\":{\"root\":" << nm(P.root) << ",\"segment_relation\":"
       << (P.segrel >= 0 ? nm(P.segrel) : std::string("null")) << ",\"n_segments\":" << P.nseg
       << ",\"outer\":[";
@@ -3739,9 +3843,10 @@ int lmfao_cart_variances(lmfao_ctx *ctx, const int *qids, int n, double *out, vo
   return guarded(ctx, [&]() -> int {
     if (n < 0 || (n && (!qids || !out))) return fail(ctx, LMFAO_ERR_ARG, "bad arguments");
     std::vector<int64_t> qd((size_t)std::max(n, 0) * kCartDescWords);
-    const int nb = cart_descriptors(ctx, qids, n, qd.data());
+    PhysPlan *PP = nullptr;
+    const int nb = cart_descriptors(ctx, qids, n, qd.data(), &PP);
     if (!n || nb < 2) return LMFAO_OK;
-    PhysPlan &P = *ctx->plan;
+    PhysPlan &P = *PP;
     check_device_flags(ctx);  // the run's own failures (counts above 2^32, a wait that ran out)
     int64_t *dq = P.arena.upload(qd, ctx->stream);
     LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -3792,6 +3897,7 @@ int lmfao_cart_tree(lmfao_ctx *ctx, const char *target, const char *const *featu
         }
       int rc = lmfao_plan(ctx, opts, nullptr);
       if (rc != LMFAO_OK) return rc;
+      if (!ctx->plan) return fail(ctx, LMFAO_ERR_UNSUPPORTED, "a tree level needs several roots");
       const auto t1 = std::chrono::steady_clock::now();
       PhysPlan &P = *ctx->plan;
       enqueue_run(ctx, P, ctx->tree, ctx->stream);
@@ -3860,7 +3966,7 @@ int lmfao_ridge_fit(lmfao_ctx *ctx, int query_id, const char *target, const char
                     double lambda, int method, int iters, double step, double *theta, double *loss,
                     double *grad_norm) {
   return guarded(ctx, [&]() -> int {
-    if (!ctx->ran || !ctx->plan) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
+    if (!ctx->ran || (!ctx->plan && ctx->subs.empty())) return fail(ctx, LMFAO_ERR_NOT_PLANNED, "no run yet");
     if (query_id < 0 || query_id >= (int)ctx->queries.size() || !target || !theta || nfeatures < 0 ||
         (nfeatures && !features) || nfeatures > 126 || lambda < 0 || (method != LMFAO_RIDGE_CLOSED_FORM &&
         method != LMFAO_RIDGE_BGD) || (method == LMFAO_RIDGE_BGD && (iters < 0 || !(step > 0))))
@@ -3884,7 +3990,8 @@ int lmfao_ridge_fit(lmfao_ctx *ctx, int query_id, const char *target, const char
     z.push_back(target);
     const int d = nfeatures, w = d + 2;
     std::vector<int> zmap((size_t)w * w, -1);
-    const QueryOut &qo = ctx->plan->qout[query_id];
+    const auto pq = plan_of(ctx, query_id);
+    const QueryOut &qo = pq.first->qout[pq.second];
     for (int i = 0; i < w; ++i)
       for (int j = 0; j < w; ++j) {
         if (i == 0 && j == 0) continue;  // the COUNT of the (single) group
@@ -3900,7 +4007,7 @@ int lmfao_ridge_fit(lmfao_ctx *ctx, int query_id, const char *target, const char
         zmap[(size_t)i * w + j] = it->second;
       }
     check_device_flags(ctx);
-    PhysPlan &P = *ctx->plan;
+    PhysPlan &P = *pq.first;
     int *dz = P.arena.upload(zmap, ctx->stream);
     double *dout = (double *)P.arena.alloc((size_t)(d + 3) * 8);
     launch_ridge(P.icnt, P.fsum, qo.io, qo.fo, dz, d, lambda, method, iters, step, dout, ctx->stream);

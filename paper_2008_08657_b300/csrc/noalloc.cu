@@ -74,14 +74,15 @@ extern "C" int lmfao_cart_variances_noalloc(lmfao_ctx *ctx, const int *qids, int
       throw lmfao::Error(LMFAO_ERR_CUDA, "cudaSetDevice failed");
     }
     // the same checks as lmfao_cart_variances, without writing descriptors yet
-    const int nb = lmfao::cart_descriptors(ctx, qids, n, nullptr);
+    lmfao::PhysPlan *PP = nullptr;
+    const int nb = lmfao::cart_descriptors(ctx, qids, n, nullptr, &PP);
     if (!n || nb < 2) return LMFAO_OK;
-    lmfao::PhysPlan &P = *ctx->plan;
+    lmfao::PhysPlan &P = *PP;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_mu);
     // First call on this device: look up the array's device address (the device is current).
     void *desc = scratch_address_locked(ctx->device);
-    lmfao::cart_descriptors(ctx, qids, n, g_host_desc);
+    lmfao::cart_descriptors(ctx, qids, n, g_host_desc, nullptr);
     cudaError_t e = cudaMemcpyAsync(desc, g_host_desc, (size_t)n * kDescWords * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {

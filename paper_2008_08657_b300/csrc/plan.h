@@ -159,6 +159,7 @@ struct PhysPlan {
   bool use_c5 = false;
   std::string c5_why;              // why the two-kernel block combine does not run (if not)
   std::string fast_why;            // why the specialised root pass declined the batch (if it did)
+  std::map<int, int *> result_flags;  // per query: integral flags on the device (lmfao_result_device)
   int c3_grid = 0, c3_block = 512;
   DSegWeight sw{};
   int fp_grid = 0, fp_block = 256;
@@ -184,6 +185,8 @@ constexpr int kCartDescWords = 6;
 // context's last run: every query id valid, one BUCKET group-by, exactly three aggregates that
 // are COUNT, SUM(y) and SUM(y^2) of one attribute y (in any order), and the same number of
 // buckets for all queries. Writes n descriptors of kCartDescWords words into desc (host, may
-// be null) and returns the bucket count. Throws Error(LMFAO_ERR_ARG / ERR_NOT_PLANNED).
-int cart_descriptors(const lmfao_ctx *ctx, const int *qids, int n, int64_t *desc);
+// be null) and returns the bucket count; *plan (may be null) receives the physical plan that
+// holds the queries (all of them must be evaluated by one plan). Throws Error(LMFAO_ERR_ARG /
+// ERR_NOT_PLANNED / ERR_UNSUPPORTED).
+int cart_descriptors(lmfao_ctx *ctx, const int *qids, int n, int64_t *desc, PhysPlan **plan);
 }  // namespace lmfao

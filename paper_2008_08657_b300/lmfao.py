@@ -74,7 +74,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("root_rel", C.c_int32), ("segment_rel", C.c_int32), ("n_segments", C.c_int64),
                 ("n_views", C.c_int32), ("n_groups", C.c_int32), ("n_kernels", C.c_int32),
                 ("mode", C.c_int32), ("predicted_ms", C.c_double), ("plan_ms", C.c_double),
-                ("reorg_ms", C.c_double), ("reorg_reused", C.c_int32)]
+                ("reorg_ms", C.c_double), ("reorg_reused", C.c_int32), ("n_roots", C.c_int32)]
 
 
 class CartNode(C.Structure):

@@ -461,3 +461,46 @@ def test_autotuned_plans_match_the_oracle_and_reuse_their_tiles(which, tmp_path,
             assert tiles["candidates"] >= 5, tiles
         for i, (q, g, r) in enumerate(zip(qs, got, ref)):
             compare(q, g, r, where=f"attempt {attempt} query {i}")
+
+
+def test_queries_that_need_different_roots_get_one_plan_per_root():
+    """F(a, b, x) with A(a, ga) and B(b, gb) whose join keys repeat with different ga / gb values:
+    a group-by on ga is determined only when A is the root, one on gb only when B is, so no
+    single root serves the batch. Each query takes its own root (Section 2: per-query roots),
+    the engine runs one physical plan per root, and every result equals the oracle's."""
+    r = np.random.default_rng(12)
+    n = 5000
+    F = W.relation("F", [W.column("a", r.integers(0, 40, n).astype(np.int32), "key", 40),
+                         W.column("b", r.integers(0, 30, n).astype(np.int32), "key", 30),
+                         W.column("x", r.standard_normal(n).astype(np.float32), "cont")])
+    A = W.relation("A", [W.column("a", np.repeat(np.arange(40), 3).astype(np.int32), "key", 40),
+                         W.column("ga", r.integers(0, 5, 120).astype(np.int32), "cat", 5),
+                         W.column("xa", r.standard_normal(120).astype(np.float32), "cont")])
+    B = W.relation("B", [W.column("b", np.repeat(np.arange(30), 2).astype(np.int32), "key", 30),
+                         W.column("gb", r.integers(0, 4, 60).astype(np.int32), "cat", 4)])
+    rels = [F, A, B]
+    qs = [{"aggs": [[], [("x", "id", 1)], [("xa", "id", 1)]], "groupby": [("ga", "value", None)], "filters": []},
+          {"aggs": [[], [("x", "pow", 2)]], "groupby": [("gb", "value", None)], "filters": []},
+          {"aggs": [[], [("x", "id", 1), ("xa", "id", 1)]], "groupby": [], "filters": []}]
+    ref = O.evaluate(rels, qs)
+    e = Engine(0)
+    try:
+        for R in rels:
+            e.load_relation(R)
+        e.add_queries(qs)
+        info = e.plan()
+        desc = e.describe()
+        e.run()
+        got = e.fetch_all()
+        with pytest.raises(LmfaoError) as ei:
+            e.result_state()
+        assert ei.value.code == ERR_UNSUPPORTED
+    finally:
+        e.close()
+    assert info["n_roots"] >= 2, desc["physical_roots"]
+    roots = {tuple(x["queries"]) if isinstance(x["queries"], list) else x["queries"]: x["root"]
+             for x in desc["physical_roots"]}
+    assert any(v == "A" for v in roots.values()) and any(v == "B" for v in roots.values()), roots
+    assert desc["query_roots"][0] == "A" and desc["query_roots"][1] == "B"
+    for i, (q, g, r_) in enumerate(zip(qs, got, ref)):
+        compare(q, g, r_, where=f"query {i}")
