@@ -272,20 +272,35 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
     o << "    if (ws != 0ull) {  // else no outer partner for the whole segment\n";
     o << "      const long long rend = wk.r0 + wk.len;\n";
-    o << "      for (; r < rend; r += 32) {\n";
-    if (s.ni) o << "        const int kk = kn0;\n";
-    for (int i = 0; i < s.nx; ++i) o << "        const T xk" << i << " = xn" << i << "_0;\n";
-    for (int j = 0; j + 1 < D; ++j) {  // the ring moves one step
-      if (s.ni) o << "        kn" << j << " = kn" << j + 1 << ";\n";
-      for (int i = 0; i < s.nx; ++i) o << "        xn" << i << "_" << j << " = xn" << i << "_" << j + 1 << ";\n";
+    // D steps per iteration: slot j is consumed and refilled with the tuple D steps ahead, so
+    // every slot's load has a whole iteration to land (no register moves between slots)
+    auto lane_tuple = [&](int j, const std::string &ind) {
+      o << ind << "tuple(" << (s.ni ? "kk" : "0");
+      for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? "xk" + std::to_string(i) : std::string("(T)0"));
+      o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
+      (void)j;
+    };
+    o << "      for (; r + " << 32 * (D - 1) << " < rend; r += " << 32 * D << ") {\n";
+    for (int j = 0; j < D; ++j) {
+      o << "        {\n";
+      if (s.ni) o << "          const int kk = kn" << j << ";\n";
+      for (int i = 0; i < s.nx; ++i) o << "          const T xk" << i << " = xn" << i << "_" << j << ";\n";
+      o << "          if (r + " << 32 * (D + j) << " < rend) {\n";
+      lane_load_slot(j, "r + " + std::to_string(32 * (D + j)), "            ");
+      o << "          }\n";
+      lane_tuple(j, "          ");
+      o << "        }\n";
     }
-    o << "        if (r + " << 32 * D << " < rend) {\n";
-    lane_load_slot(D - 1, "r + " + std::to_string(32 * D), "          ");
-    o << "        }\n";
-    o << "        tuple(" << (s.ni ? "kk" : "0");
-    for (int i = 0; i < 3; ++i) o << ", " << (i < s.nx ? "xk" + std::to_string(i) : std::string("(T)0"));
-    o << ", acc, tab, tcode, hist, Pf, Pi, wsT, wsu);\n";
-    o << "      }\n    }\n";
+    o << "      }\n";
+    // the last steps of the item (fewer than D), already in the slots
+    for (int j = 0; j + 1 < D; ++j) {
+      o << "      if (r + " << 32 * j << " < rend) {\n";
+      if (s.ni) o << "        const int kk = kn" << j << ";\n";
+      for (int i = 0; i < s.nx; ++i) o << "        const T xk" << i << " = xn" << i << "_" << j << ";\n";
+      lane_tuple(j, "        ");
+      o << "      }\n";
+    }
+    o << "    }\n";
     o << "    unsigned long long wsn = 0ull;\n";
     o << "    if (wn < nwork) wsn = wseg[wkn.seg];\n";
     o << "    r = wkn.r0 + lane;\n";

@@ -48,12 +48,15 @@ def test_tiny_schemas_match_oracle(seed, precision, mode, segment):
         compare(q, g, r, where=f"seed {seed} query {i}")
 
 
+@pytest.mark.parametrize("lanes", ["0", "1"])
 @pytest.mark.parametrize("seed,segment", [(a, b) for a, b in TINY_SEG_CASES if b is not None])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_tiny_schemas_generated_root_pass(seed, precision, segment, monkeypatch):
+def test_tiny_schemas_generated_root_pass(seed, precision, segment, lanes, monkeypatch):
     """Tiny schemas (duplicate and dangling keys, group-bys, buckets, filters) with the root
-    pass generated at plan time at any size; shapes outside the generator keep the template."""
+    pass generated at plan time at any size, in both lane layouts (segments far shorter than
+    a warp's step); shapes outside the generator keep the template."""
     monkeypatch.setenv("LMFAO_CODEGEN", "1")
+    monkeypatch.setenv("LMFAO_ROOT_LANES", lanes)
     shared3 = seed % 2 == 1
     rels = W.tiny_schema(seed, shared3=shared3, fd=True)
     qs = W.tiny_queries(seed, rels, nq=6, group_attrs=TINY_GROUPS, bucket_attrs=TINY_BUCKETS)
@@ -334,13 +337,16 @@ def _shape_case(which):
     return _SHAPES[which]
 
 
-@pytest.mark.parametrize("codegen", ["0", "1"])
+@pytest.mark.parametrize("codegen", ["0", "1", "lanes"])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("which", ["star", "retailer", "favorita"])
 def test_generated_and_template_root_pass_match_the_oracle(which, precision, codegen, monkeypatch):
     """The plan-specialised root pass (compiled at plan time) and the template kernel, on the
-    benchmark shapes with ragged segments (head and tail tuples outside full quads)."""
-    monkeypatch.setenv("LMFAO_CODEGEN", codegen)
+    benchmark shapes with ragged segments (head and tail tuples outside full quads); "lanes" is
+    the generated pass in its one-tuple-per-lane layout (items of any length end inside the
+    unrolled ring of loads)."""
+    monkeypatch.setenv("LMFAO_CODEGEN", "0" if codegen == "0" else "1")
+    monkeypatch.setenv("LMFAO_ROOT_LANES", "1" if codegen == "lanes" else "0")
     rels, qs, ref = _shape_case(which)
     e = Engine(0)
     try:
@@ -351,6 +357,7 @@ def test_generated_and_template_root_pass_match_the_oracle(which, precision, cod
         phys = e.describe()["physical"]
         assert "root_pass" in phys and phys["lean_pass"], phys
         rp = phys["root_pass"]
+        lanes = phys["tiles"]["root_pass_lanes"]
         e.run()
         got = e.fetch_all()
     finally:
@@ -360,6 +367,8 @@ def test_generated_and_template_root_pass_match_the_oracle(which, precision, cod
     else:  # generated unless its table and partials exceed shared memory (FP64 Retailer)
         assert rp["generated"] or rp["not_generated_because"] == "shared memory", rp["not_generated_because"]
         assert rp["generated"] or precision == "fp64"
+        if rp["generated"]:
+            assert lanes == ("tuple per lane" if codegen == "lanes" else "quad per lane"), lanes
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"{which} {precision} codegen={codegen} query {i}")
 
