@@ -269,7 +269,9 @@ def bench_lmfao(args):
         "combine_roofline": comb,
         "tiles": desc["physical"].get("tiles"),
         "kernel_ms": kernel_ms,
-        "root_pass_shape": desc["physical"].get("root_pass"),
+        "root_pass_shape": dict(desc["physical"].get("root_pass") or {},
+                                **{k: desc["physical"].get(k) for k in
+                                   ("filter_family", "cta_items", "per_tuple_items", "segment_sums", "work_items")}),
         "combine_shape": {k: desc["physical"].get(k) for k in
                           ("block_combine", "projection_combine", "projection_entries", "combine_items",
                            "outer_terms",

@@ -12,8 +12,11 @@
 //     column, with every index a constant;
 //   * a work item's full 4-tuple quads are read with 16-byte loads and no range checks; the
 //     at most 6 tuples of its ragged head and tail are taken by single lanes;
-//   * work-item tickets are taken one item ahead, so the next item's record is requested when
-//     the current item starts and its weight and first quad while the segment sums are reduced.
+//   * each CTA takes a contiguous range of work items with about 1/G of the tuples (tuple
+//     quantiles of the work list) and hands them to its warps with a ticket in shared memory
+//     (one global counter for all warps of the GPU was a serial point);
+//   * the next item's ticket and record are requested when the current item starts, and its
+//     weight and first quad while the segment sums of the current one are reduced.
 #include "codegen.h"
 
 #include <nvrtc.h>
@@ -29,7 +32,7 @@ namespace lmfao {
 namespace {
 
 enum Arg {
-  A_NWORK, A_WORK, A_WSEG, A_TICKET, A_TABLE, A_CODES, A_PHI0F, A_PHI0I, A_PHI1I, A_P3F, A_P3I, A_KC, A_X0,
+  A_NWORK, A_WORK, A_WSEG, A_WORKQ, A_TABLE, A_CODES, A_PHI0F, A_PHI0I, A_PHI1I, A_P3F, A_P3I, A_KC, A_X0,
   A_NARGS = A_X0 + 3
 };
 
@@ -43,6 +46,7 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 struct Shape {
   bool fp64;
   int block, nx, ni, nw, nm, nb1, ncode, n3, n3f, n3i, n0i, hist, rs;
+  int nfull, tew;  // FP32 rows: full 16-byte planes and the element width (words) of the tail plane
   long long nkeys, phi1i_seg;
   int xdt[3];
   size_t off_tab, off_code, off_pf, off_pi, off_h, smem;
@@ -68,13 +72,18 @@ Shape shape_of(const DFast &d, bool fp64, int block) {
   for (int i = 0; i < 3; ++i) s.xdt[i] = i < d.nx ? d.col[d.xslot[i]].dtype : LMFAO_F32;
   const size_t ts = fp64 ? 8 : 4;
   s.rs = fp64 ? round_up(s.nw, 2) : round_up(s.nw + s.nb1, 4);
+  {
+    const int rw = s.nw + s.nb1, tw = rw % 4;
+    s.nfull = rw / 4;
+    s.tew = tw == 3 ? 4 : tw;  // a row tail of 1 or 2 words is read with a 4- or 8-byte load
+  }
   size_t off = 0;
   auto region = [&](size_t bytes) {
     size_t at = off;
     off = (off + bytes + 15) & ~(size_t)15;
     return at;
   };
-  s.off_tab = region(ts * (size_t)s.nkeys * s.rs);
+  s.off_tab = region(fp64 ? ts * (size_t)s.nkeys * s.rs : 4 * (size_t)s.nkeys * (4 * s.nfull + s.tew));
   s.off_code = region(fp64 ? 4 * (size_t)s.nkeys * s.nb1 : 0);
   s.off_pf = region(ts * (size_t)s.nkeys * s.n3f);
   s.off_pi = region(4 * (size_t)s.nkeys * s.n3i);
@@ -103,9 +112,66 @@ std::string x_component(int dt, const std::string &reg, int i) {
 
 }  // namespace
 
+WarpReduce gen_warp_reduce(int V, const std::string &ind) {
+  WarpReduce w{};
+  w.V = V;
+  std::ostringstream o;
+  if (V <= 32) {
+    int L = 0;
+    while ((1 << L) < V) ++L;
+    const int PV = 1 << L;
+    w.F = 1;
+    w.shift = 5 - L;
+    o << ind << "T r_[" << PV << "];\n";
+    o << "#pragma unroll\n" << ind << "for (int i = 0; i < " << PV << "; ++i) r_[i] = i < " << V << " ? acc[i < " << V
+      << " ? i : 0] : (T)0;\n";
+    if (L > 0) {
+      o << "#pragma unroll\n" << ind << "for (int lvl = 0; lvl < " << L << "; ++lvl) {\n";
+      o << ind << "  const int o = 16 >> lvl, h = " << PV << " >> (lvl + 1);\n";
+      o << ind << "  const bool up = (lane & o) != 0;\n";
+      o << "#pragma unroll\n" << ind << "  for (int i = 0; i < h; ++i) {\n";
+      o << ind << "    const T send = up ? r_[i] : r_[i + h];\n";
+      o << ind << "    const T keep = up ? r_[i + h] : r_[i];\n";
+      o << ind << "    r_[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);\n" << ind << "  }\n" << ind << "}\n";
+    }
+    for (int b = (16 >> L); b >= 1; b >>= 1) o << ind << "r_[0] += __shfl_xor_sync(0xffffffffu, r_[0], " << b << ");\n";
+  } else {
+    w.F = (V + 31) / 32;
+    w.shift = 0;
+    const int PV = 32 * w.F;
+    o << ind << "T r_[" << PV << "];\n";
+    o << "#pragma unroll\n" << ind << "for (int i = 0; i < " << PV << "; ++i) r_[i] = i < " << V << " ? acc[i < " << V
+      << " ? i : 0] : (T)0;\n";
+    o << "#pragma unroll\n" << ind << "for (int lvl = 0; lvl < 5; ++lvl) {\n";
+    o << ind << "  const int o = 16 >> lvl, h = " << PV << " >> (lvl + 1);\n";
+    o << ind << "  const bool up = (lane & o) != 0;\n";
+    o << "#pragma unroll\n" << ind << "  for (int i = 0; i < h; ++i) {\n";
+    o << ind << "    const T send = up ? r_[i] : r_[i + h];\n";
+    o << ind << "    const T keep = up ? r_[i + h] : r_[i];\n";
+    o << ind << "    r_[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);\n" << ind << "  }\n" << ind << "}\n";
+  }
+  w.src = o.str();
+  return w;
+}
+
+std::string gen_reduce_flush(const WarpReduce &w, const std::string &dst, const std::string &base,
+                             const std::string &ind) {
+  std::ostringstream o;
+  if (w.F == 1) {
+    const int mask = (1 << w.shift) - 1;
+    o << ind << "{ const int i = lane >> " << w.shift << "; if (" << (mask ? "(lane & " + std::to_string(mask) + ") == 0 && " : "")
+      << "i < " << w.V << " && r_[0] != (T)0) atomicAdd(" << dst << " + " << base << " + i, r_[0]); }\n";
+  } else {
+    for (int e = 0; e < w.F; ++e)
+      o << ind << "{ const int i = lane * " << w.F << " + " << e << "; if (i < " << w.V << " && r_[" << e
+        << "] != (T)0) atomicAdd(" << dst << " + " << base << " + i, r_[" << e << "]); }\n";
+  }
+  return o.str();
+}
+
 std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   const Shape s = shape_of(d, fp64, block);
-  const int V = s.nm * s.nw, F = (V + 31) / 32, PV = 32 * F;
+  const int V = s.nm * s.nw;
   std::ostringstream o;
   o << "// generated lean root pass\n";
   o << "typedef " << (fp64 ? "double" : "float") << " T;\n";
@@ -120,16 +186,22 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   if (s.ni) {
     if (!fp64) {
       // planar rows: 16-byte part q of row k at plane q, element k (consecutive keys in
-      // consecutive bank groups, so a warp's random rows spread over all banks)
+      // consecutive bank groups, so a warp's random rows spread over all banks); a tail of one
+      // or two words sits in a plane of 4- or 8-byte elements (a random gather of narrower
+      // elements takes fewer shared-memory wavefronts)
       static const char *c[4] = {"x", "y", "z", "w"};
-      for (int q = 0; q < s.rs / 4; ++q)
+      for (int q = 0; q < s.nfull; ++q)
         o << "  const float4 t" << q << " = reinterpret_cast<const float4 *>(tab)[" << (long long)q * s.nkeys
           << " + k];\n";
-      for (int w = 0; w < s.nw; ++w) v[w] = "t" + std::to_string(w / 4) + "." + c[w % 4];
-      for (int b = 0; b < s.nb1; ++b) {
-        int p = s.nw + b;
-        code[b] = "__float_as_int(t" + std::to_string(p / 4) + "." + c[p % 4] + ")";
-      }
+      const std::string tail = "reinterpret_cast<const " + std::string(s.tew == 4 ? "float4" : s.tew == 2 ? "float2" : "float") +
+                               " *>(tab + " + std::to_string((long long)s.nfull * s.nkeys * 4) + ")[k]";
+      if (s.tew) o << "  const " << (s.tew == 4 ? "float4" : s.tew == 2 ? "float2" : "float") << " tt = " << tail << ";\n";
+      auto word = [&](int p) {
+        if (p < 4 * s.nfull) return "t" + std::to_string(p / 4) + "." + c[p % 4];
+        return s.tew == 1 ? std::string("tt") : "tt." + std::string(c[p - 4 * s.nfull]);
+      };
+      for (int w = 0; w < s.nw; ++w) v[w] = word(w);
+      for (int b = 0; b < s.nb1; ++b) code[b] = "__float_as_int(" + word(s.nw + b) + ")";
     } else {
       for (int q = 0; q < s.rs / 2; ++q)
         o << "  const double2 t" << q << " = reinterpret_cast<const double2 *>(tab)[" << (long long)q * s.nkeys
@@ -167,10 +239,14 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   // kernel
   o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", 1) lmfao_gen_root_pass(const GenArgs a) {\n";
   o << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n";
-  o << "  const long long nwork = (long long)a.v[" << A_NWORK << "];\n";
+  // this CTA's work items: a contiguous range of about 1/G of the tuples, handed to its warps
+  // by a ticket in shared memory
   o << "  const Work *__restrict__ work = (const Work *)a.v[" << A_WORK << "];\n";
   o << "  const unsigned long long *__restrict__ wseg = (const unsigned long long *)a.v[" << A_WSEG << "];\n";
-  o << "  unsigned int *ticket = (unsigned int *)a.v[" << A_TICKET << "];\n";
+  o << "  const int *__restrict__ wq = (const int *)a.v[" << A_WORKQ << "];\n";
+  o << "  const int ib = wq[" << kWorkQ << " * blockIdx.x / gridDim.x];\n";
+  o << "  const int nwork = wq[" << kWorkQ << " * (blockIdx.x + 1) / gridDim.x];  // end of the range\n";
+  o << "  __shared__ unsigned int ticket;\n";
   o << "  const T *__restrict__ gtab = (const T *)a.v[" << A_TABLE << "];\n";
   o << "  const int *__restrict__ gcod = (const int *)a.v[" << A_CODES << "];\n";
   o << "  T *phi0f = (T *)a.v[" << A_PHI0F << "];\n";
@@ -194,17 +270,22 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "  unsigned int *hist = hist0 + warp * " << s.hist << ";\n";
   // staging
   if (s.ni) {
-    o << "  for (int i = tid; i < " << s.nkeys * s.rs << "; i += " << block << ") {\n";
-    o << "    const int k = i / " << s.rs << ", c = i - k * " << s.rs << ";\n";
+    const int rsw = fp64 ? s.rs : 4 * s.nfull + s.tew;  // staged words per row
+    o << "#pragma unroll 4\n";  // several loads of the staging loop in flight
+    o << "  for (int i = tid; i < " << s.nkeys * rsw << "; i += " << block << ") {\n";
+    o << "    const int k = i / " << rsw << ", c = i - k * " << rsw << ";\n";
     o << "    T t = (T)0;\n";
     o << "    if (c < " << s.nw << ") t = gtab[(long long)k * " << s.nw << " + c];\n";
     if (!fp64)
       for (int b = 0; b < s.nb1; ++b)
         o << "    else if (c == " << s.nw + b << ") t = __int_as_float(gcod[(long long)k * " << s.ncode << " + "
           << d.b1code[b] << "]);\n";
-    {
-      const int vw = fp64 ? 2 : 4;  // elements per 16-byte part
-      o << "    tab[(c / " << vw << ") * " << s.nkeys * vw << " + k * " << vw << " + c % " << vw << "] = t;\n  }\n";
+    if (fp64) {
+      o << "    tab[(c / 2) * " << s.nkeys * 2 << " + k * 2 + c % 2] = t;\n  }\n";
+    } else {
+      o << "    if (c < " << 4 * s.nfull << ") tab[(c / 4) * " << s.nkeys * 4 << " + k * 4 + c % 4] = t;\n";
+      o << "    else tab[" << (long long)s.nfull * s.nkeys * 4 << " + k * " << s.tew << " + c - " << 4 * s.nfull
+        << "] = t;\n  }\n";
     }
     if (fp64 && s.nb1) {
       o << "  for (int i = tid; i < " << s.nkeys * s.nb1 << "; i += " << block << ") {\n";
@@ -218,6 +299,7 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "  for (int i = tid; i < " << s.nkeys * s.n3f << "; i += " << block << ") Pf[i] = (T)0;\n";
   o << "  for (int i = tid; i < " << s.nkeys * s.n3i << "; i += " << block << ") Pi[i] = 0u;\n";
   o << "  for (int i = tid; i < " << (long long)(block / 32) * s.hist << "; i += " << block << ") hist0[i] = 0u;\n";
+  o << "  if (tid == 0) ticket = 0u;\n";
   o << "  __syncthreads();\n";
   // work loop: the ticket, record and outer weight of the next work item and the first quad
   // of each lane in it are requested while the current item is processed
@@ -231,9 +313,9 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     if (s.ni) o << ind << "kn = reinterpret_cast<const int4 *>(kc)[" << q << "];\n";
     for (int i = 0; i < s.nx; ++i) o << ind << "xn" << i << " = " << xreg_load(i, q) << ";\n";
   };
-  o << "  long long wi;\n";
-  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
-  o << "    wi = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
+  o << "  int wi;\n";
+  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(&ticket, 1u);\n";
+  o << "    wi = ib + (int)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  Work wk = {0, 0, 0};\n  unsigned long long ws = 0ull;\n";
   o << "  if (wi < nwork) { wk = work[wi]; ws = wseg[wk.seg]; }\n";
   if (d.lanes) {
@@ -258,12 +340,10 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
     }
     o << "  long long r = wk.r0 + lane;\n";
     lane_fill("r", "wk.r0 + wk.len", "  ");
-    o << "  long long wn;\n";
-    o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
-    o << "    wn = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
     o << "  while (wi < nwork) {\n";
-    o << "    unsigned int tnext = 0u;\n";
-    o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // the item after the next one\n";
+    o << "    int wn;  // the next item (shared-memory ticket): its record is requested now\n";
+    o << "    {\n      unsigned int t = 0u;\n      if (lane == 0) t = atomicAdd(&ticket, 1u);\n";
+    o << "      wn = ib + (int)__shfl_sync(0xffffffffu, t, 0);\n    }\n";
     o << "    Work wkn = {0, 0, 0};\n";
     o << "    if (wn < nwork) wkn = work[wn];  // used after the tuples of this item\n";
     o << "    const T wsT = (T)ws;\n";
@@ -314,13 +394,10 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "  if (q < qe) {\n";
   quad_load("q", "    ");
   o << "  }\n";
-  // tickets are taken one item ahead: the next item's record is requested when this item starts
-  o << "  long long wn;\n";
-  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
-  o << "    wn = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  while (wi < nwork) {\n";
-  o << "    unsigned int tnext = 0u;\n";
-  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // the item after the next one\n";
+  o << "    int wn;  // the next item (shared-memory ticket): its record is requested now\n";
+  o << "    {\n      unsigned int t = 0u;\n      if (lane == 0) t = atomicAdd(&ticket, 1u);\n";
+  o << "      wn = ib + (int)__shfl_sync(0xffffffffu, t, 0);\n    }\n";
   o << "    Work wkn = {0, 0, 0};\n";
   o << "    if (wn < nwork) wkn = work[wn];  // used after the tuples of this item\n";
   o << "    const T wsT = (T)ws;\n";
@@ -364,25 +441,15 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   }
   o << "    if (ws != 0ull) {\n";
   // per-segment sums: reduce-scatter over the warp
-  o << "    T r_[" << PV << "];\n";
-  o << "#pragma unroll\n    for (int i = 0; i < " << PV << "; ++i) r_[i] = i < " << V << " ? acc[i < " << V
-    << " ? i : 0] : (T)0;\n";
-  o << "#pragma unroll\n    for (int lvl = 0; lvl < 5; ++lvl) {\n";
-  o << "      const int o = 16 >> lvl, h = " << PV << " >> (lvl + 1);\n";
-  o << "      const bool up = (lane & o) != 0;\n";
-  o << "#pragma unroll\n      for (int i = 0; i < h; ++i) {\n";
-  o << "        const T send = up ? r_[i] : r_[i + h];\n";
-  o << "        const T keep = up ? r_[i + h] : r_[i];\n";
-  o << "        r_[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);\n      }\n    }\n";
-  for (int e = 0; e < F; ++e)
-    o << "    { const int i = lane * " << F << " + " << e << "; if (i < " << V << " && r_[" << e
-      << "] != (T)0) atomicAdd(phi0f + (long long)wk.seg * " << V << " + i, r_[" << e << "]); }\n";
+  const WarpReduce wr = gen_warp_reduce(V, "    ");
+  o << wr.src;
+  o << gen_reduce_flush(wr, "phi0f", "(long long)wk.seg * " + std::to_string(V), "    ");
   if (s.n0i) {
     o << "    {\n      T iv = (T)0;\n";
     for (int e = 0; e < s.n0i; ++e) {
       const int q = d.i0j[e] * s.nw + d.i0w[e];
-      o << "      { const T t = __shfl_sync(0xffffffffu, r_[" << q % F << "], " << q / F << "); if (lane == " << e
-        << ") iv = t; }\n";
+      o << "      { const T t = __shfl_sync(0xffffffffu, r_[" << wr.reg_of(q) << "], " << wr.lane_of(q)
+        << "); if (lane == " << e << ") iv = t; }\n";
     }
     o << "      if (lane < " << s.n0i << ") {\n";
     o << "        const unsigned long long it = (unsigned long long)(iv + (T)0.5);\n";
@@ -401,7 +468,6 @@ std::string gen_root_pass_source(const DFast &d, bool fp64, int block) {
   o << "    }\n";
   if (d.lanes) o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n";
   else o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
-  o << "    wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n";
   o << "  }\n";
   // root-to-inner partials: CTA-private -> global
   o << "  __syncthreads();\n";
@@ -591,7 +657,7 @@ cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid,
   a.v[A_NWORK] = (unsigned long long)d.nwork;
   a.v[A_WORK] = (unsigned long long)d.work;
   a.v[A_WSEG] = (unsigned long long)d.wseg;
-  a.v[A_TICKET] = (unsigned long long)d.ticket;
+  a.v[A_WORKQ] = (unsigned long long)d.work_q;
   a.v[A_TABLE] = (unsigned long long)d.table;
   a.v[A_CODES] = (unsigned long long)d.codes;
   a.v[A_PHI0F] = (unsigned long long)d.phi0f;
@@ -607,7 +673,7 @@ cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid,
   f.v[F_NWORK] = (unsigned long long)d.nwork;
   f.v[F_WORK] = (unsigned long long)d.work;
   f.v[F_WSEG] = (unsigned long long)d.wseg;
-  f.v[F_TICKET] = (unsigned long long)d.ticket;
+  f.v[F_WORKQ] = (unsigned long long)d.work_q;
   f.v[F_TABLE] = (unsigned long long)d.table;
   f.v[F_CODES] = (unsigned long long)d.codes;
   f.v[F_PHI0F] = (unsigned long long)d.phi0f;

@@ -35,11 +35,12 @@ GenRootPass gen_root_pass(const DFast &d, bool fp64, int device, const std::vect
 // and source.
 struct FamilyLayout {
   int rs;
+  int nfull, tew;  // FP32 rows: full 16-byte planes and the element width (words) of the tail plane
   bool pi_smem;  // integral root-to-inner partials in shared memory (also when the float ones are not)
   size_t off_tab, off_code, off_pf, off_pi, off_h, off_b4f, off_b4i, smem;
 };
 enum FamArg {
-  F_NWORK, F_WORK, F_WSEG, F_TICKET, F_TABLE, F_CODES, F_PHI0F, F_PHI0I, F_PHI1F, F_PHI1I, F_P3F, F_P3F32, F_P3I,
+  F_NWORK, F_WORK, F_WSEG, F_WORKQ, F_TABLE, F_CODES, F_PHI0F, F_PHI0I, F_PHI1F, F_PHI1I, F_P3F, F_P3F32, F_P3I,
   F_FSUM, F_ICNT, F_KC, F_X0, F_OV0 = F_X0 + 6, F_NARGS = F_OV0 + 6
 };
 FamilyLayout family_layout(const DFast &d, bool fp64, int block);
@@ -52,5 +53,22 @@ cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid,
 
 // The source text that gen_root_pass compiles for d (for tests and inspection).
 std::string gen_root_pass_source(const DFast &d, bool fp64, int block);
+
+// Source of the warp's reduce-scatter of the V per-lane segment sums acc[0..V) of a work item
+// into r_[]: with V <= 32, the values are padded to the next power of two PV = 2^L, reduced
+// over L lane bits by exchanging halves (PV - 1 shuffles) and over the remaining 5 - L lane bits
+// by butterflies, so that lane l holds value (l >> (5 - L)) in r_[0]; with V > 32, F = ceil(V / 32)
+// values per lane, lane l holding values l F .. l F + F - 1 in r_[0..F).
+struct WarpReduce {
+  int V, F, shift;  // shift = 5 - L (V <= 32), else 0
+  std::string src;
+  // lane that holds value q (and the register it is in)
+  int lane_of(int q) const { return F == 1 ? q << shift : q / F; }
+  int reg_of(int q) const { return F == 1 ? 0 : q % F; }
+};
+WarpReduce gen_warp_reduce(int V, const std::string &ind);
+// atomicAdd of every reduced value to dst[base + q] (the lane that owns it; zero values skipped)
+std::string gen_reduce_flush(const WarpReduce &w, const std::string &dst, const std::string &base,
+                             const std::string &ind);
 
 }  // namespace lmfao

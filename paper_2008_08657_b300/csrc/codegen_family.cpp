@@ -51,6 +51,8 @@ FamilyLayout family_layout(const DFast &d, bool fp64, int block) {
   const size_t ts = fp64 ? 8 : 4;
   const long long nkeys = d.ni ? d.nkeys : 0;
   L.rs = fp64 ? rup(nw, 2) : rup(nw + d.ncode, 4);
+  L.nfull = (nw + d.ncode) / 4;
+  L.tew = (nw + d.ncode) % 4 == 3 ? 4 : (nw + d.ncode) % 4;  // a tail of 1 or 2 words: 4- or 8-byte loads
   size_t off = 0;
   auto region = [&](size_t bytes) {
     size_t at = off;
@@ -63,7 +65,7 @@ FamilyLayout family_layout(const DFast &d, bool fp64, int block) {
     // first try the integral partials in shared memory even when the float ones do not fit
     L.pi_smem = d.smem_p || (pass == 0 && d.n3i > 0);
     off = 0;
-    L.off_tab = region(ts * (size_t)nkeys * L.rs);
+    L.off_tab = region(fp64 ? ts * (size_t)nkeys * L.rs : 4 * (size_t)nkeys * (4 * L.nfull + L.tew));
     L.off_code = region(fp64 ? 4 * (size_t)nkeys * d.ncode : 0);
     L.off_pf = region(d.smem_p ? ts * (size_t)nkeys * d.n3f * ls : 0);
     L.off_pi = region(L.pi_smem ? pi_bytes : 0);
@@ -113,7 +115,24 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   const FamilyLayout L = family_layout(d, fp64, block);
   const int nw = d.ni ? d.nw : 1, nm = d.nm, nx = d.nx;
   const long long nkeys = d.ni ? d.nkeys : 0;
-  const int V = nm * nw, F = (V + 31) / 32, PV = 32 * F;
+  const int V = nm * nw;
+  // Histogram sets with few cells (such as one per leaf of a decision-tree level) are kept in
+  // registers: their float cells extend the per-lane segment sums acc[] (reduced over the warp
+  // with them), their integral cells sit in hri[] (summed with the warp's integer reduction).
+  // Every tuple of a warp then adds to registers instead of a few shared-memory cells that the
+  // whole warp would hit with serialised atomics.
+  std::vector<int> hoff(d.nb1, -1), hoffi(d.nb1, -1);
+  int VX = V, NRI = 0;
+  if (V <= 32)
+    for (int s = 0; s < d.nb1; ++s) {
+      const DFastB1 &b = d.b1[s];
+      if (b.G <= 8 && VX + b.G * b.nf <= 32 && NRI + b.G * b.ni <= 8) {
+        hoff[s] = VX;
+        hoffi[s] = NRI;
+        VX += b.G * b.nf;
+        NRI += b.G * b.ni;
+      }
+    }
   const int ls = std::max(1, d.b3leaf);
   auto xidx = [&](int slot) {
     for (int i = 0; i < nx; ++i)
@@ -127,10 +146,13 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "struct Work { long long r0; int seg; int len; };\n";
   o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", 1) lmfao_gen_root_pass(const GenArgs a) {\n";
   o << "  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n";
-  o << "  const long long nwork = (long long)a.v[" << F_NWORK << "];\n";
+  // this CTA's work items (a contiguous range of about 1/G of the tuples) and its ticket
   o << "  const Work *__restrict__ work = (const Work *)a.v[" << F_WORK << "];\n";
   o << "  const unsigned long long *__restrict__ wseg = (const unsigned long long *)a.v[" << F_WSEG << "];\n";
-  o << "  unsigned int *ticket = (unsigned int *)a.v[" << F_TICKET << "];\n";
+  o << "  const int *__restrict__ wq = (const int *)a.v[" << F_WORKQ << "];\n";
+  o << "  const int ib = wq[" << kWorkQ << " * blockIdx.x / gridDim.x];\n";
+  o << "  const int nwork = wq[" << kWorkQ << " * (blockIdx.x + 1) / gridDim.x];  // end of the range\n";
+  o << "  __shared__ unsigned int ticket;\n";
   o << "  const T *__restrict__ gtab = (const T *)a.v[" << F_TABLE << "];\n";
   o << "  const int *__restrict__ gcod = (const int *)a.v[" << F_CODES << "];\n";
   o << "  T *phi0f = (T *)a.v[" << F_PHI0F << "];\n";
@@ -170,15 +192,22 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "  unsigned int *b4i = (unsigned int *)(smem + " << L.off_b4i << ");\n";
   // staging: planar inner rows (values, then codes as int bits in FP32), zeroed accumulators
   if (d.ni) {
-    const int vw = fp64 ? 2 : 4;
-    o << "  for (int i = tid; i < " << nkeys * L.rs << "; i += " << block << ") {\n";
-    o << "    const int k = i / " << L.rs << ", c = i - k * " << L.rs << ";\n";
+    const int rsw = fp64 ? L.rs : 4 * L.nfull + L.tew;  // staged words per row
+    o << "#pragma unroll 4\n";
+    o << "  for (int i = tid; i < " << nkeys * rsw << "; i += " << block << ") {\n";
+    o << "    const int k = i / " << rsw << ", c = i - k * " << rsw << ";\n";
     o << "    T t = (T)0;\n";
     o << "    if (c < " << nw << ") t = gtab[(long long)k * " << nw << " + c];\n";
     if (!fp64)
       o << "    else if (c < " << nw + d.ncode << ") t = __int_as_float(gcod[(long long)k * " << d.ncode << " + c - " << nw
         << "]);\n";
-    o << "    tab[(c / " << vw << ") * " << nkeys * vw << " + k * " << vw << " + c % " << vw << "] = t;\n  }\n";
+    if (fp64) {
+      o << "    tab[(c / 2) * " << nkeys * 2 << " + k * 2 + c % 2] = t;\n  }\n";
+    } else {
+      o << "    if (c < " << 4 * L.nfull << ") tab[(c / 4) * " << nkeys * 4 << " + k * 4 + c % 4] = t;\n";
+      o << "    else tab[" << (long long)L.nfull * nkeys * 4 << " + k * " << L.tew << " + c - " << 4 * L.nfull
+        << "] = t;\n  }\n";
+    }
     if (fp64 && d.ncode)
       o << "  for (int i = tid; i < " << nkeys * d.ncode << "; i += " << block << ") tcode[i] = gcod[i];\n";
   }
@@ -190,24 +219,31 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     << ") hf0[i] = 0.f;\n";
   o << "  for (int i = tid; i < " << d.b4_fcells << "; i += " << block << ") b4f[i] = (T)0;\n";
   o << "  for (int i = tid; i < " << d.b4_icells << "; i += " << block << ") b4i[i] = 0u;\n";
+  o << "  if (tid == 0) ticket = 0u;\n";
   o << "  __syncthreads();\n";
 
   // ---------------------------------------------------------------- per tuple
   o << "  auto tuple = [&](const int k";
   for (int i = 0; i < nx; ++i) o << ", const float xr" << i;
-  o << ", const unsigned int obits, T (&acc)[" << V << "], const T wsT, const unsigned long long ws) {\n";
+  o << ", const unsigned int obits, T (&acc)[" << VX << "], unsigned int (&hri)[" << std::max(1, NRI)
+    << "], const T wsT, const unsigned long long ws) {\n";
   std::vector<std::string> v(nw), code(d.ncode);
   if (d.ni) {
     static const char *c4[4] = {"x", "y", "z", "w"};
     if (!fp64) {
-      for (int q = 0; q < L.rs / 4; ++q)
+      for (int q = 0; q < L.nfull; ++q)
         o << "    const float4 t" << q << " = reinterpret_cast<const float4 *>(tab)[" << (long long)q * nkeys
           << " + k];\n";
-      for (int w = 0; w < nw; ++w) v[w] = "t" + std::to_string(w / 4) + "." + c4[w % 4];
-      for (int c = 0; c < d.ncode; ++c) {
-        const int p = nw + c;
-        code[c] = "__float_as_int(t" + std::to_string(p / 4) + "." + c4[p % 4] + ")";
-      }
+      const char *tt = L.tew == 4 ? "float4" : L.tew == 2 ? "float2" : "float";
+      if (L.tew)
+        o << "    const " << tt << " tt = reinterpret_cast<const " << tt << " *>(tab + " << (long long)L.nfull * nkeys * 4
+          << ")[k];\n";
+      auto word = [&](int p) {
+        if (p < 4 * L.nfull) return "t" + std::to_string(p / 4) + "." + c4[p % 4];
+        return L.tew == 1 ? std::string("tt") : "tt." + std::string(c4[p - 4 * L.nfull]);
+      };
+      for (int w = 0; w < nw; ++w) v[w] = word(w);
+      for (int c = 0; c < d.ncode; ++c) code[c] = "__float_as_int(" + word(nw + c) + ")";
     } else {
       for (int q = 0; q < L.rs / 2; ++q)
         o << "    const double2 t" << q << " = reinterpret_cast<const double2 *>(tab)[" << (long long)q * nkeys
@@ -281,12 +317,24 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
         << "; }\n";
     }
     o << "      if (ok) {\n";
-    for (int c = 0; c < b.nf; ++c)
-      o << "        { const T val = " << sel_u(b.fj[c]) << " * " << v[b.fw[c]] << "; if (val != (T)0) atomicAdd(hf + "
-        << b.smem_f << " + g * " << b.nf << " + " << c << ", (float)val); }\n";
-    for (int c = 0; c < b.ni; ++c)
-      o << "        { const T val = " << sel_u(b.ij[c]) << " * " << v[b.iw[c]] << "; if (val != (T)0) atomicAdd(hi + "
-        << b.smem_i << " + g * " << b.ni << " + " << c << ", (unsigned int)val); }\n";
+    if (hoff[s] >= 0) {
+      for (int c = 0; c < b.nf; ++c) o << "        const T vf" << c << " = " << sel_u(b.fj[c]) << " * " << v[b.fw[c]] << ";\n";
+      for (int c = 0; c < b.ni; ++c)
+        o << "        const unsigned int vi" << c << " = (unsigned int)(" << sel_u(b.ij[c]) << " * " << v[b.iw[c]] << ");\n";
+      for (int gg = 0; gg < b.G; ++gg) {
+        o << "        if (g == " << gg << ") {";
+        for (int c = 0; c < b.nf; ++c) o << " acc[" << hoff[s] + gg * b.nf + c << "] += vf" << c << ";";
+        for (int c = 0; c < b.ni; ++c) o << " hri[" << hoffi[s] + gg * b.ni + c << "] += vi" << c << ";";
+        o << " }\n";
+      }
+    } else {
+      for (int c = 0; c < b.nf; ++c)
+        o << "        { const T val = " << sel_u(b.fj[c]) << " * " << v[b.fw[c]] << "; if (val != (T)0) atomicAdd(hf + "
+          << b.smem_f << " + g * " << b.nf << " + " << c << ", (float)val); }\n";
+      for (int c = 0; c < b.ni; ++c)
+        o << "        { const T val = " << sel_u(b.ij[c]) << " * " << v[b.iw[c]] << "; if (val != (T)0) atomicAdd(hi + "
+          << b.smem_i << " + g * " << b.ni << " + " << c << ", (unsigned int)val); }\n";
+    }
     o << "      }\n    }\n";
   }
   // root-to-inner partials (split by leaf)
@@ -309,7 +357,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     o << "    }\n";
   }
   // CTA-private items: those of every filter, then those of the tuple's filter
-  auto b4_item = [&](int i) {
+  auto b4_item = [&](int i, const std::string &off) {
     o << "      { const T val = " << sel_u(d.b4_j[i]) << " * " << v[d.b4_w[i]] << ";\n";
     o << "        if (val != (T)0) {\n          long long cell = 0;\n          bool ok = true;\n";
     for (int gi = d.b4_g0[i]; gi < d.b4_g0[i] + d.b4_ng[i]; ++gi) {
@@ -319,22 +367,60 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     }
     o << "          if (ok) ";
     if (d.b4_int[i])
-      o << "atomicAdd(b4i + " << d.b4_so[i] << " + cell * " << d.b4_cellmul[i]
+      o << "atomicAdd(b4i + " << d.b4_so[i] << off << " + cell * " << d.b4_cellmul[i]
         << ", (unsigned int)val * (unsigned int)ws);\n";
     else
-      o << "atomicAdd(b4f + " << d.b4_so[i] << " + cell * " << d.b4_cellmul[i] << ", val * wsT);\n";
+      o << "atomicAdd(b4f + " << d.b4_so[i] << off << " + cell * " << d.b4_cellmul[i] << ", val * wsT);\n";
     o << "        }\n      }\n";
   };
   if (d.nb4) {
     o << "    {\n";
-    for (int i = d.b4_off[0]; i < d.b4_off[1]; ++i) b4_item(i);
+    for (int i = d.b4_off[0]; i < d.b4_off[1]; ++i) b4_item(i, "");
     o << "    }\n";
-    if (d.nfam) {
+    // Filters whose items differ only by a constant shift of their output cells per filter
+    // index (the leaves of a decision-tree level ask the same questions) run one copy of the
+    // items with the tuple's filter index in the address: no divergence over the filters.
+    const int n0 = d.nfam ? d.b4_off[2] - d.b4_off[1] : 0;
+    bool uniform = d.nfam > 1 && n0 > 0;
+    long long dint = 0, dflt = 0;  // per-filter shift of the integral / float cells
+    bool hint = false, hflt = false;
+    for (int f = 1; f < d.nfam && uniform; ++f) {
+      if (d.b4_off[f + 2] - d.b4_off[f + 1] != n0) { uniform = false; break; }
+      for (int k = 0; k < n0 && uniform; ++k) {
+        const int a = d.b4_off[1] + k, b = d.b4_off[f + 1] + k;
+        if (d.b4_j[a] != d.b4_j[b] || d.b4_w[a] != d.b4_w[b] || d.b4_int[a] != d.b4_int[b] ||
+            d.b4_ng[a] != d.b4_ng[b] || d.b4_cellmul[a] != d.b4_cellmul[b]) {
+          uniform = false;
+          break;
+        }
+        for (int g = 0; g < d.b4_ng[a] && uniform; ++g) {
+          const DGroupRef &qa = grefs4[d.b4_g0[a] + g], &qb = grefs4[d.b4_g0[b] + g];
+          if (qa.src != qb.src || qa.a != qb.a || qa.b != qb.b || qa.kind != qb.kind || qa.thr0 != qb.thr0 ||
+              qa.nthr != qb.nthr || qa.stride != qb.stride)
+            uniform = false;
+        }
+        long long &dl = d.b4_int[a] ? dint : dflt;
+        bool &has = d.b4_int[a] ? hint : hflt;
+        const long long sh = (long long)(d.b4_so[b] - d.b4_so[a]);
+        if (sh % f) uniform = false;
+        else if (!has) { dl = sh / f; has = true; }
+        else if (dl != sh / f) uniform = false;
+      }
+    }
+    if (uniform) {
+      o << "    if (leaf >= 0) {\n";
+      o << "      const int lo_i = leaf * " << dint << ", lo_f = leaf * " << dflt << ";\n";
+      for (int k = 0; k < n0; ++k) {
+        const int i = d.b4_off[1] + k;
+        b4_item(i, d.b4_int[i] ? " + lo_i" : " + lo_f");
+      }
+      o << "    }\n";
+    } else if (d.nfam) {
       o << "    switch (leaf) {\n";
       for (int f = 0; f < d.nfam; ++f) {
         if (d.b4_off[f + 2] <= d.b4_off[f + 1]) continue;
         o << "    case " << f << ": {\n";
-        for (int i = d.b4_off[f + 1]; i < d.b4_off[f + 2]; ++i) b4_item(i);
+        for (int i = d.b4_off[f + 1]; i < d.b4_off[f + 2]; ++i) b4_item(i, "");
         o << "      break;\n    }\n";
       }
       o << "    default: break;\n    }\n";
@@ -360,9 +446,9 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     if (d.ni) o << ind << "kn = reinterpret_cast<const int4 *>(kc)[" << q << "];\n";
     for (int i = 0; i < nx; ++i) o << ind << "xn" << i << " = " << xreg_load(i, q) << ";\n";
   };
-  o << "  long long wi;\n";
-  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
-  o << "    wi = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
+  o << "  int wi;\n";
+  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(&ticket, 1u);\n";
+  o << "    wi = ib + (int)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  Work wk = {0, 0, 0};\n  unsigned long long ws = 0ull;\n";
   o << "  if (wi < nwork) { wk = work[wi]; ws = wseg[wk.seg]; }\n";
   o << "  long long qa = (wk.r0 + 3) >> 2, qe = (wk.r0 + wk.len) >> 2;\n";
@@ -372,18 +458,17 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "  long long q = qa + lane;\n  if (q < qe) {\n";
   quad_load("q", "    ");
   o << "  }\n";
-  // tickets are taken one item ahead: the next item's record is requested when this item starts
-  o << "  long long wn;\n";
-  o << "  {\n    unsigned int t = 0u;\n    if (lane == 0) t = atomicAdd(ticket, 1u);\n";
-  o << "    wn = (long long)__shfl_sync(0xffffffffu, t, 0);\n  }\n";
   o << "  while (wi < nwork) {\n";
-  o << "    unsigned int tnext = 0u;\n";
-  o << "    if (lane == 0) tnext = atomicAdd(ticket, 1u);  // the item after the next one\n";
+  o << "    int wn;  // the next item (shared-memory ticket): its record is requested now\n";
+  o << "    {\n      unsigned int t = 0u;\n      if (lane == 0) t = atomicAdd(&ticket, 1u);\n";
+  o << "      wn = ib + (int)__shfl_sync(0xffffffffu, t, 0);\n    }\n";
   o << "    Work wkn = {0, 0, 0};\n";
   o << "    if (wn < nwork) wkn = work[wn];  // used after the tuples of this item\n";
   o << "    const T wsT = (T)ws;\n";
-  o << "    T acc[" << V << "];\n";
-  o << "#pragma unroll\n    for (int i = 0; i < " << V << "; ++i) acc[i] = (T)0;\n";
+  o << "    T acc[" << VX << "];\n";
+  o << "#pragma unroll\n    for (int i = 0; i < " << VX << "; ++i) acc[i] = (T)0;\n";
+  o << "    unsigned int hri[" << std::max(1, NRI) << "];\n";
+  o << "#pragma unroll\n    for (int i = 0; i < " << std::max(1, NRI) << "; ++i) hri[i] = 0u;\n";
   o << "    if (ws != 0ull) {\n";
   // outer predicate bits of the segment
   o << "      unsigned int obits = 0u;\n";
@@ -409,7 +494,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "        else if (lane >= 8 && lane < 12) { if (te + (lane - 8) < rend) r = te + (lane - 8); }\n";
   o << "        if (r >= 0) tuple(" << (d.ni ? "kc[r]" : "0");
   for (int i = 0; i < nx; ++i) o << ", (float)xc" << i << "[r]";
-  o << ", obits, acc, wsT, ws);\n      }\n";
+  o << ", obits, acc, hri, wsT, ws);\n      }\n";
   o << "      for (; q < qe; q += 32) {\n";
   if (d.ni) o << "        const int4 kk = kn;\n";
   for (int i = 0; i < nx; ++i) o << "        const " << xreg_type(i) << " xk" << i << " = xn" << i << ";\n";
@@ -420,7 +505,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   for (int u = 0; u < 4; ++u) {
     o << "        tuple(" << (d.ni ? std::string("kk.") + comp[u] : std::string("0"));
     for (int i = 0; i < nx; ++i) o << ", " << xcomp(i, "xk" + std::to_string(i), u);
-    o << ", obits, acc, wsT, ws);\n";
+    o << ", obits, acc, hri, wsT, ws);\n";
   }
   o << "      }\n    }\n";
   o << "    unsigned long long wsn = 0ull;\n";
@@ -432,25 +517,36 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   o << "    }\n";
   o << "    if (ws != 0ull) {\n";
   // per-segment sums: reduce-scatter over the warp
-  o << "      T r_[" << PV << "];\n";
-  o << "#pragma unroll\n      for (int i = 0; i < " << PV << "; ++i) r_[i] = i < " << V << " ? acc[i < " << V
-    << " ? i : 0] : (T)0;\n";
-  o << "#pragma unroll\n      for (int lvl = 0; lvl < 5; ++lvl) {\n";
-  o << "        const int o = 16 >> lvl, h = " << PV << " >> (lvl + 1);\n";
-  o << "        const bool up = (lane & o) != 0;\n";
-  o << "#pragma unroll\n        for (int i = 0; i < h; ++i) {\n";
-  o << "          const T send = up ? r_[i] : r_[i + h];\n";
-  o << "          const T keep = up ? r_[i + h] : r_[i];\n";
-  o << "          r_[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);\n        }\n      }\n";
-  for (int e = 0; e < F; ++e)
-    o << "      { const int i = lane * " << F << " + " << e << "; if (i < " << V << " && r_[" << e
-      << "] != (T)0) atomicAdd(phi0f + (long long)wk.seg * " << V << " + i, r_[" << e << "]); }\n";
+  const WarpReduce wr = gen_warp_reduce(VX, "      ");
+  o << wr.src;
+  if (VX == V) {
+    o << gen_reduce_flush(wr, "phi0f", "(long long)wk.seg * " + std::to_string(V), "      ");
+  } else {  // the segment sums, then the float cells of the register histograms
+    const int mask = (1 << wr.shift) - 1;
+    o << "      { const int i = lane >> " << wr.shift << ";\n";
+    o << "        if (" << (mask ? "(lane & " + std::to_string(mask) + ") == 0 && " : "") << "r_[0] != (T)0) {\n";
+    o << "          if (i < " << V << ") atomicAdd(phi0f + (long long)wk.seg * " << V << " + i, r_[0]);\n";
+    for (int s = 0; s < d.nb1; ++s) {
+      const DFastB1 &b = d.b1[s];
+      if (hoff[s] < 0 || !b.nf) continue;
+      o << "          else if (i >= " << hoff[s] << " && i < " << hoff[s] + b.G * b.nf << ") atomicAdd(phi1f + (long long)wk.seg * "
+        << d.phi1f_seg << " + " << b.gbase_f << " + (i - " << hoff[s] << "), (float)r_[0]);\n";
+    }
+    o << "        }\n      }\n";
+  }
+  for (int s = 0; s < d.nb1; ++s) {  // the integral cells of the register histograms
+    const DFastB1 &b = d.b1[s];
+    for (int k = 0; hoffi[s] >= 0 && k < b.G * b.ni; ++k)
+      o << "      { const unsigned int x = __reduce_add_sync(0xffffffffu, hri[" << hoffi[s] + k
+        << "]); if (lane == 0 && x) atomicAdd(phi1i + (long long)wk.seg * " << d.phi1i_seg << " + " << b.gbase_i << " + "
+        << k << ", x); }\n";
+  }
   if (d.n0i) {
     o << "      {\n        T iv = (T)0;\n";
     for (int e = 0; e < d.n0i; ++e) {
       const int qq = d.i0j[e] * nw + d.i0w[e];
-      o << "        { const T t = __shfl_sync(0xffffffffu, r_[" << qq % F << "], " << qq / F << "); if (lane == " << e
-        << ") iv = t; }\n";
+      o << "        { const T t = __shfl_sync(0xffffffffu, r_[" << wr.reg_of(qq) << "], " << wr.lane_of(qq)
+        << "); if (lane == " << e << ") iv = t; }\n";
     }
     o << "        if (lane < " << d.n0i << ") {\n";
     o << "          const unsigned long long it = (unsigned long long)(iv + (T)0.5);\n";
@@ -460,6 +556,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
     o << "      __syncwarp();\n";
     for (int s = 0; s < d.nb1; ++s) {
       const DFastB1 &b = d.b1[s];
+      if (hoff[s] >= 0) continue;  // in registers
       if (b.nf)
         o << "      for (int i = lane; i < " << (long long)b.G * b.nf << "; i += 32) { const float x = hf[" << b.smem_f
           << " + i]; if (x != 0.f) { hf[" << b.smem_f << " + i] = 0.f; atomicAdd(phi1f + (long long)wk.seg * "
@@ -473,7 +570,7 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
   }
   o << "    }\n";
   o << "    wi = wn;\n    wk = wkn;\n    ws = wsn;\n    qa = qan;\n    qe = qen;\n";
-  o << "    wn = (long long)__shfl_sync(0xffffffffu, tnext, 0);\n  }\n";
+  o << "  }\n";
   // end of the CTA: shared partials and CTA-private items to the outputs
   o << "  __syncthreads();\n";
   if (d.smem_p)

@@ -130,11 +130,11 @@ __global__ void __launch_bounds__(256) proj_d0_kernel(const DComb4 dp) {
   }
   if (jb.x) {
     if (si) {
-      if (dp.need_d0) atomicAdd(dp.yd0_i + d0 * dp.njobs + J, si);
+      if (dp.need_d0) atomicAdd(dp.yd0_i + (int64_t)J * dp.dom0 + d0, si);
       atomicAdd(dp.yall_i + J, si);
     }
   } else if (sf != 0.0) {
-    if (dp.need_d0) atomicAdd(dp.yd0_f + d0 * dp.njobs + J, sf);
+    if (dp.need_d0) atomicAdd(dp.yd0_f + (int64_t)J * dp.dom0 + d0, sf);
     atomicAdd(dp.yall_f + J, sf);
   }
 }
@@ -158,10 +158,11 @@ __global__ void tab_kernel(const DComb4 dp, int cls) {
       double v = 0.0;
       unsigned long long iv = 0ull;
       if (live) psi_at(d, tb.t[k], d0, d1, v, iv, dp.skip_counts != 0);
-      tb.pf[x * tb.nt + k] = v;
-      tb.pi[x * tb.nt + k] = iv;
+      const int64_t at = cls == 3 ? x * tb.nt + k : k * nv + x;  // classes 1, 2: by term, then digit
+      tb.pf[at] = v;
+      tb.pi[at] = iv;
     } else {
-      tb.cell[x * tb.ng + (k - tb.nt)] =
+      tb.cell[cls == 3 ? x * tb.ng + (k - tb.nt) : (k - tb.nt) * nv + x] =
           live ? cell_at(d, tb.g[k - tb.nt], d0, d1, dp.og_cstride) : -1;
     }
   }
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(256) proj_d1_kernel(const DComb4 dp) {
     }
   }
   if (dp.need_d1) {
-    if (jb.x) { if (si) atomicAdd(dp.yd1_i + (int64_t)v * dp.njobs + J, si); }
-    else if (sf != 0.0) atomicAdd(dp.yd1_f + (int64_t)v * dp.njobs + J, sf);
+    if (jb.x) { if (si) atomicAdd(dp.yd1_i + (int64_t)J * dp.dom1 + v, si); }
+    else if (sf != 0.0) atomicAdd(dp.yd1_f + (int64_t)J * dp.dom1 + v, sf);
   }
 }
 
@@ -268,18 +269,18 @@ __global__ void __launch_bounds__(256) entry_kernel(const DComb4 dp) {
       if (yint_col) yi = dp.yall_i[J];
       else yf = dp.yall_f[J];
     } else {
-      const int64_t at = (int64_t)x * dp.njobs + J;
+      const int64_t at = (int64_t)J * n + x;
       if (yint_col) yi = e.cls == 1 ? dp.yd0_i[at] : dp.yd1_i[at];
       else yf = e.cls == 1 ? dp.yd0_f[at] : dp.yd1_f[at];
     }
     if (yi == 0ull && yf == 0.0) continue;
-    const long long cell = e.cls == 0 ? 0 : tb.cell[(int64_t)x * tb.ng + e.tog];
+    const long long cell = e.cls == 0 ? 0 : tb.cell[(int64_t)e.tog * n + x];
     if (cell < 0) continue;
     double pv = 1.0;
     unsigned long long pi = 1ull;
     if (e.cls != 0) {
-      pv = tb.pf[(int64_t)x * tb.nt + e.psi];
-      pi = tb.pi[(int64_t)x * tb.nt + e.psi];
+      pv = tb.pf[(int64_t)e.psi * n + x];
+      pi = tb.pi[(int64_t)e.psi * n + x];
     }
     if (integ) atomicAdd(si + cell, pi * yi);
     else atomicAdd(sf + cell, pv * (yint_col ? (double)yi : yf));
@@ -295,7 +296,162 @@ __global__ void __launch_bounds__(256) entry_kernel(const DComb4 dp) {
   }
 }
 
+
+// ------------------------------------------------------------------ streaming form
+// CTA (x, y) covers the minor digits [x c1, x c1 + c1) and the major digits [y c0, y c0 + c0).
+// Per major digit it stages the tile row's per-segment sums (a warp per segment, lanes over
+// the jobs: coalesced), adds them to the CTA's minor-digit sums (each element by the thread
+// that staged it), writes the row's major-digit partial, and lets each class 3 entry (one per
+// thread) add the row's terms x sums into its cells. Every per-segment sum is read once.
+template <typename T>
+__global__ void proj_stream_kernel(const DComb4 dp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DComb2 &d = dp.c;
+  const int nj = dp.njobs, c1 = dp.c1;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
+  const DTab4 &tb = dp.tab[3];
+  const int nt3 = dp.fused3 ? tb.nt : 0, ng3 = dp.fused3 ? tb.ng : 0;
+  unsigned long long *stage = reinterpret_cast<unsigned long long *>(smem);
+  unsigned long long *acc1 = stage + (size_t)c1 * nj;
+  unsigned long long *slots = acc1 + (size_t)c1 * nj;
+  double *tpf = reinterpret_cast<double *>(slots + (dp.fused3 ? dp.nslots3 : 0));  // the row's class 3 terms
+  unsigned long long *tpi = reinterpret_cast<unsigned long long *>(tpf + (size_t)c1 * nt3);
+  long long *tcl = reinterpret_cast<long long *>(tpi + (size_t)c1 * nt3);            // and cells
+  int2 *sjob = reinterpret_cast<int2 *>(tcl + (size_t)c1 * ng3);                     // job descriptors
+  for (int J = tid; J < nj; J += bs) sjob[J] = dp.job[J];
+  const int x0 = blockIdx.x * c1, xn = min(c1, dp.dom1 - x0);
+  const int y0 = blockIdx.y * dp.c0, y1 = min(dp.dom0, y0 + dp.c0);
+  for (int i = tid; i < c1 * nj; i += bs) acc1[i] = 0ull;
+  if (dp.fused3)
+    for (int i = tid; i < dp.nslots3; i += bs) slots[i] = 0ull;
+  DEntry4 e{};
+  int2 ejb = make_int2(0, 0);
+  const bool has_e = dp.fused3 && tid < dp.nent3;
+  if (has_e) {
+    e = dp.ent3[tid];
+    ejb = dp.job[e.job];
+  }
+  __syncthreads();  // sjob
+  for (int d0 = y0; d0 < y1; ++d0) {
+    __syncthreads();  // the previous row's readers are done with stage
+    for (int r = warp; r < xn; r += nwarp) {
+      const int64_t s = (int64_t)d0 * dp.dom1 + x0 + r;
+      const bool live = d.wseg[s] != 0ull;
+#pragma unroll 4
+      for (int J = lane; J < nj; J += 32) {
+        const int2 jb = sjob[J];
+        unsigned long long w = 0ull;
+        if (jb.x) {
+          const unsigned long long y = live ? yint(d, s, jb.y) : 0ull;
+          w = y;
+          acc1[r * nj + J] += y;
+        } else {
+          const double y = live ? yflt<T>(d, s, jb.y) : 0.0;
+          w = (unsigned long long)__double_as_longlong(y);
+          acc1[r * nj + J] = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)acc1[r * nj + J]) + y);
+        }
+        stage[r * nj + J] = w;
+      }
+      for (int t = lane; t < nt3; t += 32) {
+        tpf[r * nt3 + t] = tb.pf[s * tb.nt + t];
+        tpi[r * nt3 + t] = tb.pi[s * tb.nt + t];
+      }
+      for (int g = lane; g < ng3; g += 32) tcl[r * ng3 + g] = tb.cell[s * tb.ng + g];
+    }
+    __syncthreads();
+    // the row's major-digit partial
+    for (int J = tid; J < nj; J += bs) {
+      const int2 jb = sjob[J];
+      unsigned long long si = 0ull;
+      double sf = 0.0;
+      for (int r = 0; r < xn; ++r) {
+        const unsigned long long w = stage[r * nj + J];
+        if (jb.x) si += w;
+        else sf += __longlong_as_double((long long)w);
+      }
+      dp.yd0p[((size_t)blockIdx.x * dp.dom0 + d0) * nj + J] = jb.x ? si : (unsigned long long)__double_as_longlong(sf);
+    }
+    // class 3 entries of this thread
+    if (has_e) {
+      for (int r = 0; r < xn; ++r) {
+        const long long cl = tcl[r * ng3 + e.tog];  // -1 also where w_s = 0
+        if (cl < 0) continue;
+        const unsigned long long w = stage[r * nj + e.job];
+        if (e.flags & 1) {
+          slots[e.pad + cl] += tpi[r * nt3 + e.psi] * (ejb.x ? w : 0ull);
+        } else {
+          const double y = ejb.x ? (double)w : __longlong_as_double((long long)w);
+          const double v = tpf[r * nt3 + e.psi] * y;
+          slots[e.pad + cl] = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)slots[e.pad + cl]) + v);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < xn * nj; i += bs) {
+    const int r = i / nj, J = i - r * nj;
+    dp.yd1p[((size_t)blockIdx.y * dp.dom1 + x0 + r) * nj + J] = acc1[i];
+  }
+  if (has_e) {
+    const long long ncell = dp.og_ncells[e.og];
+    const int r0 = d.og_off[e.og], r1 = d.og_off[e.og + 1];
+    for (long long c = 0; c < ncell; ++c) {
+      const unsigned long long w = slots[e.pad + c];
+      if (!w) continue;
+      long long g = 0;
+      for (int r = r0; r < r1; ++r) g += ((c / dp.og_cstride[r]) % dp.og_dom[r]) * d.grefs[r].stride;
+      const long long idx = e.out + (g + e.icell) * e.cellmul;
+      if (e.flags & 1) atomicAdd(d.icnt + idx, w);
+      else atomicAdd(d.fsum + idx, __longlong_as_double((long long)w));
+    }
+  }
+}
+
+// Sums of the partial projections: Yd0 (and the column totals) over the minor-digit tiles,
+// Yd1 over the major-digit tiles.
+__global__ void proj_reduce_kernel(const DComb4 dp) {
+  const int nj = dp.njobs;
+  const int64_t n0 = (int64_t)dp.dom0 * nj, n1 = dp.need_d1 ? (int64_t)dp.dom1 * nj : 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += stride) {
+    const bool one = i >= n0;
+    const int64_t k = one ? i - n0 : i;
+    const int J = (int)(k % nj);
+    const int2 jb = dp.job[J];
+    const int parts = one ? dp.ny : dp.nx;
+    const int64_t pstride = (one ? (int64_t)dp.dom1 : (int64_t)dp.dom0) * nj;
+    const unsigned long long *src = (one ? dp.yd1p : dp.yd0p) + k;
+    unsigned long long si = 0ull;
+    double sf = 0.0;
+    for (int p = 0; p < parts; ++p) {
+      const unsigned long long w = src[p * pstride];
+      if (jb.x) si += w;
+      else sf += __longlong_as_double((long long)w);
+    }
+    const int64_t dig = k / nj;
+    if (one) {
+      const int64_t at = (int64_t)J * dp.dom1 + dig;
+      if (jb.x) dp.yd1_i[at] = si;
+      else dp.yd1_f[at] = sf;
+    } else {
+      const int64_t at = (int64_t)J * dp.dom0 + dig;
+      if (jb.x) {
+        if (dp.need_d0) dp.yd0_i[at] = si;
+        if (si) atomicAdd(dp.yall_i + J, si);
+      } else {
+        if (dp.need_d0) dp.yd0_f[at] = sf;
+        if (sf != 0.0) atomicAdd(dp.yall_f + J, sf);
+      }
+    }
+  }
+}
+
 }  // namespace
+
+size_t combine4_stream_smem(const DComb4 &d) {
+  const size_t t3 = d.fused3 ? (size_t)d.nslots3 + (size_t)d.c1 * (2 * d.tab[3].nt + d.tab[3].ng) : 0;
+  return 8 * (2 * (size_t)d.c1 * d.njobs + t3 + (size_t)d.njobs);
+}
 
 void launch_combine4(const DComb4 &d, bool fp64, cudaStream_t s) {
   const int bs = 256;
@@ -304,6 +460,36 @@ void launch_combine4(const DComb4 &d, bool fp64, cudaStream_t s) {
     const int64_t nv = cls == 1 ? d.dom0 : cls == 2 ? d.dom1 : d.c.nseg;
     const int64_t n = nv * (int64_t)(d.tab[cls].nt + d.tab[cls].ng);
     if (n) tab_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 148 * 8), 256, 0, s>>>(d, cls);
+  }
+  if (d.stream) {
+    const size_t sm = combine4_stream_smem(d);
+    const dim3 grid((unsigned)d.nx, (unsigned)d.ny);
+    if (fp64) {
+      cudaFuncSetAttribute(proj_stream_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      proj_stream_kernel<double><<<grid, d.sblock, sm, s>>>(d);
+    } else {
+      cudaFuncSetAttribute(proj_stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      proj_stream_kernel<float><<<grid, d.sblock, sm, s>>>(d);
+    }
+    const int64_t nred = (int64_t)d.dom0 * d.njobs + (d.need_d1 ? (int64_t)d.dom1 * d.njobs : 0);
+    proj_reduce_kernel<<<(int)std::min<int64_t>((nred + 255) / 256, 148 * 8), 256, 0, s>>>(d);
+    if (d.nent3 && !d.fused3) {
+      const int etiles = (d.nent3 + bs - 1) / bs;
+      const int r3 = std::max(1, (2 * 148 + etiles - 1) / etiles);
+      const size_t sm3 = (size_t)8 * std::max(1, d.max_slots3);
+      if (fp64) {
+        cudaFuncSetAttribute(class3_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+        class3_kernel<double><<<dim3(r3, etiles), bs, sm3, s>>>(d);
+      } else {
+        cudaFuncSetAttribute(class3_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+        class3_kernel<float><<<dim3(r3, etiles), bs, sm3, s>>>(d);
+      }
+    }
+    if (d.nent012) {
+      const int wpb = std::max(1, std::min(8, (int)(48 * 1024 / (8 * std::max(1, d.max_cells)))));
+      entry_kernel<<<(d.nent012 + wpb - 1) / wpb, 32 * wpb, (size_t)8 * wpb * std::max(1, d.max_cells), s>>>(d);
+    }
+    return;
   }
   // about four CTAs per SM in each projection
   const int z0 = std::max(1, std::min(d.dom1, (4 * 148 + d.dom0 * tiles - 1) / (d.dom0 * tiles)));

@@ -542,6 +542,248 @@ __global__ void __launch_bounds__(256) block_z_kernel(DComb5 D) {
   if (gave_up && tid == 0) atomicOr(D.err, 8);
 }
 
+// ------------------------------------------------------------------ dense-B contraction
+// When every B term is one column of an outer view (or the constant 1) with no segment-digit
+// factor, a chunk's B operand is read straight from the view rows. block_zd_kernel keeps the
+// block's Z_p in registers, 4 x 4 tiles (4 B terms x 4 Y columns, read from shared memory with
+// one 16-byte load each per segment) of which each thread owns KT, accumulated over the block's
+// chunks and written once. The chunk's operands are staged by warps over rows and lanes over
+// columns (coalesced, no index division); the exact integral part is spread over all threads
+// and summed in shared memory. The small shared footprint leaves several CTAs per SM, so one
+// CTA's loads overlap another's multiply-adds.
+constexpr int kZq = 4;  // tile edge
+constexpr int kZl = 4;  // operand columns per lane in staging (Y and B of at most 128 columns)
+
+struct ZdLayout {
+  size_t ysf, bt, yi0, yi1, bti, lv, kmin, asv, zacc, bsrc, total;
+};
+__host__ __device__ inline ZdLayout zd_layout(const DComb3 &d, int kc, int ts) {
+  const int ny = d.nyf + d.nyi;
+  const size_t nyp = (size_t)(ny + kZq - 1) / kZq * kZq, nbp = (size_t)(d.nb + kZq - 1) / kZq * kZq;
+  ZdLayout L{};
+  size_t o = 0;
+  L.ysf = o; o += up16((size_t)kc * nyp * ts);
+  L.bt = o; o += up16((size_t)kc * nbp * ts);
+  L.yi0 = o; o += up16((size_t)kc * d.n0i * 8);
+  L.yi1 = o; o += up16((size_t)kc * (d.nyi - d.n0i) * 4);
+  L.bti = o; o += up16((size_t)kc * d.nbi * 8);
+  L.lv = o; o += up16((size_t)kc * 4);
+  L.kmin = o; o += up16((size_t)d.nouter * kc * 8);
+  L.asv = o; o += up16((size_t)d.nast * ts);
+  L.zacc = o; o += up16((size_t)d.nbi * d.nyi * 8);
+  L.bsrc = o; o += up16((size_t)d.nb * 8);
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float *p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void load(const double *p, double (&v)[4]) {
+    const double2 x = reinterpret_cast<const double2 *>(p)[0], y = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+};
+
+template <typename T, int KT>
+__global__ void __launch_bounds__(256) block_zd_kernel(DComb5 D) {
+  const DComb3 &d = D.c;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long akey[MAXOUT];
+  __shared__ int block_live;
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
+  const int kc = D.kc, m = (int)d.m, ny = d.nyf + d.nyi, nb = d.nb, nyi1 = d.nyi - d.n0i;
+  const int nyp = (ny + kZq - 1) / kZq * kZq, nbp = (nb + kZq - 1) / kZq * kZq;
+  const int nct = nyp / kZq, ntile = (nbp / kZq) * nct, nzi = d.nbi * d.nyi;
+  const ZdLayout L = zd_layout(d, kc, (int)sizeof(T));
+  T *ysf = (T *)(smem + L.ysf);
+  T *bt = (T *)(smem + L.bt);
+  unsigned long long *yi0 = (unsigned long long *)(smem + L.yi0);
+  unsigned int *yi1 = (unsigned int *)(smem + L.yi1);
+  unsigned long long *bti = (unsigned long long *)(smem + L.bti);
+  int *lv = (int *)(smem + L.lv);
+  long long *kmin = (long long *)(smem + L.kmin);
+  T *asv = (T *)(smem + L.asv);
+  unsigned long long *zacc = (unsigned long long *)(smem + L.zacc);
+  // the B terms' sources, read by every staged row
+  int2 *sbsrc = (int2 *)(smem + L.bsrc);
+  for (int b = tid; b < nb; b += bs) sbsrc[b] = D.bsrc[b];
+  for (int64_t p = blockIdx.x; p < d.nblocks; p += gridDim.x) {
+    const int64_t s0 = p * d.m;
+    // ---- prefix side (as in block_z_kernel): view keys, A terms, outer cells
+    if (tid < d.nouter) {
+      const DOuter &o = d.outer[tid];
+      int64_t k = 0;
+      for (int i = 0; i < d.seg.ndig; ++i)
+        if (o.dstride[i] && d.seg.radix[i] >= d.m) k += digit5(d.seg, s0, i) * o.dstride[i];
+      akey[tid] = k;
+    }
+    if (tid == 0) block_live = 0;
+    for (int i = tid; i < nzi; i += bs) zacc[i] = 0ull;
+    __syncthreads();
+    for (int j = tid; j < d.nast; j += bs) {
+      const int2 sc = d.astage[j];
+      const DOuter &o = d.outer[sc.x];
+      asv[j] = (T)__ldg(o.v.v64 + akey[sc.x] * o.v.ncols + sc.y);
+    }
+    __syncthreads();
+    {
+      T *ag = (T *)D.a + p * d.na;
+      unsigned long long *aig = D.ai + p * d.na;
+      for (int a = tid; a < d.na; a += bs) {
+        T v;
+        unsigned long long iv;
+        term5<T>(d.aterm[a], d.segfacs, d.apart, asv, d.seg, s0, v, iv);
+        ag[a] = v;
+        aig[a] = iv;
+      }
+      for (int g = tid; g < d.nog; g += bs) {
+        long long cell = 0;
+        for (int r = d.og_off[g]; r < d.og_off[g + 1] && cell >= 0; ++r) {
+          const DGroupRef q = d.grefs[r];
+          const long long code = q.src == 0 ? digit5(d.seg, s0, q.a)
+                                            : __ldg(d.outer[q.a].v.codes + akey[q.a] * d.outer[q.a].v.ncodes + q.b);
+          if (code < 0) cell = -1;
+          else cell += code * q.stride;
+        }
+        D.cells[p * d.nog + g] = cell;
+      }
+    }
+    T acc[KT][kZq * kZq];
+#pragma unroll
+    for (int t = 0; t < KT; ++t)
+#pragma unroll
+      for (int i = 0; i < kZq * kZq; ++i) acc[t][i] = T(0);
+    for (int k0 = 0; k0 < m; k0 += kc) {
+      const int kn = min(kc, m - k0);
+      const int64_t sb = s0 + k0;
+      // 1. liveness and the minor-digit part of each B-side view key
+      for (int i = tid; i < kn; i += bs) lv[i] = d.wseg[sb + i] != 0ull;
+      for (int o = 0; o < d.nouter; ++o)
+        for (int j = tid; j < kn; j += bs) {
+          const int jj = k0 + j;
+          long long k = 0;
+          for (int i = 0; i < d.seg.ndig; ++i)
+            if (d.outer[o].dstride[i] && d.seg.radix[i] < d.m)
+              k += ((jj / d.seg.radix[i]) % d.seg.dom[i]) * d.outer[o].dstride[i];
+          kmin[o * kc + j] = k;
+        }
+      __syncthreads();
+      // 2. operands, one warp per segment row: Y (integral columns also exactly) and B (zero
+      // on segments without outer partners; integral B terms also exactly)
+      for (int s = warp; s < kn; s += nwarp) {
+        const int64_t g = sb + s;
+        const T *f0 = (const T *)d.phi0f + g * d.n0f;
+        const float *f1 = d.phi1f + g * d.phi1f_seg;
+        const unsigned long long *i0 = d.phi0i + g * d.n0i;
+        const unsigned int *i1 = d.phi1i + g * d.phi1i_seg;
+#pragma unroll
+        for (int i = 0; i < kZl; ++i) {
+          const int c = lane + 32 * i;
+          if (c >= nyp) break;
+          T v = T(0);
+          // the Y array of column c: 0 float sums, 1 float cells, 2 integral sums, 3 integral cells
+          switch (c >= ny ? -1 : c < d.n0f ? 0 : c < d.nyf ? 1 : c < d.nyf + d.n0i ? 2 : 3) {
+            case 0: v = f0[c]; break;
+            case 1: v = (T)f1[c - d.n0f]; break;
+            case 2: {
+              const unsigned long long y = i0[c - d.nyf];
+              yi0[s * d.n0i + (c - d.nyf)] = y;
+              v = (T)y;
+              break;
+            }
+            case 3: {
+              const unsigned int y = i1[c - d.nyf - d.n0i];
+              yi1[s * nyi1 + (c - d.nyf - d.n0i)] = y;
+              v = (T)y;
+              break;
+            }
+            default: break;
+          }
+          ysf[s * nyp + c] = v;
+        }
+        const bool live = lv[s] != 0;
+#pragma unroll
+        for (int i = 0; i < kZl; ++i) {
+          const int b = lane + 32 * i;
+          if (b >= nbp) break;
+          T v = T(0);
+          unsigned long long iv = 0ull;
+          if (b < nb && live) {
+            const int2 src = sbsrc[b];
+            if (src.x < 0) {
+              v = T(1);
+              iv = 1ull;
+            } else {
+              const DOuter &o = d.outer[src.x];
+              const double x = __ldg(o.v.v64 + (akey[src.x] + kmin[src.x * kc + s]) * o.v.ncols + src.y);
+              v = (T)x;
+              iv = (unsigned long long)x;
+            }
+          }
+          bt[s * nbp + b] = v;
+          if (b < d.nbi) bti[s * d.nbi + b] = iv;
+        }
+        if (lane == 0 && live) block_live = 1;
+      }
+      __syncthreads();
+      // 3. the contraction into the register tiles
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int tile = tid + t * bs;
+        if (tile < ntile) {
+          const int b0 = (tile / nct) * kZq, c0 = (tile - (tile / nct) * nct) * kZq;
+          const T *br = bt + b0, *yr = ysf + c0;
+          for (int s = 0; s < kn; ++s, br += nbp, yr += nyp) {
+            T bv[4], yv[4];
+            Vec4<T>::load(br, bv);
+            Vec4<T>::load(yr, yv);
+#pragma unroll
+            for (int i = 0; i < kZq; ++i)
+#pragma unroll
+              for (int j = 0; j < kZq; ++j) acc[t][i * kZq + j] += bv[i] * yv[j];
+          }
+        }
+      }
+      // 4. integral B terms x integral Y columns, exactly: (output, 8-segment run) per thread
+      for (int w = tid; w < nzi * ((kn + 7) >> 3); w += bs) {
+        const int o = w % nzi, s1 = (w / nzi) * 8, s2 = min(kn, s1 + 8);
+        const int b = o / d.nyi, c = o - b * d.nyi;
+        unsigned long long z = 0;
+        for (int s = s1; s < s2; ++s)
+          z += bti[s * d.nbi + b] * (c < d.n0i ? yi0[s * d.n0i + c] : (unsigned long long)yi1[s * nyi1 + (c - d.n0i)]);
+        if (z) atomicAdd(zacc + o, z);
+      }
+      __syncthreads();
+    }
+    T *zg = (T *)D.z + p * (int64_t)nb * ny;
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int tile = tid + t * bs;
+      if (tile < ntile) {
+        const int b0 = (tile / nct) * kZq, c0 = (tile - (tile / nct) * nct) * kZq;
+#pragma unroll
+        for (int i = 0; i < kZq; ++i)
+#pragma unroll
+          for (int j = 0; j < kZq; ++j)
+            if (b0 + i < nb && c0 + j < ny) zg[(size_t)(b0 + i) * ny + c0 + j] = acc[t][i * kZq + j];
+      }
+    }
+    unsigned long long *zig = D.zi + p * (int64_t)nzi;
+    for (int i = tid; i < nzi; i += bs) zig[i] = zacc[i];
+    if (tid == 0) D.live[p] = block_live;
+    __syncthreads();
+  }
+}
+
 // SUM_p a(p) Z_p[b][c] per entry, one thread per (entry, range of blocks).
 template <typename T>
 __global__ void __launch_bounds__(256) block_entries_kernel(DComb5 D) {
@@ -589,11 +831,39 @@ __global__ void __launch_bounds__(256) block_entries_kernel(DComb5 D) {
 }  // namespace
 
 size_t combine5_smem(const DComb5 &D, bool fp64) {
+  if (D.dense) return zd_layout(D.c, D.kc, fp64 ? 8 : 4).total;
   return z5_layout(D.c, D.kc, D.npad, fp64 ? 8 : 4, D.tc).total;
+}
+
+static int zd_ntile(const DComb3 &d) {
+  const int ny = d.nyf + d.nyi;
+  return ((d.nb + kZq - 1) / kZq) * ((ny + kZq - 1) / kZq);
+}
+
+bool combine5_dense_fits(const DComb3 &d) {
+  const int ny = d.nyf + d.nyi;
+  return zd_ntile(d) <= 2 * 256 && (ny + kZq - 1) / kZq * kZq <= 32 * kZl && (d.nb + kZq - 1) / kZq * kZq <= 32 * kZl;
+}
+
+template <typename T, int KT>
+static void launch_zd(const DComb5 &D, size_t smem, cudaStream_t s) {
+  cudaFuncSetAttribute(block_zd_kernel<T, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 1, dev = 0, nsm = 148;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_zd_kernel<T, KT>, 256, smem);
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(D.c.nblocks, (int64_t)nsm * std::max(1, per_sm)));
+  block_zd_kernel<T, KT><<<grid, 256, smem, s>>>(D);
 }
 
 void launch_combine5_z(const DComb5 &D, bool fp64, cudaStream_t s) {
   const size_t smem = combine5_smem(D, fp64);
+  if (D.dense) {
+    const bool one = zd_ntile(D.c) <= 256;  // one tile per thread
+    if (fp64) one ? launch_zd<double, 1>(D, smem, s) : launch_zd<double, 2>(D, smem, s);
+    else one ? launch_zd<float, 1>(D, smem, s) : launch_zd<float, 2>(D, smem, s);
+    return;
+  }
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(D.c.nblocks, (int64_t)D.grid));
 #define LMFAO_Z5(TT, TCV)                                                                                    \
   {                                                                                                          \

@@ -1198,6 +1198,7 @@ void compute_multiplicities(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
     LMFAO_CUDA(cudaStreamSynchronize(s));
     v.maxmult = h;
     v.unique_keys = h <= 1;
+
     double b = std::max(1u, h);
     for (int c : t.children[r]) b *= P.views[c].count_bound;
     v.count_bound = b;
@@ -1283,6 +1284,20 @@ void setup_views(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, bool need32) {
     d.ncols = (int)v.cols.size();
     d.ncodes = (int)v.codes.size();
     d.unique = v.unique_keys ? 1 : 0;
+    d.nfac = (int)facs.size();
+    v.keyrow = nullptr;
+    if (v.unique_keys && v.nkeys < (int64_t(1) << 31) && Rr.nrows < (int64_t(1) << 31) &&
+        view_key_rows_smem(d) <= 48 * 1024) {
+      // the row of each key: the view is then computed key by key (coalesced, no memset)
+      std::vector<DCol> kcols;
+      for (int c : v.keycols) kcols.push_back(dcol(Rr.cols[c]));
+      std::vector<int64_t> kst(d.kstride, d.kstride + d.nk);
+      v.keyrow = (int *)P.arena.alloc(v.nkeys * 4 + 16);
+      LMFAO_CUDA(cudaMemsetAsync(v.keyrow, 0xff, v.nkeys * 4 + 16, s));
+      launch_key_rows(kcols.data(), (int)kcols.size(), P.arena.upload(kst, s), Rr.nrows, v.keyrow, s);
+    }
+    d.keyrow = v.keyrow;
+    d.nkeys = v.nkeys;
     d.col_fac_off = P.arena.upload(cfo, s);
     d.facs = P.arena.upload(facs, s);
     d.col_part_off = P.arena.upload(cpo, s);
@@ -1321,6 +1336,17 @@ void build_work(lmfao_ctx *ctx, PhysPlan &P) {
   P.nwork = (int64_t)work.size();
   P.work = P.arena.upload(work.empty() ? std::vector<DWork>{DWork{0, 0, 0}} : work, ctx->stream);
   if (work.empty()) P.nwork = 0;
+  // tuple quantiles: q[j] = first item whose r0 >= ceil(j * total / kWorkQ)
+  std::vector<int> q(kWorkQ + 1);
+  const long long total = r0;
+  size_t i = 0;
+  for (int j = 0; j <= kWorkQ; ++j) {
+    const long long at = (long long)(((__int128)total * j + kWorkQ - 1) / kWorkQ);
+    while (i < work.size() && work[i].r0 < at) ++i;
+    q[j] = (int)i;
+  }
+  q[kWorkQ] = (int)work.size();
+  P.work_q = P.arena.upload(q, ctx->stream);
 }
 
 void setup_root(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t) {
@@ -1415,6 +1441,7 @@ void setup_fast(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, DCombine &cb) {
   const size_t ts = P.fp64 ? 8 : 4;
   d.nwork = P.nwork;
   d.work = P.work;
+  d.work_q = P.work_q;
   d.wseg = P.wseg;
   d.ncols = (int)P.rowdev.size();
   for (size_t i = 0; i < P.rowdev.size(); ++i) d.col[i] = P.rowdev[i];
@@ -1971,6 +1998,12 @@ bool setup_combine4(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
     max_slots3 = std::max(max_slots3, (int)used);
   }
   if (max_slots3 > 12 * 1024) return false;
+  // streaming form: every class 3 entry's cells after those of the entries before it
+  long long nslots3 = 0;
+  for (DEntry4 &x : e3) {
+    x.pad = (int)nslots3;
+    nslots3 += ncells[x.og];
+  }
   std::vector<int> e3_off(nj + 1, 0);
   for (const DEntry4 &x : e3) e3_off[x.job + 1]++;
   for (int j = 0; j < nj; ++j) e3_off[j + 1] += e3_off[j];
@@ -2013,6 +2046,27 @@ bool setup_combine4(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   d.og_cstride = P.arena.upload(cstride, s);
   d.og_dom = P.arena.upload(cdom, s);
   d.max_cells = (int)max_cells;
+  // streaming form for batches with few Y columns (a decision-tree level: 24), the separate
+  // projection kernels for many (Favorita's 379, where the streaming form measured slower);
+  // LMFAO_PROJECTION=stream|kernels overrides. Tiles of about 6,144 staged sums, about two CTAs
+  // per SM, class 3 fused when its cells fit.
+  const char *pk = std::getenv("LMFAO_PROJECTION");
+  d.stream = pk ? (std::string(pk) == "stream" ? 1 : 0) : (nj <= 64 ? 1 : 0);
+  if (d.stream) {
+    d.c1 = (int)std::max<int64_t>(1, std::min<int64_t>(d.dom1, (6144 + nj - 1) / std::max(1, nj)));
+    while (d.c1 > 1 && 16 * (size_t)d.c1 * nj > 160 * 1024) d.c1 /= 2;
+    d.nx = (d.dom1 + d.c1 - 1) / d.c1;
+    int ny = (int)std::max<int64_t>(1, std::min<int64_t>(d.dom0, 296 / std::max(1, d.nx)));
+    d.c0 = (d.dom0 + ny - 1) / ny;
+    d.ny = (d.dom0 + d.c0 - 1) / d.c0;
+    d.nslots3 = (int)std::min<long long>(nslots3, 1 << 30);
+    const size_t tab3 = (size_t)d.c1 * (2 * d.tab[3].nt + d.tab[3].ng);  // staged terms and cells of a row
+    d.fused3 = d.nent3 > 0 && d.nent3 <= 512 && 8 * (2 * (size_t)d.c1 * nj + (size_t)nslots3 + tab3 + nj) <= 200 * 1024
+                   ? 1 : 0;
+    d.sblock = d.fused3 && d.nent3 > 256 ? 512 : 256;
+    d.yd0p = (unsigned long long *)P.arena.alloc((size_t)d.nx * d.dom0 * nj * 8);
+    d.yd1p = (unsigned long long *)P.arena.alloc((size_t)d.ny * d.dom1 * nj * 8);
+  }
   P.use_c4 = true;
   return true;
 }
@@ -2042,6 +2096,11 @@ bool setup_combine5(lmfao_ctx *ctx, PhysPlan &P) {
   D.tmem_cols = 32;
   while (D.tmem_cols < D.npad) D.tmem_cols *= 2;
   const int ts = P.fp64 ? 8 : 4;
+  // CUDA cores with single-column B terms: the dense kernel (LMFAO_COMBINE=general keeps the
+  // general one)
+  D.dense = !D.tc && (int)P.c3_bsrc.size() == d.nb && d.nb > 0 && combine5_dense_fits(d) &&
+            !(env && std::string(env) == "general");
+  if (D.dense) D.bsrc = P.arena.upload(P.c3_bsrc, ctx->stream);
   int kc0 = 64;
   if (const char *k = getenv("LMFAO_COMBINE_CHUNK")) kc0 = std::max(16, atoi(k) / 16 * 16);
   int kc = D.tc ? (int)std::min<int64_t>(kc0, (m + 15) / 16 * 16) : (int)std::min<int64_t>(kc0, m);
@@ -2056,8 +2115,8 @@ bool setup_combine5(lmfao_ctx *ctx, PhysPlan &P) {
   // TMA bulk staging: every chunk's rows start on a 16-byte boundary and span a multiple of 16 bytes
   const int64_t rb[5] = {(int64_t)d.n0f * ts, d.phi1f_seg * 4, (int64_t)d.n0i * 8, d.phi1i_seg * 4, 8};
   const void *base[5] = {d.phi0f, d.phi1f, d.phi0i, d.phi1i, d.wseg};
-  D.bulk = 1;
-  for (int i = 0; i < 5; ++i) {
+  D.bulk = D.dense ? 0 : 1;  // the dense kernel reads its operands with coalesced loads
+  for (int i = 0; i < 5 && D.bulk; ++i) {
     if (!rb[i]) continue;
     if ((m * rb[i]) % 16 || ((int64_t)D.kc * rb[i]) % 16 || ((uintptr_t)base[i] % 16)) D.bulk = 0;
   }
@@ -2192,6 +2251,15 @@ bool setup_combine3(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   stage_terms(bterms, border, bstage, bdesc, bpart, bint);
   with_segf(adesc, aterms, aorder);
   with_segf(bdesc, bterms, border);
+  // B terms that are single view columns (or 1): the dense two-kernel contraction reads them
+  P.c3_bsrc.clear();
+  for (const DPsi &b : bdesc) {
+    if (b.nf || b.np > 1) {
+      P.c3_bsrc.clear();
+      break;
+    }
+    P.c3_bsrc.push_back(b.np ? bstage[bpart[b.p0]] : make_int2(-1, -1));
+  }
   // Y columns
   d.n0f = cb.n0f;
   d.n0i = cb.n0i;
@@ -2514,10 +2582,14 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   for (size_t i = 0; i < P.vk.size(); ++i) {
     int r = P.vk_rel[i];
     View &v = P.views[r];
-    LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
-    if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+    if (!v.keyrow) {  // the key-major kernel writes every cell
+      LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
+      if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+    }
     launch_view_kernel(P.vk[i], s);
-    launch_view_finish(v.v64, v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint, v.nkeys, P.err, s);
+    // the FP32 copy is read by the general fact pass only
+    launch_view_finish(v.v64, P.fast.on ? nullptr : v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint,
+                       v.nkeys, P.err, s);
     mark("view:" + ctx->rels[r].name);
   }
   launch_segment_weights(P.sw, s);
@@ -2887,6 +2959,7 @@ void set_work_chunk(lmfao_ctx *ctx, PhysPlan &P, int chunk) {
   build_work(ctx, P);
   P.fd.nwork = P.nwork;
   P.fd.work = P.work;
+  P.fd.work_q = P.work_q;
   P.fp.nwork = P.nwork;
   P.fp.work = P.work;
   if (P.gen.fn) {
@@ -3030,8 +3103,10 @@ int view_flags(lmfao_ctx *ctx) {
   LMFAO_CUDA(cudaMemsetAsync(P.err, 0, 4, s));
   for (size_t i = 0; i < P.vk.size(); ++i) {
     View &v = P.views[P.vk_rel[i]];
-    LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
-    if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+    if (!v.keyrow) {
+      LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
+      if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+    }
     launch_view_kernel(P.vk[i], s);
     launch_view_finish(v.v64, v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint, v.nkeys, P.err, s);
   }
@@ -3786,7 +3861,9 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << ",\"block_combine\":" << (P.use_c3 ? "true" : "false") << ",\"prefix_digits\":" << P.prefix_len
       << ",\"block_combine_two_kernels\":" << (P.use_c5 ? "true" : "false") << ",\"contraction\":\""
       << (!P.use_c5 ? (P.use_c3 ? "cuda cores, single kernel" : "none")
-                    : P.c5.tc ? "tensor cores (tcgen05, split BF16)" : (P.fp64 ? "cuda cores FP64" : "cuda cores FP32"))
+                    : P.c5.tc ? "tensor cores (tcgen05, split BF16)"
+                              : std::string(P.fp64 ? "cuda cores FP64" : "cuda cores FP32") +
+                                    (P.c5.dense ? ", dense B operand" : ""))
       << "\",\"combine_chunk\":" << P.c5.kc << ",\"combine_bulk_copies\":" << (P.c5.bulk ? "true" : "false")
       << ",\"combine_blocks\":" << P.c3.nblocks << ",\"combine_entries\":" << P.c3.nent
       << ",\"block_terms\":[" << P.c3.na << "," << P.c3.nb << "," << P.c3.nbi << "]"
@@ -3795,6 +3872,9 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << ",\"combine_z_bytes\":" << combine_z_bytes(P) << ",\"combine_z_flops\":" << combine_z_flops(P)
       << ",\"projection_combine\":" << (!P.use_c3 && P.use_c4 ? "true" : "false")
       << ",\"projection_entries\":[" << P.c4.nent012 << "," << P.c4.nent3 << "," << P.c4.njobs << "]"
+      << ",\"projection_stream\":" << (P.use_c4 && P.c4.stream ? "true" : "false")
+      << ",\"projection_stream_tile\":[" << P.c4.c1 << "," << P.c4.c0 << "," << P.c4.nx << "," << P.c4.ny << "]"
+      << ",\"projection_fused_class3\":" << (P.use_c4 && P.c4.stream && P.c4.fused3 ? "true" : "false")
       << ",\"filter_family\":" << P.fast.fam_k << ",\"cta_items\":" << P.fast.b4.size()
       << ",\"segment_sums\":" << P.b0f.size() + P.b0i.size()
       << ",\"combine_items\":" << P.comb.size() << ",\"per_tuple_items\":" << P.b2.size()

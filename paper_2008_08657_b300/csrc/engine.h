@@ -135,6 +135,7 @@ struct View {
   float *v32 = nullptr;       // nkeys x ncols (FP32 copy for FP32 passes)
   uint32_t *vint = nullptr;   // nkeys x nint (exact integral columns)
   int32_t *vcodes = nullptr;  // nkeys x ncodes (-1: no tuple)
+  int *keyrow = nullptr;      // unique keys: row of each key (-1: none), built at plan time
   int *intcols_dev = nullptr; // view columns copied into vint
 };
 
@@ -188,6 +189,9 @@ struct DViewKernel {
   int32_t *codes;
   int ncols, ncodes;
   int unique;        // plain stores instead of atomics
+  const int *keyrow; // unique keys: row of each key (-1: none); the key-major kernel runs
+  int64_t nkeys;
+  int nfac;          // factors of all columns (col_fac_off[ncols])
   // columns: [col] -> factor list (offsets into facs) and child column list
   const int *col_fac_off;   // ncols+1
   const DFac *facs;

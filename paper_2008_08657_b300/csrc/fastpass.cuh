@@ -40,6 +40,7 @@ struct DFastB1 {
 struct DFast {
   int64_t nwork;
   const DWork *work;
+  const int *work_q;      // tuple quantiles of the work list (kWorkQ + 1 entries)
   const unsigned long long *wseg;
   int ncols;
   DCol col[MAXRC];

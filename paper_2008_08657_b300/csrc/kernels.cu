@@ -92,9 +92,11 @@ __device__ __forceinline__ int64_t outer_key(const DOuter &o, const DSegment &s,
 }
 
 // ------------------------------------------------------------------ view kernel
-// grid (tiles of rows, column groups): CTA (x, y) computes view columns y, y + gridDim.y, ...
-// for a tile of rows of r (one thread per row: coalesced reads of r's columns, uniform column
-// descriptors); the last column group also writes the group codes
+// grid (tiles of rows, column groups): CTA (x, y) computes the y-th run of consecutive view
+// columns for a tile of rows of r (one thread per row: coalesced reads of r's columns, uniform
+// column descriptors, and a row's columns of a run written by one thread); the number of runs
+// gives large relations one run (each row's key and child lookups done once) and small ones a
+// run per column (enough threads); the last run also writes the group codes
 __global__ void __launch_bounds__(256) view_kernel(DViewKernel d) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.nrows) return;
@@ -110,7 +112,9 @@ __global__ void __launch_bounds__(256) view_kernel(DViewKernel d) {
     w *= __ldg(v.v64 + kk * v.ncols);
   }
   if (w == 0.0) return;  // the tuple has no partner in some child: it does not join
-  for (int j = blockIdx.y; j < d.ncols; j += gridDim.y) {
+  const int run = (d.ncols + gridDim.y - 1) / gridDim.y;
+  const int j1 = min(d.ncols, (int)(blockIdx.y + 1) * run);
+  for (int j = blockIdx.y * run; j < j1; ++j) {
     double val = 1.0;
     for (int f = d.col_fac_off[j]; f < d.col_fac_off[j + 1]; ++f) val *= fac_at<double>(d.in, d.facs[f], r);
     for (int p = d.col_part_off[j]; p < d.col_part_off[j + 1]; ++p) {
@@ -136,13 +140,91 @@ __global__ void __launch_bounds__(256) view_kernel(DViewKernel d) {
   }
 }
 
+// Key-major form with one thread per key (kb consecutive keys per CTA): the column
+// descriptors are staged in shared memory, the thread reads its row's input columns once and
+// forms every view column of the key in a shared tile; the CTA then writes its keys' rows,
+// which are one contiguous span of the view, with coalesced stores.
+__global__ void __launch_bounds__(128) view_key_rows_kernel(DViewKernel d, int kb) {
+  extern __shared__ __align__(16) unsigned char vsm[];
+  const int tid = threadIdx.x;
+  const int w = d.ncols + 1;
+  double *vtile = reinterpret_cast<double *>(vsm);  // [kb][ncols + 1]
+  int *scfo = reinterpret_cast<int *>(vtile + (size_t)kb * w);
+  const int nfac = d.col_fac_off[d.ncols];
+  DFac *sfac = reinterpret_cast<DFac *>(scfo + ((d.ncols + 1 + 3) & ~3));
+  for (int i = tid; i <= d.ncols; i += blockDim.x) scfo[i] = d.col_fac_off[i];
+  for (int i = tid; i < nfac; i += blockDim.x) sfac[i] = d.facs[i];
+  __syncthreads();
+  const int64_t k0 = (int64_t)blockIdx.x * kb;
+  const int nk = (int)(d.nkeys - k0 < kb ? d.nkeys - k0 : kb);
+  for (int t = tid; t < nk; t += blockDim.x) {
+    const int64_t k = k0 + t;
+    const int r = __ldg(d.keyrow + k);
+    bool live = r >= 0;
+    int64_t ck[MAXCH];
+    double xin[MAXRC];
+    if (live) {
+      for (int c = 0; c < d.ncolsin; ++c) xin[c] = ld_num<double>(d.in[c], r);
+      for (int c = 0; c < d.nchild; ++c) {
+        const DViewRef &v = d.child[c];
+        int64_t kk = 0;
+        for (int i = 0; i < v.nk; ++i) kk += (int64_t)ld_i32(d.in[v.kcol[i]], r) * v.kstride[i];
+        ck[c] = kk;
+        if (__ldg(v.v64 + kk * v.ncols) == 0.0) live = false;  // no partner in this child
+      }
+    }
+    for (int j = 0; j < d.ncols; ++j) {
+      double val = 0.0;
+      if (live) {
+        val = 1.0;
+        for (int f = scfo[j]; f < scfo[j + 1]; ++f) {
+          const DFac fc = sfac[f];
+          const double x = xin[fc.col];
+          if (fc.ind) {
+            // predicates compare the stored value: FP32 columns in FP32, integer columns exactly
+            const bool ok = d.in[fc.col].dtype == LMFAO_F32 ? cmp_op<float>((float)x, fc.t, fc.op)
+                                                            : cmp_op<double>(x, (double)fc.t, fc.op);
+            val *= ok ? 1.0 : 0.0;
+          } else {
+            double v = x;
+            for (int p = 1; p < fc.pow; ++p) v *= x;
+            val *= v;
+          }
+        }
+        for (int p = d.col_part_off[j]; p < d.col_part_off[j + 1]; ++p) {
+          const int2 pp = d.parts[p];
+          val *= __ldg(d.child[pp.x].v64 + ck[pp.x] * d.child[pp.x].ncols + pp.y);
+        }
+      }
+      vtile[t * w + j] = val;
+    }
+    for (int c = 0; c < d.ncodes; ++c) {
+      int code = -1;
+      if (live) {
+        const int4 cd = d.code_desc[c];
+        if (cd.x >= 0) {
+          code = code_at(d.in[cd.x], r, cd.y, d.thr + cd.z, cd.w);
+        } else {
+          const int2 ch = d.code_child[c];
+          code = __ldg(d.child[ch.x].codes + ck[ch.x] * d.child[ch.x].ncodes + ch.y);
+        }
+      }
+      d.codes[k * d.ncodes + c] = code;
+    }
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  double *out = d.v64 + k0 * d.ncols;
+  for (int t = warp; t < nk; t += nwarp)
+    for (int j = lane; j < d.ncols; j += 32) out[(int64_t)t * d.ncols + j] = vtile[t * w + j];
+}
+
 __global__ void view_finish_kernel(const double *v64, float *v32, uint32_t *vint, const int *intcols,
                                    int ncols, int nint, int64_t nkeys, int *err) {
   const int64_t n = nkeys * ncols;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    if (v32) v32[i] = (float)v64[i];
-  }
+  if (v32)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v32[i] = (float)v64[i];
   const int64_t ni = nkeys * nint;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += stride) {
     int64_t k = i / nint;
@@ -423,6 +505,16 @@ __global__ void range_check_kernel(const int *p, int64_t n, int64_t domain, int 
   }
 }
 
+// row of each key of a relation whose keys are unique (keyrow is -1 beforehand)
+__global__ void key_row_kernel(DScatterCols cols, const int64_t *stride_k, int64_t n, int *keyrow) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    int64_t k = 0;
+    for (int j = 0; j < cols.ncols; ++j) k += (int64_t)reinterpret_cast<const int *>(cols.in[j])[r] * stride_k[j];
+    keyrow[k] = (int)r;
+  }
+}
+
 __global__ void key_mult_kernel(DScatterCols cols, const int64_t *stride_k, int64_t n, unsigned int *hist) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -642,15 +734,26 @@ static int grid_for(int64_t n, int block) {
   return (int)g;
 }
 
+size_t view_key_rows_smem(const DViewKernel &d) {
+  return (size_t)kVkb * (d.ncols + 1) * 8 + 4 * (size_t)((d.ncols + 1 + 3) & ~3) + sizeof(DFac) * (size_t)d.nfac;
+}
+
 void launch_view_kernel(const DViewKernel &d, cudaStream_t s) {
+  if (d.keyrow) {  // the plan gives a key-row map only to views whose key tile fits (view_key_rows_smem)
+    const size_t sm = view_key_rows_smem(d);
+    if (d.nkeys) view_key_rows_kernel<<<(unsigned)((d.nkeys + kVkb - 1) / kVkb), kVkb, sm, s>>>(d, kVkb);
+    return;
+  }
   if (d.nrows == 0) return;
-  const int groups = std::max(1, std::min(d.ncols, 65535));
+  // enough rows x runs to fill 148 SMs x 2048 threads, and no more runs than that
+  const int64_t want = (148LL * 2048 + d.nrows - 1) / d.nrows;
+  const int groups = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(d.ncols, 65535), want));
   view_kernel<<<dim3((unsigned)((d.nrows + 255) / 256), groups), 256, 0, s>>>(d);
 }
 
 void launch_view_finish(const double *v64, float *v32, uint32_t *vint, const int *intcols, int ncols, int nint,
                         int64_t nkeys, int *err, cudaStream_t s) {
-  int64_t n = nkeys * (int64_t)ncols;
+  const int64_t n = std::max<int64_t>(v32 ? nkeys * (int64_t)ncols : 0, nkeys * (int64_t)nint);
   if (n == 0) return;
   view_finish_kernel<<<grid_for(n, 256), 256, 0, s>>>(v64, v32, vint, intcols, ncols, nint, nkeys, err);
 }
@@ -736,6 +839,14 @@ void launch_key_multiplicity(const DCol *cols, int ncols, const int64_t *stride,
   c.ncols = ncols;
   for (int j = 0; j < ncols; ++j) c.in[j] = cols[j].p;
   key_mult_kernel<<<grid_for(n, 256), 256, 0, s>>>(c, stride, n, hist);
+}
+
+void launch_key_rows(const DCol *cols, int ncols, const int64_t *stride, int64_t n, int *keyrow, cudaStream_t s) {
+  if (n == 0) return;
+  DScatterCols c{};
+  c.ncols = ncols;
+  for (int j = 0; j < ncols; ++j) c.in[j] = cols[j].p;
+  key_row_kernel<<<grid_for(n, 256), 256, 0, s>>>(c, stride, n, keyrow);
 }
 
 void launch_max_u32(const unsigned int *h, int64_t n, unsigned int *out, cudaStream_t s) {

@@ -24,6 +24,10 @@ struct DWork {  // one work item: tuples [r0, r0 + len) of segment seg
   int seg;
   int len;
 };
+// Tuple quantiles of the work list: entry j (0 <= j <= kWorkQ) is the first item whose first
+// tuple is at or past j / kWorkQ of all tuples, so CTA b of G takes the items
+// [q[kWorkQ b / G], q[kWorkQ (b + 1) / G]): contiguous ranges of about equal tuple counts.
+constexpr int kWorkQ = 4096;
 
 struct DOuter {  // an outer child: key index from the segment id
   DViewRef v;
@@ -174,9 +178,9 @@ struct DEntry4 {
 struct DTab4 {
   int nt, ng;               // tabulated terms and cell sets
   const int *t, *g;         // their ids
-  double *pf;               // [nvalues][nt]
-  unsigned long long *pi;
-  long long *cell;          // [nvalues][ng] (-1: a code is missing, or class 3 and w_s = 0)
+  double *pf;               // classes 1, 2: [nt][nvalues] (lanes over the digit read consecutive
+  unsigned long long *pi;   // words); class 3: [nvalues][nt] (a segment's terms together)
+  long long *cell;          // the same with ng (-1: a code is missing, or class 3 and w_s = 0)
 };
 struct DComb4 {
   DComb2 c;                 // segments, outer views, psi terms, outer-cell sets, Y columns
@@ -190,7 +194,7 @@ struct DComb4 {
   const int *e3_off;
   DTab4 tab[4];             // classes 1 (per d0), 2 (per d1), 3 (per segment); [0] unused
   int max_slots3;           // shared slots of one tile of 256 class 3 entries
-  double *yd0_f, *yd1_f, *yall_f;             // [dom0][njobs], [dom1][njobs], [njobs]
+  double *yd0_f, *yd1_f, *yall_f;             // [njobs][dom0], [njobs][dom1], [njobs]
   unsigned long long *yd0_i, *yd1_i, *yall_i;
   int need_d0, need_d1;
   int skip_counts;          // every outer COUNT is 0 or 1: on live segments the COUNT parts of
@@ -198,6 +202,12 @@ struct DComb4 {
   const long long *og_ncells;                 // per outer-cell set: compact cells
   const long long *og_cstride, *og_dom;       // per outer group ref: compact stride and domain
   int max_cells;
+  // streaming form (stream != 0): one pass over the per-segment sums in tiles of c1 minor x
+  // c0 major digit values (grid nx x ny) forms partial projections (Yd0p: nx x dom0 x njobs,
+  // Yd1p: ny x dom1 x njobs, 8-byte words typed by the job) and, when fused3, the class 3
+  // entries from the staged rows (slots: the cumulative cell base of each entry in pad)
+  int stream, c1, c0, nx, ny, sblock, fused3, nslots3;
+  unsigned long long *yd0p, *yd1p;
 };
 void launch_combine4(const DComb4 &d, bool fp64, cudaStream_t s);
 
@@ -223,6 +233,11 @@ void launch_scatter_rows(const int *segid, int64_t n, unsigned long long *cursor
 void launch_permute_rows(const unsigned int *dest, int64_t n, const DCol *in, DCol *out, const int *elem_size,
                          int ncols, cudaStream_t s);
 void launch_range_check(const void *p, int dtype, int64_t n, int64_t domain, int *bad, cudaStream_t s);
+// Views of unique-key relations computed key by key (kVkb keys per CTA, a shared tile of their
+// rows): used when the tile fits 48 KB of shared memory.
+constexpr int kVkb = 128;
+size_t view_key_rows_smem(const DViewKernel &d);
+void launch_key_rows(const DCol *cols, int ncols, const int64_t *stride, int64_t n, int *keyrow, cudaStream_t s);
 void launch_key_multiplicity(const DCol *cols, int ncols, const int64_t *stride, int64_t n,
                              unsigned int *hist, cudaStream_t s);
 void launch_max_u32(const unsigned int *h, int64_t n, unsigned int *out, cudaStream_t s);
@@ -297,6 +312,8 @@ struct DComb5 {
   int npad;                  // tensor-core path: N of the MMA (B terms rounded up to 16)
   int tmem_cols;             // tensor-core path: tensor-memory columns allocated per CTA
   int tc;                    // 1: contraction on the tensor cores (split BF16)
+  int dense;                 // 1: every B term is one outer-view column or 1 (block_zd_kernel)
+  const int2 *bsrc;          // dense: per B term (outer view, column); (-1, -1) for the constant 1
   int bulk;                  // 1: per-segment sums staged with TMA bulk copies (16-byte aligned)
   int grid;                  // CTAs of block_z_kernel
   int eranges;               // block ranges of block_entries_kernel (grid.y)
@@ -309,6 +326,7 @@ struct DComb5 {
   int *err;                  // error flags (8: a bounded wait of block_z_kernel ran out)
 };
 size_t combine5_smem(const DComb5 &d, bool fp64);
+bool combine5_dense_fits(const DComb3 &d);  // the dense kernel's register tiles cover Z_p
 void launch_combine5_z(const DComb5 &d, bool fp64, cudaStream_t s);
 void launch_combine5_entries(const DComb5 &d, bool fp64, cudaStream_t s);
 

@@ -135,6 +135,7 @@ struct PhysPlan {
   DeviceArena arena;
   std::vector<DCol> rowdev;        // reorganised root columns (per row slot)
   DWork *work = nullptr;
+  int *work_q = nullptr;           // tuple quantiles of the work list (CTA ranges)
   int64_t nwork = 0;
   unsigned long long *wseg = nullptr;
   void *phi0f = nullptr;
@@ -157,6 +158,8 @@ struct PhysPlan {
   bool use_c3 = false, no_c3 = false;
   DComb5 c5{};                     // two-kernel block combine (combine5.cu)
   bool use_c5 = false;
+  std::vector<int2> c3_bsrc;       // per B term (outer view, column), (-1, -1) for 1; empty when
+                                   // some B term is a product or has a segment-digit factor
   std::string c5_why;              // why the two-kernel block combine does not run (if not)
   std::string fast_why;            // why the specialised root pass declined the batch (if it did)
   std::map<int, int *> result_flags;  // per query: integral flags on the device (lmfao_result_device)

@@ -109,6 +109,14 @@ int main() {
       std::string why;
       if (!family_eligible(d, why, g4)) printf("dt_level%s FAIL not eligible: %s\n", sfx.c_str(), why.c_str());
       else check(("dt_level" + sfx).c_str(), gen_family_source(d, fp64, block, thr, g4, mir));
+      // the per-segment sums by leaf alone (8 cells of 2 float and 1 integral column): kept in
+      // registers and reduced over the warp with the segment sums
+      d.b1[0].nref = 1;
+      d.b1[0].ref[0] = DGroupRef{4, 0, 0, 0, 0, 0, 1};
+      d.b1[0].G = 8;
+      d.hist_f = 16; d.hist_i = 8; d.phi1f_seg = 16; d.phi1i_seg = 8;
+      if (!family_eligible(d, why, g4)) printf("dt_leaf_sums%s FAIL not eligible: %s\n", sfx.c_str(), why.c_str());
+      else check(("dt_leaf_sums" + sfx).c_str(), gen_family_source(d, fp64, block, thr, g4, mir));
     }
     {  // general pass without an inner relation: two value columns (float and uint8), an
        // indicator factor and CTA-private items grouped by buckets of both columns

@@ -34,7 +34,8 @@ def results():
     return {line.split()[0]: line.split()[1:] for line in out.splitlines() if line.strip()}
 
 
-SHAPES = [f"{s}_{p}" for s in ("lean_retailer", "lean_retailer_lanes", "lean_favorita", "lean_no_inner", "dt_level", "general_no_inner")
+SHAPES = [f"{s}_{p}" for s in ("lean_retailer", "lean_retailer_lanes", "lean_favorita", "lean_no_inner", "dt_level", "dt_leaf_sums",
+                                    "general_no_inner")
           for p in ("fp32", "fp64")]
 
 

@@ -376,16 +376,19 @@ def test_generated_and_template_root_pass_match_the_oracle(which, precision, cod
 _FAV = {}
 
 
-@pytest.mark.parametrize("projection", [True, False])
+@pytest.mark.parametrize("projection", ["stream", "kernels", False])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_favorita_projection_and_entry_combine(precision, projection, monkeypatch):
     """Favorita with the (date, store) segment key: outer store groups change inside every
     date block, so the combine is the projection combine (per-date and per-store projections
-    of the per-segment sums, per-segment store x holiday cells) or, with it switched off, the
-    entry combine. The batch adds the Section 2 queries Q1-Q3 (Q2 has a factor on the date
-    key digit)."""
+    of the per-segment sums, per-segment store x holiday cells; "stream": one pass over the
+    sums in tiles with the per-segment entries fused, "kernels": one kernel per projection)
+    or, with it switched off, the entry combine. The batch adds the Section 2 queries Q1-Q3
+    (Q2 has a factor on the date key digit)."""
     if projection is False:
         monkeypatch.setenv("LMFAO_NO_PROJECTION_COMBINE", "1")
+    else:
+        monkeypatch.setenv("LMFAO_PROJECTION", projection)
     if not _FAV:
         rels = W.favorita_schema(n_fact=700_001, seed=3)
         qs = W.favorita_batch() + W.favorita_example_queries()
@@ -403,19 +406,25 @@ def test_favorita_projection_and_entry_combine(precision, projection, monkeypatc
     finally:
         e.close()
     assert phys["segment_relation"] == "Transactions" and not phys["block_combine"], phys
-    assert phys["projection_combine"] == projection
+    assert phys["projection_combine"] == (projection is not False)
+    assert phys["projection_stream"] == (projection == "stream"), phys
     for i, (q, g, r) in enumerate(zip(qs, got, ref)):
         compare(q, g, r, where=f"{precision} projection={projection} query {i}")
 
 
-@pytest.mark.parametrize("precision,impl", [("fp32", "two"), ("fp64", "two"), ("split_bf16", "two"),
-                                            ("fp32", "single"), ("fp64", "single")])
-def test_block_combine_kernels_match_the_oracle(precision, impl, monkeypatch):
+@pytest.mark.parametrize("precision,impl,chunk", [("fp32", "two", None), ("fp64", "two", None), ("fp32", "two", 16),
+                                                  ("split_bf16", "two", None), ("fp32", "general", None),
+                                                  ("fp64", "general", None), ("fp32", "single", None),
+                                                  ("fp64", "single", None)])
+def test_block_combine_kernels_match_the_oracle(precision, impl, chunk, monkeypatch):
     """The block combine as two kernels (per-block contraction into scratch, then the entries;
-    FP32 and FP64 on the CUDA cores, split BF16 on the tensor cores with TMA-staged sums) and
-    as the single-kernel form, on the Retailer shape with ragged segments: blocks of 124
-    segments run as chunks of 64 and 60 (the last padded to the MMA's K)."""
+    FP32 and FP64 on the CUDA cores with the B operand read from the view rows (dense) or
+    built term by term (general, TMA-staged sums), split BF16 on the tensor cores) and as the
+    single-kernel form, on the Retailer shape with ragged segments: blocks of 124 segments run
+    as chunks of 64 and 60 (the last padded to the MMA's K), or of 16 (7 full, 12 left)."""
     monkeypatch.setenv("LMFAO_COMBINE", impl)
+    if chunk:
+        monkeypatch.setenv("LMFAO_COMBINE_CHUNK", str(chunk))
     rels, qs, ref = _shape_case("retailer")
     e = Engine(0)
     try:
@@ -425,13 +434,15 @@ def test_block_combine_kernels_match_the_oracle(precision, impl, monkeypatch):
         e.plan(precision=precision)
         phys = e.describe()["physical"]
         # in FP64 the single-kernel block tables exceed shared memory: the entry combine runs
-        assert phys["block_combine"] == (impl == "two" or precision != "fp64"), phys
-        assert phys["block_combine_two_kernels"] == (impl == "two"), phys["combine_note"]
-        if impl == "two":
-            assert phys["combine_bulk_copies"], phys
+        assert phys["block_combine"] == (impl != "single" or precision != "fp64"), phys
+        assert phys["block_combine_two_kernels"] == (impl != "single"), phys["combine_note"]
+        if impl != "single":
+            dense = impl == "two" and precision != "split_bf16"
+            assert phys["combine_bulk_copies"] == (not dense), phys
             want = {"fp32": "cuda cores FP32", "fp64": "cuda cores FP64",
                     "split_bf16": "tensor cores (tcgen05, split BF16)"}[precision]
-            assert phys["contraction"] == want, phys
+            assert phys["contraction"] == want + (", dense B operand" if dense else ""), phys
+            assert phys["combine_chunk"] == (chunk or 64), phys
         e.run()
         got = e.fetch_all()
     finally:
