@@ -784,6 +784,250 @@ __global__ void __launch_bounds__(256) block_zd_kernel(DComb5 D) {
   }
 }
 
+// ------------------------------------------------------------------ pipelined dense contraction
+// block_zp_kernel: block_zd_kernel with the operand reads made asynchronous. Every thread
+// issues cp.async copies (4 or 8 bytes each, so no alignment beyond the element's is needed)
+// of the next chunk's per-segment sums, segment weights and B-side view values into the other
+// of two raw stages while the current chunk is converted and contracted; a CTA's chunks run in
+// one sequence across its blocks, so the next block's first chunk is in flight during the last
+// chunk of the current one.
+struct ZpLayout {
+  size_t rf0, rf1, ri0, ri1, rws, rb, stage, ysf, bt, bti, lv, asv, zacc, bsrc, total;  // raw stage st at st * stage
+};
+__host__ __device__ inline ZpLayout zp_layout(const DComb3 &d, int kc, int ts) {
+  const int ny = d.nyf + d.nyi;
+  const size_t nyp = (size_t)(ny + kZq - 1) / kZq * kZq, nbp = (size_t)(d.nb + kZq - 1) / kZq * kZq;
+  ZpLayout L{};
+  size_t o = 0;  // offsets inside one raw stage
+  L.rf0 = o; o += up16((size_t)kc * d.n0f * ts);
+  L.rf1 = o; o += up16((size_t)kc * d.phi1f_seg * 4);
+  L.ri0 = o; o += up16((size_t)kc * d.n0i * 8);
+  L.ri1 = o; o += up16((size_t)kc * d.phi1i_seg * 4);
+  L.rws = o; o += up16((size_t)kc * 8);
+  L.rb = o; o += up16((size_t)kc * d.nb * 8);
+  L.stage = o;
+  o *= 2;
+  L.ysf = o; o += up16((size_t)kc * nyp * ts);
+  L.bt = o; o += up16((size_t)kc * nbp * ts);
+  L.bti = o; o += up16((size_t)kc * d.nbi * 8);
+  L.lv = o; o += up16((size_t)kc * 4);
+  L.asv = o; o += up16((size_t)d.nast * ts);
+  L.zacc = o; o += up16((size_t)d.nbi * d.nyi * 8);
+  L.bsrc = o; o += up16((size_t)d.nb * 8);
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <typename T, int KT>
+__global__ void __launch_bounds__(256, KT == 1 && sizeof(T) == 4 ? 4 : 2) block_zp_kernel(DComb5 D) {
+  const DComb3 &d = D.c;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long akey[MAXOUT];
+  __shared__ int block_live;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  const int kc = D.kc, m = (int)d.m, ny = d.nyf + d.nyi, nb = d.nb;
+  const int nyp = (ny + kZq - 1) / kZq * kZq, nbp = (nb + kZq - 1) / kZq * kZq;
+  const int nct = nyp / kZq, ntile = (nbp / kZq) * nct, nzi = d.nbi * d.nyi;
+  const int ts = (int)sizeof(T);
+  const ZpLayout L = zp_layout(d, kc, ts);
+  T *ysf = (T *)(smem + L.ysf);
+  T *bt = (T *)(smem + L.bt);
+  unsigned long long *bti = (unsigned long long *)(smem + L.bti);
+  int *lv = (int *)(smem + L.lv);
+  T *asv = (T *)(smem + L.asv);
+  unsigned long long *zacc = (unsigned long long *)(smem + L.zacc);
+  int2 *sbsrc = (int2 *)(smem + L.bsrc);
+  for (int b = tid; b < nb; b += bs) sbsrc[b] = D.bsrc[b];
+  const DOuter &ob = d.outer[D.bout];
+  const int nchunk = (m + kc - 1) / kc;
+  const int64_t nitems = ((d.nblocks - blockIdx.x + gridDim.x - 1) / gridDim.x) * nchunk;
+  __syncthreads();  // sbsrc
+  // row of outer view bout at the prefix digits of block p
+  auto brow0 = [&](int64_t p) {
+    int64_t k = 0;
+    const int64_t s0 = p * d.m;
+    for (int i = 0; i < d.seg.ndig; ++i)
+      if (ob.dstride[i] && d.seg.radix[i] >= d.m) k += digit5(d.seg, s0, i) * ob.dstride[i];
+    return k;
+  };
+  // copies of item it (block, chunk) into raw stage st
+  auto issue = [&](int64_t it, int st) {
+    const int64_t p = blockIdx.x + (it / nchunk) * gridDim.x;
+    const int k0 = (int)(it % nchunk) * kc, kn = min(kc, m - k0);
+    const int64_t sb = p * d.m + k0;
+    unsigned char *raw = smem + (st ? L.stage : 0);
+    for (int i = tid; i < kn * d.n0f; i += bs)
+      if (ts == 8) cp_async8(raw + L.rf0 + (size_t)i * 8, (const T *)d.phi0f + sb * d.n0f + i);
+      else cp_async4(raw + L.rf0 + (size_t)i * 4, (const T *)d.phi0f + sb * d.n0f + i);
+    for (int i = tid; i < kn * (int)d.phi1f_seg; i += bs) cp_async4(raw + L.rf1 + (size_t)i * 4, d.phi1f + sb * d.phi1f_seg + i);
+    for (int i = tid; i < kn * d.n0i; i += bs) cp_async8(raw + L.ri0 + (size_t)i * 8, d.phi0i + sb * d.n0i + i);
+    for (int i = tid; i < kn * (int)d.phi1i_seg; i += bs) cp_async4(raw + L.ri1 + (size_t)i * 4, d.phi1i + sb * d.phi1i_seg + i);
+    for (int i = tid; i < kn; i += bs) cp_async8(raw + L.rws + (size_t)i * 8, d.wseg + sb + i);
+    const double *vrow = ob.v.v64 + (brow0(p) + (int64_t)k0 * D.bstride) * ob.v.ncols;
+    const int64_t rstride = D.bstride * ob.v.ncols;
+    for (int i = tid; i < kn * nb; i += bs) {
+      const int s = i / nb, b = i - s * nb;
+      const int2 src = sbsrc[b];
+      if (src.x >= 0) cp_async8(raw + L.rb + (size_t)i * 8, vrow + (int64_t)s * rstride + src.y);
+    }
+  };
+  if (nitems > 0) issue(0, 0);
+  cp_async_commit();
+  T acc[KT][kZq * kZq];
+  for (int64_t it = 0; it < nitems; ++it) {
+    const int st = (int)(it & 1);
+    const int64_t p = blockIdx.x + (it / nchunk) * gridDim.x;
+    const int k0 = (int)(it % nchunk) * kc, kn = min(kc, m - k0);
+    const int64_t s0 = p * d.m;
+    if (k0 == 0) {
+      // ---- prefix side (as in block_z_kernel): view keys, A terms, outer cells
+      if (tid < d.nouter) {
+        const DOuter &o = d.outer[tid];
+        int64_t k = 0;
+        for (int i = 0; i < d.seg.ndig; ++i)
+          if (o.dstride[i] && d.seg.radix[i] >= d.m) k += digit5(d.seg, s0, i) * o.dstride[i];
+        akey[tid] = k;
+      }
+      if (tid == 0) block_live = 0;
+      for (int i = tid; i < nzi; i += bs) zacc[i] = 0ull;
+      __syncthreads();
+      for (int j = tid; j < d.nast; j += bs) {
+        const int2 sc = d.astage[j];
+        const DOuter &o = d.outer[sc.x];
+        asv[j] = (T)__ldg(o.v.v64 + akey[sc.x] * o.v.ncols + sc.y);
+      }
+      __syncthreads();
+      T *ag = (T *)D.a + p * d.na;
+      unsigned long long *aig = D.ai + p * d.na;
+      for (int a = tid; a < d.na; a += bs) {
+        T v;
+        unsigned long long iv;
+        term5<T>(d.aterm[a], d.segfacs, d.apart, asv, d.seg, s0, v, iv);
+        ag[a] = v;
+        aig[a] = iv;
+      }
+      for (int g = tid; g < d.nog; g += bs) {
+        long long cell = 0;
+        for (int r = d.og_off[g]; r < d.og_off[g + 1] && cell >= 0; ++r) {
+          const DGroupRef q = d.grefs[r];
+          const long long code = q.src == 0 ? digit5(d.seg, s0, q.a)
+                                            : __ldg(d.outer[q.a].v.codes + akey[q.a] * d.outer[q.a].v.ncodes + q.b);
+          if (code < 0) cell = -1;
+          else cell += code * q.stride;
+        }
+        D.cells[p * d.nog + g] = cell;
+      }
+#pragma unroll
+      for (int t = 0; t < KT; ++t)
+#pragma unroll
+        for (int i = 0; i < kZq * kZq; ++i) acc[t][i] = T(0);
+    }
+    // the next item's copies go to the other stage (free: its conversion ended before the
+    // barrier that closed the previous item)
+    if (it + 1 < nitems) issue(it + 1, st ^ 1);
+    cp_async_commit();
+    cp_async_wait1();  // this item's copies
+    __syncthreads();
+    // convert the raw stage: Y (FP32 / FP64, integral columns as numbers), B (zero without
+    // outer partners), integral B terms exactly
+    const unsigned char *raw = smem + (st ? L.stage : 0);
+    const T *rf0 = (const T *)(raw + L.rf0);
+    const float *rf1 = (const float *)(raw + L.rf1);
+    const unsigned long long *ri0 = (const unsigned long long *)(raw + L.ri0);
+    const unsigned int *ri1 = (const unsigned int *)(raw + L.ri1);
+    const unsigned long long *rws = (const unsigned long long *)(raw + L.rws);
+    const double *rb = (const double *)(raw + L.rb);
+    for (int i = tid; i < kn; i += bs) {
+      lv[i] = rws[i] != 0ull;
+      if (rws[i] != 0ull) block_live = 1;
+    }
+    for (int i = tid; i < kn * nyp; i += bs) {
+      const int s = i / nyp, c = i - s * nyp;
+      T v = T(0);
+      if (c < d.n0f) v = rf0[s * d.n0f + c];
+      else if (c < d.nyf) v = (T)rf1[s * (int)d.phi1f_seg + (c - d.n0f)];
+      else if (c < d.nyf + d.n0i) v = (T)ri0[s * d.n0i + (c - d.nyf)];
+      else if (c < ny) v = (T)ri1[s * (int)d.phi1i_seg + (c - d.nyf - d.n0i)];
+      ysf[i] = v;
+    }
+    for (int i = tid; i < kn * nbp; i += bs) {
+      const int s = i / nbp, b = i - s * nbp;
+      T v = T(0);
+      unsigned long long iv = 0ull;
+      if (b < nb && rws[s] != 0ull) {
+        if (sbsrc[b].x < 0) {
+          v = T(1);
+          iv = 1ull;
+        } else {
+          const double x = rb[s * nb + b];
+          v = (T)x;
+          iv = (unsigned long long)x;
+        }
+      }
+      bt[i] = v;
+      if (b < d.nbi) bti[s * d.nbi + b] = iv;
+    }
+    __syncthreads();
+    // contraction into the register tiles
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int tile = tid + t * bs;
+      if (tile < ntile) {
+        const int b0 = (tile / nct) * kZq, c0 = (tile - (tile / nct) * nct) * kZq;
+        const T *br = bt + b0, *yr = ysf + c0;
+        for (int s = 0; s < kn; ++s, br += nbp, yr += nyp) {
+          T bv[4], yv[4];
+          Vec4<T>::load(br, bv);
+          Vec4<T>::load(yr, yv);
+#pragma unroll
+          for (int i = 0; i < kZq; ++i)
+#pragma unroll
+            for (int j = 0; j < kZq; ++j) acc[t][i * kZq + j] += bv[i] * yv[j];
+        }
+      }
+    }
+    // integral B terms x integral Y columns, exactly: (output, 8-segment run) per thread
+    for (int w = tid; w < nzi * ((kn + 7) >> 3); w += bs) {
+      const int o = w % nzi, s1 = (w / nzi) * 8, s2 = min(kn, s1 + 8);
+      const int b = o / d.nyi, c = o - b * d.nyi;
+      unsigned long long z = 0;
+      for (int s = s1; s < s2; ++s)
+        z += bti[s * d.nbi + b] * (c < d.n0i ? ri0[s * d.n0i + c] : (unsigned long long)ri1[s * (int)d.phi1i_seg + (c - d.n0i)]);
+      if (z) atomicAdd(zacc + o, z);
+    }
+    if (k0 + kn >= m) {  // the block's last chunk
+      __syncthreads();
+      T *zg = (T *)D.z + p * (int64_t)nb * ny;
+#pragma unroll
+      for (int t = 0; t < KT; ++t) {
+        const int tile = tid + t * bs;
+        if (tile < ntile) {
+          const int b0 = (tile / nct) * kZq, c0 = (tile - (tile / nct) * nct) * kZq;
+#pragma unroll
+          for (int i = 0; i < kZq; ++i)
+#pragma unroll
+            for (int j = 0; j < kZq; ++j)
+              if (b0 + i < nb && c0 + j < ny) zg[(size_t)(b0 + i) * ny + c0 + j] = acc[t][i * kZq + j];
+        }
+      }
+      unsigned long long *zig = D.zi + p * (int64_t)nzi;
+      for (int i = tid; i < nzi; i += bs) zig[i] = zacc[i];
+      if (tid == 0) D.live[p] = block_live;
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // SUM_p a(p) Z_p[b][c] per entry, one thread per (entry, range of blocks).
 template <typename T>
 __global__ void __launch_bounds__(256) block_entries_kernel(DComb5 D) {
@@ -831,6 +1075,7 @@ __global__ void __launch_bounds__(256) block_entries_kernel(DComb5 D) {
 }  // namespace
 
 size_t combine5_smem(const DComb5 &D, bool fp64) {
+  if (D.pipe) return zp_layout(D.c, D.kc, fp64 ? 8 : 4).total;
   if (D.dense) return zd_layout(D.c, D.kc, fp64 ? 8 : 4).total;
   return z5_layout(D.c, D.kc, D.npad, fp64 ? 8 : 4, D.tc).total;
 }
@@ -856,8 +1101,25 @@ static void launch_zd(const DComb5 &D, size_t smem, cudaStream_t s) {
   block_zd_kernel<T, KT><<<grid, 256, smem, s>>>(D);
 }
 
+template <typename T, int KT>
+static void launch_zp(const DComb5 &D, size_t smem, cudaStream_t s) {
+  cudaFuncSetAttribute(block_zp_kernel<T, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 1, dev = 0, nsm = 148;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_zp_kernel<T, KT>, 256, smem);
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(D.c.nblocks, (int64_t)nsm * std::max(1, per_sm)));
+  block_zp_kernel<T, KT><<<grid, 256, smem, s>>>(D);
+}
+
 void launch_combine5_z(const DComb5 &D, bool fp64, cudaStream_t s) {
   const size_t smem = combine5_smem(D, fp64);
+  if (D.pipe) {
+    const bool one = zd_ntile(D.c) <= 256;
+    if (fp64) one ? launch_zp<double, 1>(D, smem, s) : launch_zp<double, 2>(D, smem, s);
+    else one ? launch_zp<float, 1>(D, smem, s) : launch_zp<float, 2>(D, smem, s);
+    return;
+  }
   if (D.dense) {
     const bool one = zd_ntile(D.c) <= 256;  // one tile per thread
     if (fp64) one ? launch_zd<double, 1>(D, smem, s) : launch_zd<double, 2>(D, smem, s);

@@ -2101,6 +2101,33 @@ bool setup_combine5(lmfao_ctx *ctx, PhysPlan &P) {
   D.dense = !D.tc && (int)P.c3_bsrc.size() == d.nb && d.nb > 0 && combine5_dense_fits(d) &&
             !(env && std::string(env) == "general");
   if (D.dense) D.bsrc = P.arena.upload(P.c3_bsrc, ctx->stream);
+  // pipelined form: the B columns come from one outer view whose row for segment j of a block
+  // is the block's row + j (its minor-digit strides equal the segment radices)
+  if (D.dense && !(env && std::string(env) == "dense")) {
+    int ob = -1;
+    std::string why;
+    for (const int2 &b : P.c3_bsrc)
+      if (b.x >= 0) {
+        if (ob < 0) ob = b.x;
+        else if (ob != b.x) why = "B columns from several outer views";
+      }
+    if (ob < 0) why = "no B view column";
+    // one minor digit (radix 1, domain m): segment j of a block reads the view row at the
+    // block's row + j x the digit's stride in the view key
+    int nminor = 0;
+    int64_t bstride = 0;
+    for (int i = 0; why.empty() && i < d.seg.ndig; ++i)
+      if (d.seg.radix[i] < m) {
+        ++nminor;
+        bstride = d.outer[ob].dstride[i];
+        if (d.seg.radix[i] != 1 || d.seg.dom[i] != m || bstride <= 0) why = "minor digit is not the whole block";
+      }
+    if (why.empty() && nminor != 1) why = "more than one minor digit";
+    D.pipe = why.empty() ? 1 : 0;
+    D.bout = why.empty() ? ob : 0;
+    D.bstride = why.empty() ? bstride : 0;
+    if (!why.empty()) P.c5_why = "pipelined contraction declined: " + why;
+  }
   int kc0 = 64;
   if (const char *k = getenv("LMFAO_COMBINE_CHUNK")) kc0 = std::max(16, atoi(k) / 16 * 16);
   int kc = D.tc ? (int)std::min<int64_t>(kc0, (m + 15) / 16 * 16) : (int)std::min<int64_t>(kc0, m);
@@ -3863,7 +3890,8 @@ int lmfao_describe_plan(lmfao_ctx *ctx, char *buf, size_t len, size_t *needed) {
       << (!P.use_c5 ? (P.use_c3 ? "cuda cores, single kernel" : "none")
                     : P.c5.tc ? "tensor cores (tcgen05, split BF16)"
                               : std::string(P.fp64 ? "cuda cores FP64" : "cuda cores FP32") +
-                                    (P.c5.dense ? ", dense B operand" : ""))
+                                    (P.c5.pipe ? ", dense B operand, cp.async pipeline"
+                                               : P.c5.dense ? ", dense B operand" : ""))
       << "\",\"combine_chunk\":" << P.c5.kc << ",\"combine_bulk_copies\":" << (P.c5.bulk ? "true" : "false")
       << ",\"combine_blocks\":" << P.c3.nblocks << ",\"combine_entries\":" << P.c3.nent
       << ",\"block_terms\":[" << P.c3.na << "," << P.c3.nb << "," << P.c3.nbi << "]"

@@ -313,6 +313,9 @@ struct DComb5 {
   int tmem_cols;             // tensor-core path: tensor-memory columns allocated per CTA
   int tc;                    // 1: contraction on the tensor cores (split BF16)
   int dense;                 // 1: every B term is one outer-view column or 1 (block_zd_kernel)
+  int pipe;                  // dense with every B column from outer view bout, whose row for
+  int bout;                  // segment j of a block is the block's row + j x bstride
+  int64_t bstride;           // (block_zp_kernel)
   const int2 *bsrc;          // dense: per B term (outer view, column); (-1, -1) for the constant 1
   int bulk;                  // 1: per-segment sums staged with TMA bulk copies (16-byte aligned)
   int grid;                  // CTAs of block_z_kernel

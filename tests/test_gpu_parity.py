@@ -413,15 +413,18 @@ def test_favorita_projection_and_entry_combine(precision, projection, monkeypatc
 
 
 @pytest.mark.parametrize("precision,impl,chunk", [("fp32", "two", None), ("fp64", "two", None), ("fp32", "two", 16),
+                                                  ("fp64", "two", 16), ("fp32", "dense", None), ("fp32", "dense", 16),
                                                   ("split_bf16", "two", None), ("fp32", "general", None),
                                                   ("fp64", "general", None), ("fp32", "single", None),
                                                   ("fp64", "single", None)])
 def test_block_combine_kernels_match_the_oracle(precision, impl, chunk, monkeypatch):
     """The block combine as two kernels (per-block contraction into scratch, then the entries;
-    FP32 and FP64 on the CUDA cores with the B operand read from the view rows (dense) or
-    built term by term (general, TMA-staged sums), split BF16 on the tensor cores) and as the
-    single-kernel form, on the Retailer shape with ragged segments: blocks of 124 segments run
-    as chunks of 64 and 60 (the last padded to the MMA's K), or of 16 (7 full, 12 left)."""
+    FP32 and FP64 on the CUDA cores with the B operand read from the view rows: pipelined with
+    cp.async ("two", the default) or with plain loads ("dense"), or built term by term
+    ("general", TMA-staged sums); split BF16 on the tensor cores) and as the single-kernel form,
+    on the Retailer shape with ragged segments: blocks of 124 segments run as chunks of 64 and
+    60 (the last padded to the MMA's K), or of 16 (7 full, 12 left; the pipeline crosses block
+    boundaries)."""
     monkeypatch.setenv("LMFAO_COMBINE", impl)
     if chunk:
         monkeypatch.setenv("LMFAO_COMBINE_CHUNK", str(chunk))
@@ -437,11 +440,13 @@ def test_block_combine_kernels_match_the_oracle(precision, impl, chunk, monkeypa
         assert phys["block_combine"] == (impl != "single" or precision != "fp64"), phys
         assert phys["block_combine_two_kernels"] == (impl != "single"), phys["combine_note"]
         if impl != "single":
-            dense = impl == "two" and precision != "split_bf16"
+            dense = impl in ("two", "dense") and precision != "split_bf16"
             assert phys["combine_bulk_copies"] == (not dense), phys
             want = {"fp32": "cuda cores FP32", "fp64": "cuda cores FP64",
                     "split_bf16": "tensor cores (tcgen05, split BF16)"}[precision]
-            assert phys["contraction"] == want + (", dense B operand" if dense else ""), phys
+            if dense:
+                want += ", dense B operand" + (", cp.async pipeline" if impl == "two" else "")
+            assert phys["contraction"] == want, phys
             assert phys["combine_chunk"] == (chunk or 64), phys
         e.run()
         got = e.fetch_all()
