@@ -43,6 +43,11 @@ struct lmfao_ctx {
   std::vector<std::string> ev_names;
   std::vector<std::string> kernel_names;
   std::vector<lmfao_reorg> reorg;   // reorganised root relations (see lmfao_reorg)
+  // side streams on which the views of different subtrees of the root run concurrently (created
+  // when a plan first has views in two subtrees; fork / join events)
+  static constexpr int kViewLanes = 4;
+  cudaStream_t view_stream[kViewLanes] = {};
+  cudaEvent_t view_fork = nullptr, view_join[kViewLanes] = {};
   // A batch planned with several physical roots (plan == nullptr then): one plan per root.
   std::vector<lmfao_subplan> subs;
   std::vector<std::pair<int, int>> qroute;  // batch query -> (index in subs, local query id)

@@ -2606,18 +2606,43 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   if (!P.fast.on && !P.b0f.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * P.b0f.size() * (P.fp64 ? 8 : 4), s));
   if (!P.fast.on && !P.b0i.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * P.b0i.size() * 8, s));
   mark("memset");
+  // views: the subtrees of different children of the root are independent, so (unless the run
+  // is timed kernel by kernel) each runs on a side stream of its own, forked from and joined
+  // back into s; within a subtree the post-order keeps children before parents
+  std::vector<int> lane(P.vk.size(), -1);
+  int nlanes = 0;
+  if (!ctx->profiling && ctx->view_fork) {
+    std::map<int, int> of_branch;
+    for (size_t i = 0; i < P.vk.size(); ++i) {
+      const int br = P.branch[P.vk_rel[i]];
+      auto it = of_branch.find(br);
+      if (it == of_branch.end()) it = of_branch.emplace(br, (int)(of_branch.size() % lmfao_ctx::kViewLanes)).first;
+      lane[i] = it->second;
+    }
+    nlanes = std::min<int>((int)of_branch.size(), lmfao_ctx::kViewLanes);
+    if (nlanes < 2) std::fill(lane.begin(), lane.end(), -1), nlanes = 0;
+  }
+  if (nlanes) {
+    LMFAO_CUDA(cudaEventRecord(ctx->view_fork, s));
+    for (int l = 0; l < nlanes; ++l) LMFAO_CUDA(cudaStreamWaitEvent(ctx->view_stream[l], ctx->view_fork, 0));
+  }
   for (size_t i = 0; i < P.vk.size(); ++i) {
     int r = P.vk_rel[i];
     View &v = P.views[r];
+    cudaStream_t vs = lane[i] >= 0 ? ctx->view_stream[lane[i]] : s;
     if (!v.keyrow) {  // the key-major kernel writes every cell
-      LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
-      if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
+      LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, vs));
+      if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, vs));
     }
-    launch_view_kernel(P.vk[i], s);
+    launch_view_kernel(P.vk[i], vs);
     // the FP32 copy is read by the general fact pass only
     launch_view_finish(v.v64, P.fast.on ? nullptr : v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint,
-                       v.nkeys, P.err, s);
+                       v.nkeys, P.err, vs);
     mark("view:" + ctx->rels[r].name);
+  }
+  for (int l = 0; l < nlanes; ++l) {
+    LMFAO_CUDA(cudaEventRecord(ctx->view_join[l], ctx->view_stream[l]));
+    LMFAO_CUDA(cudaStreamWaitEvent(s, ctx->view_join[l], 0));
   }
   launch_segment_weights(P.sw, s);
   mark("segment_weights");
@@ -2899,6 +2924,14 @@ void build_plan(lmfao_ctx *ctx, const lmfao_plan_opts &o, bool dry, std::vector<
   setup_root(ctx, *P, ctx->tree);
   setup_passes(ctx, *P, ctx->tree);
   LMFAO_CUDA(cudaStreamSynchronize(ctx->stream));
+  // side streams for views of different subtrees (once per context)
+  if (!ctx->view_fork && P->vk.size() > 1) {
+    LMFAO_CUDA(cudaEventCreateWithFlags(&ctx->view_fork, cudaEventDisableTiming));
+    for (int i = 0; i < lmfao_ctx::kViewLanes; ++i) {
+      LMFAO_CUDA(cudaStreamCreateWithFlags(&ctx->view_stream[i], cudaStreamNonBlocking));
+      LMFAO_CUDA(cudaEventCreateWithFlags(&ctx->view_join[i], cudaEventDisableTiming));
+    }
+  }
   ctx->planned = true;
 }
 
@@ -3323,6 +3356,11 @@ int lmfao_destroy(lmfao_ctx *ctx) {
     for (auto &kv : E.cols) cudaFree(kv.second);
   }
   for (auto e : ctx->events) cudaEventDestroy(e);
+  for (int i = 0; i < lmfao_ctx::kViewLanes; ++i) {
+    if (ctx->view_stream[i]) cudaStreamDestroy(ctx->view_stream[i]);
+    if (ctx->view_join[i]) cudaEventDestroy(ctx->view_join[i]);
+  }
+  if (ctx->view_fork) cudaEventDestroy(ctx->view_fork);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return LMFAO_OK;
