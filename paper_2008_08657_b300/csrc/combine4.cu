@@ -262,28 +262,39 @@ __global__ void __launch_bounds__(256) entry_kernel(const DComb4 dp) {
   const int J = e.job;
   const int n = e.cls == 0 ? 1 : e.cls == 1 ? dp.dom0 : dp.dom1;
   const DTab4 &tb = dp.tab[e.cls == 0 ? 1 : e.cls];
-  for (int x = lane; x < n; x += 32) {
-    double yf = 0.0;
-    unsigned long long yi = 0ull;
-    if (e.cls == 0) {
-      if (yint_col) yi = dp.yall_i[J];
-      else yf = dp.yall_f[J];
-    } else {
-      const int64_t at = (int64_t)J * n + x;
-      if (yint_col) yi = e.cls == 1 ? dp.yd0_i[at] : dp.yd1_i[at];
-      else yf = e.cls == 1 ? dp.yd0_f[at] : dp.yd1_f[at];
+  if (e.cls == 0) {
+    if (lane == 0) {
+      const unsigned long long yi = yint_col ? dp.yall_i[J] : 0ull;
+      const double yf = yint_col ? 0.0 : dp.yall_f[J];
+      if (integ) si[0] += yi;
+      else sf[0] += yint_col ? (double)yi : yf;
     }
-    if (yi == 0ull && yf == 0.0) continue;
-    const long long cell = e.cls == 0 ? 0 : tb.cell[(int64_t)e.tog * n + x];
-    if (cell < 0) continue;
-    double pv = 1.0;
-    unsigned long long pi = 1ull;
-    if (e.cls != 0) {
-      pv = tb.pf[(int64_t)e.psi * n + x];
-      pi = tb.pi[(int64_t)e.psi * n + x];
+  } else {
+    const unsigned long long *ypi = e.cls == 1 ? dp.yd0_i : dp.yd1_i;
+    const double *ypf = e.cls == 1 ? dp.yd0_f : dp.yd1_f;
+    constexpr int U = 4;  // digit values per lane whose loads are issued together
+    for (int x0 = lane; x0 < n; x0 += 32 * U) {
+      double yf[U], pv[U];
+      unsigned long long yi[U], pi[U];
+      long long cl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int x = x0 + 32 * u;
+        const bool in = x < n;
+        const int64_t at = (int64_t)J * n + x;
+        yi[u] = in && yint_col ? ypi[at] : 0ull;
+        yf[u] = in && !yint_col ? ypf[at] : 0.0;
+        cl[u] = in ? tb.cell[(int64_t)e.tog * n + x] : -1;
+        pv[u] = in ? tb.pf[(int64_t)e.psi * n + x] : 0.0;
+        pi[u] = in ? tb.pi[(int64_t)e.psi * n + x] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((yi[u] == 0ull && yf[u] == 0.0) || cl[u] < 0) continue;
+        if (integ) atomicAdd(si + cl[u], pi[u] * yi[u]);
+        else atomicAdd(sf + cl[u], pv[u] * (yint_col ? (double)yi[u] : yf[u]));
+      }
     }
-    if (integ) atomicAdd(si + cell, pi * yi);
-    else atomicAdd(sf + cell, pv * (yint_col ? (double)yi : yf));
   }
   __syncwarp();
   const int r0 = d.og_off[e.og], r1 = d.og_off[e.og + 1];
@@ -497,7 +508,7 @@ void launch_combine4(const DComb4 &d, bool fp64, cudaStream_t s) {
   else proj_d0_kernel<float><<<dim3(d.dom0, tiles, z0), bs, 0, s>>>(d);
   if (d.nent3) {
     const int etiles = (d.nent3 + bs - 1) / bs;
-    const int r3 = std::max(1, (2 * 148 + etiles - 1) / etiles);
+    const int r3 = std::max(1, (6 * 148 + etiles - 1) / etiles);  // several CTAs per SM
     const size_t sm3 = (size_t)8 * std::max(1, d.max_slots3);
     if (fp64) {
       cudaFuncSetAttribute(class3_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
