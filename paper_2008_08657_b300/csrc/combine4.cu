@@ -272,6 +272,11 @@ __global__ void __launch_bounds__(256) entry_kernel(const DComb4 dp) {
   } else {
     const unsigned long long *ypi = e.cls == 1 ? dp.yd0_i : dp.yd1_i;
     const double *ypf = e.cls == 1 ? dp.yd0_f : dp.yd1_f;
+    // one cell (an ungrouped aggregate): lane sums in registers, one warp reduction, instead of
+    // every lane adding to the same shared word
+    unsigned long long li = 0ull;
+    double lf = 0.0;
+    const bool one = ncell == 1;
     constexpr int U = 4;  // digit values per lane whose loads are issued together
     for (int x0 = lane; x0 < n; x0 += 32 * U) {
       double yf[U], pv[U];
@@ -291,8 +296,25 @@ __global__ void __launch_bounds__(256) entry_kernel(const DComb4 dp) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if ((yi[u] == 0ull && yf[u] == 0.0) || cl[u] < 0) continue;
-        if (integ) atomicAdd(si + cl[u], pi[u] * yi[u]);
-        else atomicAdd(sf + cl[u], pv[u] * (yint_col ? (double)yi[u] : yf[u]));
+        if (one) {
+          if (integ) li += pi[u] * yi[u];
+          else lf += pv[u] * (yint_col ? (double)yi[u] : yf[u]);
+        } else if (integ) {
+          atomicAdd(si + cl[u], pi[u] * yi[u]);
+        } else {
+          atomicAdd(sf + cl[u], pv[u] * (yint_col ? (double)yi[u] : yf[u]));
+        }
+      }
+    }
+    if (one) {
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        li += __shfl_xor_sync(0xffffffffu, li, o);
+        lf += __shfl_xor_sync(0xffffffffu, lf, o);
+      }
+      if (lane == 0) {
+        if (integ) si[0] += li;
+        else sf[0] += lf;
       }
     }
   }

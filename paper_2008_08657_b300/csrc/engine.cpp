@@ -2050,6 +2050,7 @@ bool setup_combine4(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
   // projection kernels for many (Favorita's 379, where the streaming form measured slower);
   // LMFAO_PROJECTION=stream|kernels overrides. Tiles of about 6,144 staged sums, about two CTAs
   // per SM, class 3 fused when its cells fit.
+  d.nslots3 = (int)std::min<long long>(nslots3, 1 << 30);
   const char *pk = std::getenv("LMFAO_PROJECTION");
   d.stream = pk ? (std::string(pk) == "stream" ? 1 : 0) : (nj <= 64 ? 1 : 0);
   if (d.stream) {
@@ -2059,7 +2060,6 @@ bool setup_combine4(lmfao_ctx *ctx, PhysPlan &P, const std::vector<DPsi> &psi, c
     int ny = (int)std::max<int64_t>(1, std::min<int64_t>(d.dom0, 296 / std::max(1, d.nx)));
     d.c0 = (d.dom0 + ny - 1) / ny;
     d.ny = (d.dom0 + d.c0 - 1) / d.c0;
-    d.nslots3 = (int)std::min<long long>(nslots3, 1 << 30);
     const size_t tab3 = (size_t)d.c1 * (2 * d.tab[3].nt + d.tab[3].ng);  // staged terms and cells of a row
     d.fused3 = d.nent3 > 0 && d.nent3 <= 512 && 8 * (2 * (size_t)d.c1 * nj + (size_t)nslots3 + tab3 + nj) <= 200 * 1024
                    ? 1 : 0;
