@@ -489,10 +489,10 @@ struct Compiled {
 std::mutex cache_mu;
 std::map<std::string, Compiled> cache;  // by source text (the device is the same sm_103a part)
 
-Compiled compile(const std::string &src) {
+Compiled compile(const std::string &src, const char *name = "lmfao_gen_root_pass") {
   Compiled c;
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "lmfao_gen_root_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+  if (nvrtcCreateProgram(&prog, src.c_str(), "lmfao_gen.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
     c.err = "nvrtcCreateProgram failed";
     return c;
   }
@@ -519,7 +519,7 @@ Compiled compile(const std::string &src) {
     return c;
   }
   cudaKernel_t k;
-  if (cudaLibraryGetKernel(&k, lib, "lmfao_gen_root_pass") != cudaSuccess) {
+  if (cudaLibraryGetKernel(&k, lib, name) != cudaSuccess) {
     cudaGetLastError();
     c.err = "cudaLibraryGetKernel failed";
     return c;
@@ -701,6 +701,144 @@ cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid,
   }
   void *fargs[] = {&f};
   return cudaLaunchKernel(g.fn, dim3(grid), dim3(g.block), fargs, g.smem, s);
+}
+
+
+// ------------------------------------------------------------------ generated view kernel
+// The view of a relation with unique keys and no children (view_key_rows_kernel's job) with
+// the columns as straight-line code: one thread per key reads the row's input columns into
+// registers once, forms every column (product of its factors, left to right as fac_at does,
+// times 1 or 0 for the row's presence) and its codes, into a shared tile written out by the
+// CTA as one contiguous span.
+namespace {
+const char *cmp_text(int op) {
+  switch (op) {
+    case LMFAO_LE: return "<=";
+    case LMFAO_LT: return "<";
+    case LMFAO_GE: return ">=";
+    case LMFAO_GT: return ">";
+    case LMFAO_EQ: return "==";
+    default: return "!=";
+  }
+}
+std::string flt_lit(float t) {
+  std::ostringstream o;
+  o.precision(9);
+  o << std::scientific << t << "f";
+  return o.str();
+}
+}  // namespace
+
+std::string gen_view_source(const DViewKernel &d, const std::vector<int> &cfo, const std::vector<DFac> &facs,
+                            const std::vector<int4> &cdesc, const std::vector<float> &thr) {
+  const int W = d.ncols + 1, KB = kVkb;
+  std::ostringstream o;
+  o << "// generated view kernel\n";
+  o << "struct GenArgs { unsigned long long v[32]; };\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << KB << ") lmfao_gen_view(const GenArgs a) {\n";
+  o << "  __shared__ double tile[" << KB * W << "];\n";
+  o << "  const long long nkeys = (long long)a.v[0];\n";
+  o << "  const int *__restrict__ keyrow = (const int *)a.v[1];\n";
+  o << "  double *v64 = (double *)a.v[2];\n";
+  o << "  int *codes = (int *)a.v[3];\n";
+  std::vector<bool> used(d.ncolsin, false);
+  for (const DFac &f : facs) used[f.col] = true;
+  for (const int4 &c : cdesc) used[c.x] = true;
+  auto ctype = [&](int slot) {
+    return d.in[slot].dtype == LMFAO_F32 ? "float" : d.in[slot].dtype == LMFAO_U8 ? "unsigned char" : "int";
+  };
+  for (int i = 0; i < d.ncolsin; ++i)
+    if (used[i]) o << "  const " << ctype(i) << " *__restrict__ c" << i << " = (const " << ctype(i) << " *)a.v[" << 4 + i << "];\n";
+  o << "  const int t = threadIdx.x;\n";
+  o << "  const long long k0 = (long long)blockIdx.x * " << KB << ";\n";
+  o << "  const int nk = (int)(nkeys - k0 < " << KB << " ? nkeys - k0 : " << KB << ");\n";
+  o << "  if (t < nk) {\n";
+  o << "    const long long k = k0 + t;\n";
+  o << "    const int r = keyrow[k];\n";
+  o << "    const bool live = r >= 0;\n";
+  o << "    const int rr = live ? r : 0;\n";
+  for (int i = 0; i < d.ncolsin; ++i)
+    if (used[i]) o << "    const " << ctype(i) << " x" << i << " = c" << i << "[rr];\n";
+  o << "    const double lv = live ? 1.0 : 0.0;\n";
+  for (int j = 0; j < d.ncols; ++j) {
+    std::string e = "lv";
+    for (int f = cfo[j]; f < cfo[j + 1]; ++f) {
+      const DFac &fc = facs[f];
+      std::string term;
+      if (fc.ind) {
+        // predicates compare the stored value: FP32 columns in FP32, integer columns exactly
+        const std::string x = "x" + std::to_string(fc.col);
+        term = d.in[fc.col].dtype == LMFAO_F32 ? "(" + x + " " + cmp_text(fc.op) + " " + flt_lit(fc.t) + " ? 1.0 : 0.0)"
+                                              : "((double)" + x + " " + cmp_text(fc.op) + " (double)" + flt_lit(fc.t) + " ? 1.0 : 0.0)";
+      } else {
+        const std::string x = "(double)x" + std::to_string(fc.col);
+        term = x;
+        for (int p = 1; p < fc.pow; ++p) term = "(" + term + " * " + x + ")";
+      }
+      e = "(" + e + " * " + term + ")";
+    }
+    o << "    tile[t * " << W << " + " << j << "] = " << e << ";\n";
+  }
+  for (size_t c = 0; c < cdesc.size(); ++c) {
+    const int4 cd = cdesc[c];
+    std::string code;
+    if (cd.y == LMFAO_GB_BUCKET) {
+      const std::string xf = "(float)x" + std::to_string(cd.x);
+      code = "0";
+      for (int q = 0; q < cd.w; ++q) code += " + (" + flt_lit(thr[cd.z + q]) + " < " + xf + ")";
+    } else {
+      code = "(int)x" + std::to_string(cd.x);
+    }
+    o << "    codes[k * " << cdesc.size() << " + " << c << "] = live ? (" << code << ") : -1;\n";
+  }
+  o << "  }\n";
+  o << "  __syncthreads();\n";
+  o << "  const int lane = t & 31, warp = t >> 5;\n";
+  o << "  double *out = v64 + k0 * " << d.ncols << ";\n";
+  o << "  for (int q = warp; q < nk; q += " << KB / 32 << ")\n";
+  o << "    for (int j = lane; j < " << d.ncols << "; j += 32) out[(long long)q * " << d.ncols << " + j] = tile[q * " << W
+    << " + j];\n";
+  o << "}\n";
+  return o.str();
+}
+
+GenView gen_view(const DViewKernel &d, const std::vector<int> &cfo, const std::vector<DFac> &facs,
+                 const std::vector<int4> &cdesc, const std::vector<float> &thr) {
+  GenView g;
+  if (!d.keyrow) g.why = "keys not unique or key tile too large";
+  else if (d.nchild) g.why = "relation with children";
+  else if (d.ncolsin > 28) g.why = "more than 28 input columns";
+  else if (d.ncols > 64) g.why = "more than 64 columns";
+  for (const int4 &c : cdesc)
+    if (c.x < 0) g.why = "code from a child";
+  if (!g.why.empty()) return g;
+  const std::string src = gen_view_source(d, cfo, facs, cdesc, thr);
+  g.source_hash = fnv1a_hex(src);
+  Compiled c;
+  {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    auto it = cache.find(src);
+    if (it != cache.end()) c = it->second;
+    else {
+      c = compile(src, "lmfao_gen_view");
+      cache[src] = c;
+    }
+  }
+  if (!c.fn) g.why = c.err;
+  g.fn = c.fn;
+  return g;
+}
+
+cudaError_t launch_gen_view(const GenView &g, const DViewKernel &d, cudaStream_t s) {
+  if (d.nkeys == 0) return cudaSuccess;
+  struct { unsigned long long v[32]; } a{};
+  a.v[0] = (unsigned long long)d.nkeys;
+  a.v[1] = (unsigned long long)d.keyrow;
+  a.v[2] = (unsigned long long)d.v64;
+  a.v[3] = (unsigned long long)d.codes;
+  for (int i = 0; i < d.ncolsin && i < 28; ++i) a.v[4 + i] = (unsigned long long)d.in[i].p;
+  void *args[] = {&a};
+  return cudaLaunchKernel(g.fn, dim3((unsigned)((d.nkeys + kVkb - 1) / kVkb)), dim3(kVkb), args, 0, s);
 }
 
 }  // namespace lmfao

@@ -51,6 +51,19 @@ std::string gen_family_source(const DFast &d, bool fp64, int block, const std::v
 // Launch a generated root pass on stream s over `grid` CTAs.
 cudaError_t launch_gen_root_pass(const GenRootPass &g, const DFast &d, int grid, cudaStream_t s);
 
+// Generated view kernel of a unique-key relation without children (codegen.cpp): the view's
+// columns and codes as straight-line code per key; cfo, facs, cdesc and thr are the host copies
+// of the kernel's column factor offsets, factors, code descriptors and bucket thresholds.
+struct GenView {
+  const void *fn = nullptr;  // null: view_key_rows_kernel runs
+  std::string why, source_hash;
+};
+GenView gen_view(const DViewKernel &d, const std::vector<int> &cfo, const std::vector<DFac> &facs,
+                 const std::vector<int4> &cdesc, const std::vector<float> &thr);
+std::string gen_view_source(const DViewKernel &d, const std::vector<int> &cfo, const std::vector<DFac> &facs,
+                            const std::vector<int4> &cdesc, const std::vector<float> &thr);
+cudaError_t launch_gen_view(const GenView &g, const DViewKernel &d, cudaStream_t s);
+
 // The source text that gen_root_pass compiles for d (for tests and inspection).
 std::string gen_root_pass_source(const DFast &d, bool fp64, int block);
 

@@ -1298,6 +1298,12 @@ void setup_views(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, bool need32) {
     }
     d.keyrow = v.keyrow;
     d.nkeys = v.nkeys;
+    // unique keys and no children: the view kernel generated for these columns (LMFAO_CODEGEN=0
+    // keeps the built-in one)
+    GenView gv;
+    const char *cg = std::getenv("LMFAO_CODEGEN");
+    if (v.keyrow && !(cg && std::atoi(cg) == 0)) gv = gen_view(d, cfo, facs, cdesc, thr);
+    P.vgen.push_back(gv);
     d.col_fac_off = P.arena.upload(cfo, s);
     d.facs = P.arena.upload(facs, s);
     d.col_part_off = P.arena.upload(cpo, s);
@@ -2634,7 +2640,8 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
       LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, vs));
       if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, vs));
     }
-    launch_view_kernel(P.vk[i], vs);
+    if (P.vgen[i].fn) LMFAO_CUDA(launch_gen_view(P.vgen[i], P.vk[i], vs));
+    else launch_view_kernel(P.vk[i], vs);
     // the FP32 copy is read by the general fact pass only
     launch_view_finish(v.v64, P.fast.on ? nullptr : v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint,
                        v.nkeys, P.err, vs);
@@ -3167,7 +3174,8 @@ int view_flags(lmfao_ctx *ctx) {
       LMFAO_CUDA(cudaMemsetAsync(v.v64, 0, v.nkeys * v.cols.size() * 8, s));
       if (!v.codes.empty()) LMFAO_CUDA(cudaMemsetAsync(v.vcodes, 0xff, v.nkeys * v.codes.size() * 4, s));
     }
-    launch_view_kernel(P.vk[i], s);
+    if (P.vgen[i].fn) LMFAO_CUDA(launch_gen_view(P.vgen[i], P.vk[i], s));
+    else launch_view_kernel(P.vk[i], s);
     launch_view_finish(v.v64, v.v32, v.vint, v.intcols_dev, (int)v.cols.size(), v.nint, v.nkeys, P.err, s);
   }
   LMFAO_CUDA(cudaGetLastError());

@@ -145,6 +145,7 @@ struct PhysPlan {
   int *err = nullptr;
   std::vector<DViewKernel> vk;     // per view relation, in post order
   std::vector<int> vk_rel;
+  std::vector<GenView> vgen;       // per view: the generated kernel (null fn: a built-in one runs)
   DFactPass fp{};
   DCombine cb{};
   DComb2 c2{};

@@ -44,7 +44,46 @@ static DFast lean_base() {
   return d;
 }
 
+// A Weather-like view (2 key columns, 8 float attributes; columns 1, w_i, w_i w_j) and an
+// Item-like one (a categorical code, a bucketed code, an indicator factor).
+static void check_views() {
+  static int dummy_keyrow = 0;
+  DViewKernel d{};
+  d.keyrow = &dummy_keyrow;
+  d.nkeys = 161200;
+  d.ncolsin = 10;
+  for (int i = 0; i < 10; ++i) d.in[i] = DCol{nullptr, i < 2 ? LMFAO_I32 : LMFAO_F32};
+  std::vector<int> cfo{0};
+  std::vector<DFac> facs;
+  cfo.push_back(0);  // COUNT
+  for (int a = 0; a < 8; ++a) { facs.push_back(DFac{2 + a, 0, 1, 0, 0.f}); cfo.push_back((int)facs.size()); }
+  for (int a = 0; a < 8; ++a)
+    for (int b = a; b < 8; ++b) {
+      if (a == b) facs.push_back(DFac{2 + a, 0, 2, 0, 0.f});
+      else { facs.push_back(DFac{2 + a, 0, 1, 0, 0.f}); facs.push_back(DFac{2 + b, 0, 1, 0, 0.f}); }
+      cfo.push_back((int)facs.size());
+    }
+  d.ncols = (int)cfo.size() - 1;
+  std::vector<int4> cdesc;
+  std::vector<float> thr;
+  check("view_weather", gen_view_source(d, cfo, facs, cdesc, thr));
+  DViewKernel e{};
+  e.keyrow = &dummy_keyrow;
+  e.nkeys = 3700;
+  e.ncolsin = 4;
+  e.in[0] = DCol{nullptr, LMFAO_I32}; e.in[1] = DCol{nullptr, LMFAO_F32}; e.in[2] = DCol{nullptr, LMFAO_I32};
+  e.in[3] = DCol{nullptr, LMFAO_U8};
+  std::vector<int> cfo2{0, 0, 1, 3};
+  std::vector<DFac> facs2{DFac{1, 0, 1, 0, 0.f}, DFac{1, 0, 2, 0, 0.f}, DFac{3, 1, 1, LMFAO_GT, 0.5f}};
+  e.ncols = 3;
+  std::vector<int4> cdesc2{make_int4(2, 0, 0, 0), make_int4(1, LMFAO_GB_BUCKET, 0, 3)};
+  std::vector<float> thr2{-1.f, 0.f, 1.f};
+  e.ncodes = 2;
+  check("view_item", gen_view_source(e, cfo2, facs2, cdesc2, thr2));
+}
+
 int main() {
+  check_views();
   for (int fp64 = 0; fp64 < 2; ++fp64) {
     const int block = fp64 ? 512 : 1024;
     const std::string sfx = fp64 ? "_fp64" : "_fp32";

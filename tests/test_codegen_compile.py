@@ -34,7 +34,7 @@ def results():
     return {line.split()[0]: line.split()[1:] for line in out.splitlines() if line.strip()}
 
 
-SHAPES = [f"{s}_{p}" for s in ("lean_retailer", "lean_retailer_lanes", "lean_favorita", "lean_no_inner", "dt_level", "dt_leaf_sums",
+SHAPES = ["view_weather", "view_item"] + [f"{s}_{p}" for s in ("lean_retailer", "lean_retailer_lanes", "lean_favorita", "lean_no_inner", "dt_level", "dt_leaf_sums",
                                     "general_no_inner")
           for p in ("fp32", "fp64")]
 
@@ -45,5 +45,6 @@ def test_generated_source_compiles_without_spills(results, shape):
     status = results[shape]
     assert status[0] == "ok", " ".join(status)
     regs, spill = int(status[1]), int(status[2])
-    assert 0 < regs <= (64 if shape.endswith("fp32") else 128)
+    # root passes run 1024 threads per SM (64 registers each in FP32); view kernels 128-thread CTAs
+    assert 0 < regs <= (128 if shape.endswith("fp64") or shape.startswith("view") else 64)
     assert spill == 0
