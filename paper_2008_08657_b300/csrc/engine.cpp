@@ -2607,14 +2607,10 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   };
   mark("start");
   LMFAO_CUDA(cudaMemsetAsync(P.err, 0, 4, s));
-  if (P.nfsum) LMFAO_CUDA(cudaMemsetAsync(P.fsum, 0, P.nfsum * 8, s));
-  if (P.nicnt) LMFAO_CUDA(cudaMemsetAsync(P.icnt, 0, P.nicnt * 8, s));
-  if (!P.fast.on && !P.b0f.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * P.b0f.size() * (P.fp64 ? 8 : 4), s));
-  if (!P.fast.on && !P.b0i.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * P.b0i.size() * 8, s));
-  mark("memset");
   // views: the subtrees of different children of the root are independent, so (unless the run
   // is timed kernel by kernel) each runs on a side stream of its own, forked from and joined
-  // back into s; within a subtree the post-order keeps children before parents
+  // back into s; within a subtree the post-order keeps children before parents. The zeroing of
+  // the outputs and of the root pass's arrays runs on s meanwhile.
   std::vector<int> lane(P.vk.size(), -1);
   int nlanes = 0;
   if (!ctx->profiling && ctx->view_fork) {
@@ -2632,6 +2628,22 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     LMFAO_CUDA(cudaEventRecord(ctx->view_fork, s));
     for (int l = 0; l < nlanes; ++l) LMFAO_CUDA(cudaStreamWaitEvent(ctx->view_stream[l], ctx->view_fork, 0));
   }
+  if (P.nfsum) LMFAO_CUDA(cudaMemsetAsync(P.fsum, 0, P.nfsum * 8, s));
+  if (P.nicnt) LMFAO_CUDA(cudaMemsetAsync(P.icnt, 0, P.nicnt * 8, s));
+  if (!P.fast.on && !P.b0f.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * P.b0f.size() * (P.fp64 ? 8 : 4), s));
+  if (!P.fast.on && !P.b0i.empty()) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * P.b0i.size() * 8, s));
+  if (P.fast.on) {
+    const DFast &d = P.fd;
+    if (d.nm * d.nw) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * d.nm * d.nw * (P.fp64 ? 8 : 4), s));
+    if (d.n0i) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * d.n0i * 8, s));
+    if (d.phi1f_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1f, 0, P.nseg * d.phi1f_seg * 4, s));
+    if (d.phi1i_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1i, 0, P.nseg * d.phi1i_seg * 4, s));
+    if (d.n3f) LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3f * d.b3leaf * 8, s));
+    if (d.n3f && !d.smem_p && !P.fp64) LMFAO_CUDA(cudaMemsetAsync(d.p3f32, 0, d.nkeys * d.n3f * d.b3leaf * 4, s));
+    if (d.n3i) LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3i * d.b3leaf * 8, s));
+    LMFAO_CUDA(cudaMemsetAsync(d.ticket, 0, 4, s));
+  }
+  mark("memset");
   for (size_t i = 0; i < P.vk.size(); ++i) {
     int r = P.vk_rel[i];
     View &v = P.views[r];
@@ -2653,16 +2665,9 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
   }
   launch_segment_weights(P.sw, s);
   mark("segment_weights");
+  bool b3_side = false;
   if (P.fast.on) {
     const DFast &d = P.fd;
-    if (d.nm * d.nw) LMFAO_CUDA(cudaMemsetAsync(P.phi0f, 0, P.nseg * d.nm * d.nw * (P.fp64 ? 8 : 4), s));
-    if (d.n0i) LMFAO_CUDA(cudaMemsetAsync(P.phi0i, 0, P.nseg * d.n0i * 8, s));
-    if (d.phi1f_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1f, 0, P.nseg * d.phi1f_seg * 4, s));
-    if (d.phi1i_seg) LMFAO_CUDA(cudaMemsetAsync(d.phi1i, 0, P.nseg * d.phi1i_seg * 4, s));
-    if (d.n3f) LMFAO_CUDA(cudaMemsetAsync(d.p3f, 0, d.nkeys * d.n3f * d.b3leaf * 8, s));
-    if (d.n3f && !d.smem_p && !P.fp64) LMFAO_CUDA(cudaMemsetAsync(d.p3f32, 0, d.nkeys * d.n3f * d.b3leaf * 4, s));
-    if (d.n3i) LMFAO_CUDA(cudaMemsetAsync(d.p3i, 0, d.nkeys * d.n3i * d.b3leaf * 8, s));
-    LMFAO_CUDA(cudaMemsetAsync(d.ticket, 0, 4, s));
     if (d.ni) {
       const View &v = P.views[P.inner[0]];
       launch_fast_prep(d, v.v64, (int)v.cols.size(), P.fwcol_dev, v.vcodes, (int)v.codes.size(), P.fcodecol_dev,
@@ -2675,7 +2680,18 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
       throw Error(LMFAO_ERR_UNSUPPORTED, "internal: no root-pass variant for this shape");
     }
     mark("fact_pass");
-    if (P.b3f.nitems) launch_b3_final(P.b3f, s);
+    if (P.b3f.nitems) {
+      // the inner relation's outputs (atomic adds) are independent of the combine: on a side
+      // stream, joined at the end of the run
+      if (nlanes) {
+        LMFAO_CUDA(cudaEventRecord(ctx->view_fork, s));
+        LMFAO_CUDA(cudaStreamWaitEvent(ctx->view_stream[0], ctx->view_fork, 0));
+        launch_b3_final(P.b3f, ctx->view_stream[0]);
+        b3_side = true;
+      } else {
+        launch_b3_final(P.b3f, s);
+      }
+    }
     mark("b3_final");
   } else {
     launch_fact_pass(P.fp, P.fp64, P.nb0, P.fp_grid, P.fp_block, s);
@@ -2705,6 +2721,10 @@ void enqueue_run(lmfao_ctx *ctx, PhysPlan &P, const JoinTree &t, cudaStream_t s)
     }
   }
   mark("combine");
+  if (b3_side) {
+    LMFAO_CUDA(cudaEventRecord(ctx->view_join[0], ctx->view_stream[0]));
+    LMFAO_CUDA(cudaStreamWaitEvent(s, ctx->view_join[0], 0));
+  }
   LMFAO_CUDA(cudaGetLastError());
   (void)t;
 }
