@@ -223,9 +223,15 @@ LMFAO_API int lmfao_clear_batch(struct lmfao_ctx *ctx);
  * relation's view toward the root; this is checked on the loaded data while planning. The
  * heuristic planner then moves the root (largest relations first) and a forced root that
  * fails gives LMFAO_ERR_UNSUPPORTED.
- * Environment: LMFAO_CODEGEN=0 never generates, =1 generates at any size;
- * LMFAO_NO_PROJECTION_COMBINE selects the entry-wise combine where the projection
- * combine would run; LMFAO_COMBINE=single keeps the single-kernel block combine. */
+ * The views of relations with unique keys and no children are generated the same way.
+ * Environment (for comparisons and tests; every form computes the same aggregates):
+ * LMFAO_CODEGEN=0 never generates (root pass and views), =1 generates the root pass at any
+ * size; LMFAO_ROOT_LANES=1 generates the one-tuple-per-lane layout of the root pass;
+ * LMFAO_NO_PROJECTION_COMBINE selects the entry-wise combine where the projection combine
+ * would run, LMFAO_PROJECTION=stream|kernels its streaming or per-projection form;
+ * LMFAO_COMBINE=single keeps the single-kernel block combine, =general the term-by-term
+ * two-kernel form, =dense the dense form without the cp.async pipeline;
+ * LMFAO_COMBINE_CHUNK sets the block combine's chunk of segments. */
 LMFAO_API int lmfao_plan(struct lmfao_ctx *ctx, const lmfao_plan_opts *opts, lmfao_plan_info *info);
 
 /* Candidate physical plans of the current batch (root relation, segment relation, root
